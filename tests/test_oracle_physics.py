@@ -1,0 +1,232 @@
+"""Physics pins of the oracle's full step against what the paper and the mathematics
+fix: exact mass conservation (Eqs. 1-5 with bounce-back), the telescoping energy
+balance of the finite-volume diffusion term (Eqs. 22-26), the exact series-
+resistance steady state of 1D conduction (Section 3.2), thermodynamic
+consistency of the flat interface (Section 3.1), the contact angle quoted in
+Section 4.2, the Laplace law and the nucleation-site table (Fig. 6b)."""
+import numpy as np
+import pytest
+
+from oracle import Domain, Params, eos, nucleation_Gw
+from paper_1812_10375_gb300 import workloads as wl
+
+
+def _flat(coex, **kw):
+    case = wl.flat_interface()
+    rho0, T0 = wl.initial_fields(case, coex["rho_l"], coex["rho_v"], coex["Tc"])
+    p = Params(nx=case.nx, ny=case.ny, wall_rows=case.wall_rows, top_bc=case.top_bc,
+               T_bottom=case.T_bottom(coex["Tc"]), T_top=case.T_top(coex["Tc"]),
+               eos_T_fixed=True, Gw=0.0, g_y=0.0, rho_l=coex["rho_l"], rho_v=coex["rho_v"], **kw)
+    return p, rho0, T0
+
+
+def test_mass_conserved_closed_flat_interface(coex):
+    p, rho0, T0 = _flat(coex)
+    d = Domain(p, rho0, T0).step(1)
+    m1 = d.diag()["mass"]
+    d.step(300)
+    assert d.diag()["mass"] == pytest.approx(m1, rel=1e-13)
+    assert d.diag()["error_flags"] == 0
+
+
+def test_mass_conserved_closed_box_with_heater_sites_gravity(coex):
+    """Coupled EOS temperature, wetting sites and buoyancy in a closed box: no mass
+    enters or leaves through bounce-back walls."""
+    nx, ny, W_ = 40, 30, 5
+    Tc, Ts = coex["Tc"], coex["Ts"]
+    rho0 = wl.tanh_film(ny, nx, coex["rho_l"], coex["rho_v"], 18.0)
+    T0 = wl.layered_T(ny, nx, W_, Ts + 0.1 * Tc, Ts)
+    Gw = nucleation_Gw(nx, 0.3, [(10.0, 10.0, 0.0), (28.0, 10.0, -0.6)])
+    p = Params(nx=nx, ny=ny, wall_rows=W_, top_bc="wall", T_bottom=Ts + 0.1 * Tc, T_top=Ts,
+               g_y=-3e-5, Gw=Gw, rho_l=coex["rho_l"], rho_v=coex["rho_v"])
+    d = Domain(p, rho0, T0).step(1)
+    m1 = d.diag()["mass"]
+    d.step(200)
+    assert d.diag()["mass"] == pytest.approx(m1, rel=1e-13)
+
+
+def _conduction_case(coex, two_d: bool):
+    nx, ny, W_ = 6, 40, 4
+    rho0 = wl.tanh_slab(ny, nx, coex["rho_l"], coex["rho_v"], 12.0, 28.0)
+    if two_d:
+        rho0 = rho0 * (1.0 + 0.3 * np.sin(2 * np.pi * np.arange(nx) / nx))[None, :]
+    T0 = np.full((ny, nx), 0.5)
+    p = Params(nx=nx, ny=ny, wall_rows=W_, top_bc="wall", T_bottom=1.0, T_top=0.0,
+               rho_l=coex["rho_l"], rho_v=coex["rho_v"])
+    return p, rho0, T0
+
+
+@pytest.mark.parametrize("two_d", [False, True])
+def test_energy_balance_conduction_only(coex, two_d):
+    """With u = 0 and frozen rho the FV face fluxes telescope: the change of
+    sum(rho cv T) equals the heat in through the bottom minus the heat out at the top."""
+    p, rho0, T0 = _conduction_case(coex, two_d)
+    d = Domain(p, rho0, T0, conduction_only=True).step(1)
+    E1 = d.diag()["energy"]
+    net = 0.0
+    for _ in range(300):
+        d.step(1)
+        g = d.diag()
+        net += p.nx * (g["q_bottom"] - g["q_top"])
+    assert d.diag()["energy"] - E1 == pytest.approx(net, rel=1e-11, abs=1e-11 * abs(E1))
+    assert abs(net) > 1e-3 * abs(E1) * 1e-3
+
+
+def test_series_resistance_steady_state_is_exact(coex, paper):
+    """Steady 1D conduction through cells of conductivity lambda_j: each pair of
+    half cells is a series resistance 1/(2 lambda_j) + 1/(2 lambda_j+1), so the flux
+    is q = dT / sum(resistances) and T drops by q times each resistance.  That
+    state must be a fixed point of the energy update with equal fluxes at both
+    Dirichlet faces (the paper's < 1e-10 relative flux difference, Section 3.2)."""
+    p, rho0, _ = _conduction_case(coex, False)
+    pr = p.resolved()
+    ny = p.ny
+    y = np.arange(ny)
+    solid = (y < p.wall_rows) | (y == ny - 1)
+    lam = np.where(solid, pr.lambda_w, rho0[:, 0] * pr.cv * pr.k)
+    res = 0.5 / lam[:-1] + 0.5 / lam[1:]
+    q = (p.T_bottom - p.T_top) / res.sum()
+    Ty = p.T_bottom - q * np.concatenate([[0.0], np.cumsum(res)])
+    T0 = np.repeat(Ty[:, None], p.nx, axis=1)
+    d = Domain(p, rho0, T0, conduction_only=True).step(5)
+    np.testing.assert_allclose(d.T, T0, rtol=0, atol=1e-13)
+    g = d.diag()
+    assert g["q_bottom"] == pytest.approx(q, rel=1e-11)
+    assert 2 * abs(g["q_bottom"] - g["q_top"]) / (g["q_bottom"] + g["q_top"]) < paper["fv_relative_flux_difference_max"]["value"]
+
+
+@pytest.mark.slow
+def test_flat_interface_reaches_maxwell_densities(coex):
+    """Thermodynamic consistency (Sections 2.1, 3.1): the bulk densities of the
+    relaxed flat interface must be the equal-area densities within 2%."""
+    p, rho0, T0 = _flat(coex)
+    d = Domain(p, rho0, T0).step(2000)
+    rho = d.rho[:, 0]
+    assert rho[100] == pytest.approx(coex["rho_l"], rel=0.02)
+    assert rho[10] == pytest.approx(coex["rho_v"], rel=0.02)
+    assert rho[190] == pytest.approx(coex["rho_v"], rel=0.02)
+
+
+def _sessile_angle(coex, Gw, nx=60, ny=30, R0=12.0, steps=2500):
+    Ts = coex["Ts"]
+    rho0 = wl.droplet(ny, nx, coex["rho_l"], coex["rho_v"], nx / 2, 1.0, R0)
+    p = Params(nx=nx, ny=ny, wall_rows=1, top_bc="wall", T_bottom=Ts, T_top=Ts, eos_T_fixed=True,
+               Gw=Gw, rho_l=coex["rho_l"], rho_v=coex["rho_v"])
+    d = Domain(p, rho0, np.full((ny, nx), Ts)).step(steps)
+    mid = 0.5 * (coex["rho_l"] + coex["rho_v"])
+    base = int((d.rho[1] > mid).sum())
+    height = int(np.nonzero(d.rho[:, nx // 2] > mid)[0].max())
+    # spherical cap through the base chord and the apex
+    a = 0.5 * base
+    R = (a * a + height * height) / (2.0 * height)
+    return np.degrees(np.arccos((R - height) / R)) if base > 0 else 180.0
+
+
+@pytest.mark.slow
+def test_contact_angle_near_paper_value_and_ordered(coex, paper):
+    """Section 4.2: G_w = 0.3 gives about 35 degrees; the nucleation-site minima
+    (smaller G_w) must be less wetting."""
+    th_03 = _sessile_angle(coex, 0.3)
+    th_m03 = _sessile_angle(coex, -0.3)
+    lo, hi = paper["contact_angle_Gw_0.3_deg"]["range"]
+    assert lo < th_03 < hi
+    assert th_m03 > th_03 + 20.0
+
+
+@pytest.mark.slow
+def test_laplace_law(coex):
+    """Static droplets: the pressure jump p_EOS(inside) - p_EOS(outside) grows
+    linearly with 1/R through the origin."""
+    Ts = coex["Ts"]
+    nx, ny = 48, 50
+    inv_r, dp = [], []
+    for R0 in (8.0, 11.0, 14.0):
+        rho0 = wl.droplet(ny, nx, coex["rho_l"], coex["rho_v"], nx / 2, ny / 2, R0)
+        p = Params(nx=nx, ny=ny, wall_rows=1, top_bc="wall", T_bottom=Ts, T_top=Ts, eos_T_fixed=True,
+                   Gw=0.0, rho_l=coex["rho_l"], rho_v=coex["rho_v"])
+        d = Domain(p, rho0, np.full((ny, nx), Ts)).step(2500)
+        r_in, r_out = d.rho[ny // 2, nx // 2], d.rho[3, 0]
+        area = np.sum(d.rho[d.fluid] - r_out) / (r_in - r_out)
+        inv_r.append(1.0 / np.sqrt(area / np.pi))
+        dp.append(eos.pressure(r_in, Ts, p.eos) - eos.pressure(r_out, Ts, p.eos))
+    x, yv = np.array(inv_r), np.array(dp)
+    A = np.vstack([x, np.ones_like(x)]).T
+    (slope, icpt), res, _, _ = np.linalg.lstsq(A, yv, rcond=None)
+    r2 = 1.0 - res[0] / np.sum((yv - yv.mean()) ** 2)
+    assert slope > 0 and r2 > 0.99
+    assert abs(icpt) < 0.1 * slope * x.min()
+
+
+def test_nucleation_site_table():
+    """Fig. 6b: G_w drops linearly from 0.3 to the site minimum over a width of 10;
+    the minima are set per site (0, -0.3, -0.6 in the paper)."""
+    g = nucleation_Gw(100, 0.3, [(20.0, 10.0, 0.0), (50.0, 10.0, -0.3), (80.0, 10.0, -0.6)])
+    assert g[20] == 0.0 and g[50] == -0.3 and g[80] == -0.6
+    for c, gmin in ((20, 0.0), (50, -0.3), (80, -0.6)):
+        assert g[c - 5] == pytest.approx(0.3) and g[c + 5] == pytest.approx(0.3)
+        np.testing.assert_allclose(np.diff(g[c - 5:c + 1], 2), 0.0, atol=1e-15)
+        np.testing.assert_allclose(g[c - 5:c + 6], g[c - 5:c + 6][::-1], atol=1e-15)
+    outside = np.ones(100, bool)
+    for c in (20, 50, 80):
+        outside[c - 5:c + 6] = False
+    assert np.all(g[outside] == 0.3)
+    # periodic wrap of a site at the edge
+    g2 = nucleation_Gw(40, 0.3, [(1.0, 10.0, 0.0)])
+    assert g2[39] == pytest.approx(g2[3])
+
+
+@pytest.mark.parametrize("top", ["const_rho", "convective"])
+def test_open_top_keeps_uniform_vapour_at_rest(coex, top):
+    nx, ny = 8, 12
+    Ts = coex["Ts"]
+    p = Params(nx=nx, ny=ny, wall_rows=2, top_bc=top, T_bottom=Ts, Gw=0.0, eos_T_fixed=False,
+               rho_l=coex["rho_l"], rho_v=coex["rho_v"])
+    d = Domain(p, np.full((ny, nx), coex["rho_v"]), np.full((ny, nx), Ts)).step(50)
+    np.testing.assert_allclose(d.rho[d.fluid], coex["rho_v"], rtol=1e-13)
+    assert np.abs(d.uy).max() < 1e-14 and np.abs(d.ux).max() < 1e-14
+
+
+def _manufactured_error(coex, n):
+    """Max |K_discrete - K_exact| / max|K_exact| on interior nodes for smooth fields
+    of wavelength n (lattice spacing 1)."""
+    sp = pytest.importorskip("sympy")
+    X, Y = sp.symbols("x y")
+    kx = 2 * sp.pi / n
+    ky = 2 * sp.pi / n
+    p = Params(nx=n, ny=n + 2, wall_rows=1, top_bc="wall", rho_l=coex["rho_l"], rho_v=coex["rho_v"])
+    pr = p.resolved()
+    rho_e = 3 + sp.Rational(1, 2) * sp.sin(kx * X) * sp.cos(ky * Y)
+    ux_e = sp.Rational(1, 100) * sp.cos(kx * X) * sp.sin(ky * Y)
+    uy_e = sp.Rational(1, 50) * sp.sin(kx * X + sp.Rational(3, 10)) * sp.cos(ky * Y)
+    T_e = sp.Rational(1, 10) + sp.Rational(1, 100) * sp.sin(kx * X) * sp.sin(ky * Y + sp.Rational(1, 2))
+    a, b, R, kap, Tc = pr.eos.a, pr.eos.b, pr.eos.R, pr.eos.kappa, pr.eos.Tc
+    # Eq. (28) written out symbolically; (dp/dT)_rho by symbolic differentiation
+    Tt = sp.Symbol("Tt", positive=True)
+    p_sym = rho_e * R * Tt / (1 - b * rho_e) - a * (1 + kap * (1 - sp.sqrt(Tt / Tc))) ** 2 * rho_e ** 2 / (
+        1 + 2 * b * rho_e - b ** 2 * rho_e ** 2)
+    dpdT = sp.diff(p_sym, Tt).subs(Tt, T_e)
+    lam_e = rho_e * pr.cv * pr.k
+    div_flux = sp.diff(lam_e * sp.diff(T_e, X), X) + sp.diff(lam_e * sp.diff(T_e, Y), Y)
+    divu = sp.diff(ux_e, X) + sp.diff(uy_e, Y)
+    K_e = (-(ux_e * sp.diff(T_e, X) + uy_e * sp.diff(T_e, Y)) + div_flux / (rho_e * pr.cv)
+           - T_e / (rho_e * pr.cv) * dpdT * divu)
+    f = {k: sp.lambdify((X, Y), v, "numpy") for k, v in
+         dict(rho=rho_e, ux=ux_e, uy=uy_e, T=T_e, K=K_e).items()}
+    ny = n + 2
+    yy, xx = np.meshgrid(np.arange(ny, dtype=float), np.arange(n, dtype=float), indexing="ij")
+    d = Domain(p, f["rho"](xx, yy), f["T"](xx, yy), conduction_only=True)
+    c = d.energy_coefficients(f["rho"](xx, yy), f["ux"](xx, yy) * d.fluid, f["uy"](xx, yy) * d.fluid)
+    K = d.energy_rhs(f["T"](xx, yy), c)
+    inner = slice(3, ny - 3)
+    Kx = f["K"](xx, yy)
+    return np.abs(K[inner] - Kx[inner]).max() / np.abs(Kx[inner]).max()
+
+
+def test_energy_rhs_converges_to_eq17(coex):
+    """Manufactured smooth rho, u, T: the discrete K of Eq. (17) must approach the
+    symbolic right-hand side at second order (each halving of the wavenumber cuts
+    the error about four times); a dropped or mis-signed term stays O(1)."""
+    e1 = _manufactured_error(coex, 32)
+    e2 = _manufactured_error(coex, 64)
+    assert e2 < 0.02
+    assert 3.0 < e1 / e2 < 5.0
