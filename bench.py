@@ -1,0 +1,388 @@
+"""Benchmark of the GB300 hybrid thermal LB phase-change step.
+
+Workload: the batched boiling-curve sweep of 32 independent square domains
+(sides drawn from {256, 320, 384, 448, 512}, superheats 0.02-0.30 Tc, 3-9
+nucleation sites, 25-row conjugate heater, convective top, gravity 3e-5), all
+advanced by one fused-step launch plus one FP64 reduction launch per step.
+A step is one coupled update of every cell of every domain.  The metric is
+coupled MLUPS over all lattice nodes (fluid and solid).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With torchrun (N > 1) every rank runs its own replica of the sweep (the
+domains are independent: no collective on the data path); the value is the
+cells of all ranks divided by the slowest rank's time.  The reference arm
+times the FP64 oracle on the host cores on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled MLUPS (hybrid thermal LB step, batched boiling-curve sweep)"
+UNIT = "MLUPS"
+WORKLOAD = ("boiling-curve sweep: 32 square domains, sides {256..512} seeded, superheat 0.02-0.30 Tc, "
+            "3-9 nucleation sites, 25-row heater, convective top, g = 3e-5; one fused step launch + one "
+            "FP64 reduction launch per step")
+BYTES_FLUID = 80  # f read 36 + f write 36 + T read 4 + T write 4
+BYTES_SOLID = 8   # T read + write (no populations in solid rows)
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1812_10375_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "k_step_batch_sweep32.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("- ") and ":" in line:
+                k, v = line[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_sweep"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_cpu_rate(seconds: float, domain_index: int = 0) -> dict:
+    """Time the FP64 oracle single-threaded on one sweep domain for about `seconds`
+    (run in a child process with the BLAS/OpenMP pools at one thread)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = f"""
+import sys, time, json
+sys.path.insert(0, {ROOT!r}); sys.path.insert(0, {os.path.join(ROOT, 'tests')!r})
+from helpers import coexistence, oracle_domain
+from paper_1812_10375_gb300 import workloads as wl
+coex = coexistence()
+case = wl.sweep()[{domain_index}]
+d = oracle_domain(case, coex)
+d.step(1)
+t0 = time.perf_counter(); n = 0
+while True:
+    d.step(1); n += 1
+    el = time.perf_counter() - t0
+    if el > {seconds} and n >= 2:
+        break
+print(json.dumps(dict(cells=case.nx * case.ny, steps=n, seconds=el, nx=case.nx, ny=case.ny)))
+"""
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=seconds * 4 + 600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    r["mlups"] = r["cells"] * r["steps"] / r["seconds"] / 1e6
+    return r
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    # each "step" is one oracle step of one sweep domain (cycling), on the host cores
+    import numpy as np  # noqa: F401
+    env_threads = 1
+    per_step_s = []
+    cells = []
+    sample_desc = []
+    total_budget = 150.0
+    budget_per = max(2.0, total_budget / max(1, args.steps + args.warmup))
+    for k in range(args.warmup + args.steps):
+        r = oracle_cpu_rate(seconds=budget_per, domain_index=k % 32)
+        if k >= args.warmup:
+            per_step_s.append(r["seconds"] / r["steps"])
+            cells.append(r["cells"])
+            sample_desc.append(f"{r['nx']}x{r['ny']}:{r['steps']} steps")
+    value = sum(cells) / sum(per_step_s) / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(per_step_s) / len(per_step_s),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " (reference: FP64 oracle, one domain per step, bounded sample)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": env_threads, "kind": "oracle",
+                         "sample": "; ".join(sample_desc)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def build_sweep(hlb, wl, params_for, coex_lib):
+    import torch
+    cases = wl.sweep()
+    plist, fields, n_fluid, n_solid = [], [], 0, 0
+    for c in cases:
+        p, Tc = params_for(c)
+        plist.append(p)
+        rho0, T0 = wl.initial_fields(c, p.rho_l, p.rho_v, Tc)
+        fields.append((rho0.astype("float32"), T0.astype("float32")))
+        n_solid += c.wall_rows * c.nx
+        n_fluid += (c.ny - c.wall_rows) * c.nx
+    return cases, plist, fields, n_fluid, n_solid
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1812_10375_gb300 import hlb, workloads as wl
+    from paper_1812_10375_gb300.config import params_for
+
+    cases, plist, fields, n_fluid, n_solid = build_sweep(hlb, wl, params_for, None)
+    cells = n_fluid + n_solid
+    bytes_per_step = BYTES_FLUID * n_fluid + BYTES_SOLID * n_solid
+
+    batch = hlb.Batch(plist)
+    stream = batch.stream
+    dev_fields = []
+    for i, (r, T) in enumerate(fields):
+        rt = torch.from_numpy(r).cuda()
+        Tt = torch.from_numpy(T).cuda()
+        batch.set_fields(i, rt, Tt)
+        batch.set_nucleation_sites(i, cases[i].sites)
+        dev_fields.append((rt, Tt))
+    torch.cuda.synchronize()
+
+    # warm-up
+    n_ev = args.steps
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+    ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+    with torch.cuda.stream(stream):
+        for e in ev_b + ev_a:
+            e.record(stream)  # creates the underlying cudaEvent_t
+    for _ in range(args.warmup):
+        batch.step_profiled(None, None)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, step kernel bracketed by events on the batch stream
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    start.record(stream)
+    for k in range(args.steps):
+        batch.step_profiled(ev_b[k], ev_a[k])
+    end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    elapsed_ms = start.elapsed_time(end)
+    kern_ms = [ev_b[k].elapsed_time(ev_a[k]) for k in range(args.steps)]
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = world * cells / (ms_per_step * 1e-3) / 1e6
+    kern_avg_ms = sum(kern_ms) / len(kern_ms)
+    diag0 = batch.diag(0, check_flags=False)
+
+    # end to end through the public API with host buffers
+    e2e = run_e2e(args, hlb, plist, fields, cases, cells, dist)
+
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
+    achieved = bytes_per_step / (kern_avg_ms * 1e-3) / 1e9
+    traffic = read_traffic()
+
+    line = None
+    if rank == 0:
+        cpu = oracle_cpu_rate(seconds=12.0, domain_index=0)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "domains": len(cases), "cells_per_step": cells,
+                       "fluid_cells": n_fluid, "solid_cells": n_solid,
+                       "l2": "inputs larger than L2 (state %.0f MB per buffer set)" % (
+                           (36 + 4) * cells / 1e6),
+                       "timing": "CUDA events on the batch stream; step kernel bracketed per step"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_step_batch", "bytes_per_launch": bytes_per_step,
+                         "kernel_ms": kern_avg_ms, "peak_source": peak_src},
+            "cpu_baseline": {"value": cpu["mlups"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"FP64 oracle, sweep domain 0 ({cpu['nx']}x{cpu['ny']}), "
+                                       f"{cpu['steps']} steps in {cpu['seconds']:.1f} s, one thread"},
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+            "diag_domain0": {"step": diag0.step, "q_bottom": diag0.q_bottom, "error_flags": diag0.error_flags},
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, hlb, plist, fields, cases, cells, dist):
+    """Same metric through the public API: initial fields uploaded from pinned host
+    memory, K steps, then the flux histories and the final rho/T read back to host."""
+    import torch
+    pinned = [(torch.from_numpy(r).pin_memory(), torch.from_numpy(T).pin_memory()) for r, T in fields]
+    outs = [(torch.empty(r.shape, dtype=torch.float32).pin_memory(),
+             torch.empty(T.shape, dtype=torch.float32).pin_memory()) for r, T in fields]
+    b = hlb.Batch(plist)
+    dev = [(torch.empty(r.shape, dtype=torch.float32, device="cuda"),
+            torch.empty(r.shape, dtype=torch.float32, device="cuda")) for r, _ in fields]
+    for i, c in enumerate(cases):
+        b.set_nucleation_sites(i, c.sites)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    with torch.cuda.stream(b.stream):
+        for i, ((rh, Th), (rd, Td)) in enumerate(zip(pinned, dev)):
+            rd.copy_(rh, non_blocking=True)
+            Td.copy_(Th, non_blocking=True)
+            h2d += rh.numel() * 4 + Th.numel() * 4
+    for i, (rd, Td) in enumerate(dev):
+        b.set_fields(i, rd, Td)
+    b.step(args.steps)
+    hist = [b.flux_history(i) for i in range(len(cases))]
+    d2h += sum(h.nbytes for h in hist)
+    for i, (ro, To) in enumerate(outs):
+        rd, Td = dev[i]
+        b.read_into(i, rho=rd, T=Td)
+        with torch.cuda.stream(b.stream):
+            ro.copy_(rd, non_blocking=True)
+            To.copy_(Td, non_blocking=True)
+        d2h += ro.numel() * 4 + To.numel() * 4
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([el], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    b.close()
+    return {"value": world * cells * args.steps / el / 1e6, "unit": UNIT,
+            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+            "seconds": el}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

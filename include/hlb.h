@@ -1,0 +1,213 @@
+/*
+ * hlb.h - C ABI of the GB300 (sm_103a) hybrid thermal lattice Boltzmann
+ * phase-change step of Hu & Liu, "Study of boiling heat transfer on the wall
+ * with an improved hybrid lattice Boltzmann model" (arXiv 1812.10375).
+ *
+ * One step of a domain is: D2Q9 MRT pseudo-potential collide-and-stream
+ * (Section 2.1, Eqs. 1-10), Peng-Robinson EOS (Section 3.1, Eq. 28), the energy
+ * equation (Eq. 17) advanced by RK4 (Eq. 18) with N sub-steps (Eq. 27) and
+ * finite-volume diffusion with harmonic face conductivities (Eqs. 22-26),
+ * halfway bounce-back walls, a conjugate heater and open tops (Sections 3.3,
+ * 4.2), and the wettability nucleation sites of Section 4.2 (Fig. 6b).
+ *
+ * Conventions shared by every entry point:
+ *  - Lattice arrays are row-major [y][x] with x fastest, nx*ny elements, FP32.
+ *    Row 0 is the bottom (heater) row; x is periodic.
+ *  - Pointers named d_* are CUDA device pointers; h_* are host pointers.
+ *  - The caller owns every buffer and the stream.  The library never allocates
+ *    device memory: it works inside the workspace the caller passes to
+ *    hlb_init / hlb_batch_init, which must stay valid until hlb_destroy.
+ *  - Host pointers are read or written only during the call.
+ *  - Every call returns an hlb_status and never throws or aborts.  Kernels are
+ *    launched asynchronously on the handle's stream; hlb_diag and
+ *    hlb_batch_flux_history synchronise that stream.
+ *  - Device-side problems set a sticky error word (bit 0: non-finite value,
+ *    bit 1: psi^2 < 0 outside the EOS range, bit 2: batch barrier timeout).
+ *    hlb_diag reports it; once it is set, hlb_step returns HLB_ESTATE.
+ *  - A handle is not thread-safe: use it from one host thread at a time.
+ *  - `stream` arguments are cudaStream_t values passed as void* (NULL = the
+ *    legacy default stream).
+ */
+#ifndef HLB_H
+#define HLB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HLB_OK = 0,
+  HLB_EINVAL = -1,     /* bad argument or parameter set                  */
+  HLB_ECUDA = -2,      /* a CUDA runtime call failed                      */
+  HLB_EUNSTABLE = -3,  /* the device error word reports non-finite / psi  */
+  HLB_ETIMEOUT = -4,   /* a bounded device wait gave up                   */
+  HLB_ESTATE = -5      /* call not valid in the handle's current state    */
+} hlb_status;
+
+/* Top boundary kinds (Sections 3.2, 3.3, 4.2). */
+enum { HLB_TOP_WALL = 0, HLB_TOP_CONST_RHO = 1, HLB_TOP_CONVECTIVE = 2 };
+
+/* Distribution storage (precision pattern): deviations f_i - w_i rho_ref (default)
+ * or the plain populations. */
+enum { HLB_STORE_DEVIATION = 0, HLB_STORE_PLAIN = 1 };
+
+/*
+ * Model and geometry parameters, all in lattice units (dx = dt = 1, Section 3.1).
+ * hlb_params_default fills the paper's values; fields marked "<= 0: default"
+ * are derived at init from the coexistence densities.
+ */
+typedef struct {
+  int nx, ny;          /* lattice size; nx >= 4, ny >= 6                            */
+  int wall_rows;       /* rows y < wall_rows are solid (>= 1); row 0 has Dirichlet T */
+  int top_bc;          /* HLB_TOP_*; HLB_TOP_WALL makes row ny-1 a solid Dirichlet row */
+  int eos_T_fixed;     /* 1: the EOS uses Ts everywhere (Section 3.2)               */
+  int n_sub;           /* N of Eq. (27), >= 1                                        */
+  int storage;         /* HLB_STORE_DEVIATION | HLB_STORE_PLAIN                      */
+  double a, b, R, omega, Ts_over_Tc;   /* Eq. (28): 3/49, 2/21, 1, 0.344, 0.86        */
+  double G, sigma, sigma_coef;         /* Eqs. (6)-(8): -1, 0.107, 12                 */
+  double s_rho, s_e, s_zeta, s_j, s_q; /* Eq. (3) rates not printed: 1, .8, .8, 1, 1.1 */
+  double tau_l, tau_v;                 /* tau_nu at rho_l / rho_v: 0.8, 1.0 (Sec. 3.1) */
+  double cv, k;                        /* Section 3.1: 6, 0.1 (lambda = rho cv k)     */
+  double rho_w, cv_w, lambda_w;        /* solid; <= 0: default 3 rho_l, cv, 3 rho_l cv k */
+  double g_y;                          /* gravity (Eq. 9), e.g. -3e-5                 */
+  double Gw0;                          /* wall wetting strength (Eq. 10), 0.3         */
+  double T_bottom, T_top;              /* Dirichlet T of row 0 / of row ny-1 (top wall) */
+  double rho_l, rho_v;                 /* coexistence densities at Ts; <= 0: Maxwell  */
+} hlb_params;
+
+/* One nucleation site: a linear drop of G_w from Gw0 to gw_min at x_center over
+ * width/2 on either side (Section 4.2, Fig. 6b). */
+typedef struct { double x_center, width, gw_min; } hlb_site;
+
+/* FP64 diagnostics of the last completed step (Eq. 9 rho_ave; Section 4.3 wall
+ * heat flux).  q_* are RK-weighted conductive fluxes through a face over the
+ * step, averaged over x (heat per unit time and unit length). */
+typedef struct {
+  long long step;         /* completed steps                                    */
+  double mass;            /* sum of rho over fluid nodes                        */
+  double energy;          /* sum of rho cv T over all nodes (T after the step)  */
+  double q_bottom;        /* into row 1 through the bottom Dirichlet face       */
+  double q_top;           /* out of row ny-2 through the top Dirichlet face     */
+  double q_interface;     /* through the solid -> fluid face                     */
+  double rho_ave;         /* mean fluid density, used by the next step (Eq. 9)  */
+  double u_top;           /* mean u_y of row ny-2                                */
+  double q_bottom_timeavg;/* running mean of q_bottom since the last reset      */
+  int error_flags;        /* sticky device error word                            */
+} hlb_diag_record;
+
+typedef struct hlb_domain hlb_domain;
+typedef struct hlb_batch hlb_batch;
+
+/* Fill the paper's parameter values (Section 3.1) for an nx x ny lattice. */
+void hlb_params_default(hlb_params* p, int nx, int ny);
+
+/* Host-only: Tc (from a, b, R), and the Maxwell equal-area coexistence
+ * densities at T = Ts_over_Tc * Tc (Section 3.1), plus the latent heat of
+ * Eq. (14) per unit mass.  Any out pointer may be NULL.  HLB_EINVAL when the
+ * temperature has no two-phase region. */
+hlb_status hlb_eos_coexistence(const hlb_params* p, double* Tc, double* rho_l, double* rho_v,
+                               double* h_fg);
+
+/* Device bytes one domain needs (fields double-buffered, per-block FP64 partials,
+ * site table, flux history).  0 on invalid parameters. */
+size_t hlb_workspace_bytes(const hlb_params* p);
+
+/* Create a domain inside the caller's device workspace (>= hlb_workspace_bytes
+ * bytes, 256-byte aligned).  Parameters are copied; unset derived values are
+ * filled.  The initial wetting table is the constant Gw0; fields are unset
+ * until hlb_set_fields.  *out is owned by the library until hlb_destroy. */
+hlb_status hlb_init(hlb_domain** out, const hlb_params* p, void* d_workspace, size_t workspace_bytes,
+                    void* stream);
+
+/* Initial state: rho and T (device, nx*ny FP32 each).  Populations become the
+ * rest equilibrium w_i rho; Dirichlet rows take their wall value; rho_ave is the
+ * fluid mean of rho; the step counter and time averages reset. */
+hlb_status hlb_set_fields(hlb_domain* d, const float* d_rho, const float* d_T);
+
+/* Dirichlet wall temperature of row 0 (the heater bottom, Section 4.2; the
+ * hot wall of Section 3.2).  Takes effect from the next step. */
+hlb_status hlb_set_wall(hlb_domain* d, double T_bottom);
+
+/* Wetting table from nucleation sites (Section 4.2): G_w(x) = Gw0 except inside
+ * a site, where it drops linearly to gw_min at the centre (periodic in x; the
+ * lowest value wins where sites overlap).  n = 0 restores the uniform wall. */
+hlb_status hlb_set_nucleation_sites(hlb_domain* d, int n, const hlb_site* h_sites);
+
+/* Advance nsteps coupled steps (asynchronous on the handle's stream).
+ * Repeated calls reuse a captured CUDA graph of the step pair (fused step
+ * kernel + FP64 reduction kernel). */
+hlb_status hlb_step(hlb_domain* d, int nsteps);
+
+/* Fields after the last step: rho^n, u^n (the step's pre-collision moments,
+ * Eq. 5) and T^{n+1}.  Any pointer may be NULL.  Before the first step: the
+ * initial rho, u = 0 and the initial T. */
+hlb_status hlb_read(hlb_domain* d, float* d_rho, float* d_ux, float* d_uy, float* d_T);
+
+/* Copy the FP64 diagnostics of the last step to the host (synchronises the
+ * stream).  Returns HLB_EUNSTABLE if the device error word is set (the record is
+ * still written). */
+hlb_status hlb_diag(hlb_domain* d, hlb_diag_record* h_out);
+
+/* Restart the running time average of q_bottom at the next step. */
+hlb_status hlb_reset_timeavg(hlb_domain* d);
+
+/* Release the handle (the workspace stays the caller's). */
+hlb_status hlb_destroy(hlb_domain* d);
+
+/* ------------------------------------------------------------------ batch
+ * A boiling-curve sweep: n independent domains (each with its own size,
+ * superheat and sites) advanced together.  One step is a single launch of the
+ * fused step kernel whose blocks cover the tiles of every active domain
+ * (a descriptor table maps block -> domain, tile), followed by one FP64
+ * reduction launch with one CTA per domain.  Repeated hlb_batch_step calls
+ * replay a captured CUDA graph of 16 such steps. */
+
+/* Device bytes for n domains with parameters p[0..n-1]; 0 if any is invalid. */
+size_t hlb_batch_workspace_bytes(int n, const hlb_params* p);
+
+/* Create a batch inside the caller's workspace (256-byte aligned).  Each
+ * domain behaves as one made by hlb_init. */
+hlb_status hlb_batch_init(hlb_batch** out, int n, const hlb_params* p, void* d_workspace, size_t workspace_bytes,
+                          void* stream);
+
+/* Per-domain set-up, as hlb_set_fields / hlb_set_wall / hlb_set_nucleation_sites
+ * for domain i (0 <= i < n).  hlb_batch_set_fields may be called at any time: it
+ * restarts domain i from the given fields (step counter, time average and flux
+ * history reset) and makes it active again, so a slot can be reused for a new
+ * sweep point. */
+hlb_status hlb_batch_set_fields(hlb_batch* b, int i, const float* d_rho, const float* d_T);
+hlb_status hlb_batch_set_wall(hlb_batch* b, int i, double T_bottom);
+hlb_status hlb_batch_set_nucleation_sites(hlb_batch* b, int i, int n, const hlb_site* h_sites);
+
+/* Advance every active domain by nsteps (asynchronous). */
+hlb_status hlb_batch_step(hlb_batch* b, int nsteps);
+
+/* One batch step launched directly (no graph), with the caller's CUDA events
+ * (cudaEvent_t as void*, either may be NULL) recorded on the batch stream
+ * immediately before and after the fused step kernel, so that its duration
+ * can be measured apart from the reduction. */
+hlb_status hlb_batch_step_profiled(hlb_batch* b, void* ev_before, void* ev_after);
+
+/* As hlb_read / hlb_diag for domain i. */
+hlb_status hlb_batch_read(hlb_batch* b, int i, float* d_rho, float* d_ux, float* d_uy, float* d_T);
+hlb_status hlb_batch_diag(hlb_batch* b, int i, hlb_diag_record* h_out);
+
+/* Copy domain i's per-step wall heat flux q_bottom (FP64, one entry per step
+ * since hlb_batch_set_fields, at most 65536 entries) into h_out[0..max_len);
+ * *h_len receives the number written.  Synchronises the stream. */
+hlb_status hlb_batch_flux_history(hlb_batch* b, int i, double* h_out, int max_len, int* h_len);
+
+/* Stop domain i: later batch steps skip it and its state stays readable
+ * (early stop of a sweep point). */
+hlb_status hlb_batch_stop(hlb_batch* b, int i);
+
+hlb_status hlb_batch_destroy(hlb_batch* b);
+
+const char* hlb_strerror(hlb_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HLB_H */

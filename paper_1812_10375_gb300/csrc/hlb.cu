@@ -1,0 +1,829 @@
+// Host side of the C ABI declared in include/hlb.h: parameter handling, the
+// Peng-Robinson coexistence solver, workspace layout, kernel launches and
+// CUDA-graph replay of the step.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "hlb.h"
+#include "hlb_kernels.cuh"
+
+using namespace hlb;
+
+namespace {
+
+constexpr int TILE_X = 32;
+constexpr int TILE_Y = 16;
+constexpr int GRAPH_STEPS = 16;     // steps per captured graph (even: buffers return to parity 0)
+constexpr int HIST_CAP = 1 << 16;   // wall-flux history entries kept per domain
+constexpr int INIT_BLOCKS = 304;
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// ------------------------------------------------------------ Peng-Robinson
+// Eq. (28) written in the specific volume v = 1/rho:
+//   p = R T / (v - b) - a phi(T) / (v^2 + 2 b v - b^2)
+// whose antiderivative in v is
+//   Pi(v) = R T ln(v - b) - a phi / (2 sqrt2 b) ln((v + b - sqrt2 b) / (v + b + sqrt2 b)).
+struct PRHost {
+  double a, b, R, kappa, Tc;
+  double alpha(double T) const { return 1.0 + kappa * (1.0 - sqrt(fmax(T, 0.0) / Tc)); }
+  double phi(double T) const { double al = alpha(T); return al * al; }
+  double p_rho(double rho, double T) const {
+    return rho * R * T / (1.0 - b * rho) - a * phi(T) * rho * rho / (1.0 + 2.0 * b * rho - b * b * rho * rho);
+  }
+  double dp_drho(double rho, double T) const {
+    const double den = 1.0 + 2.0 * b * rho - b * b * rho * rho;
+    const double dden = 2.0 * b - 2.0 * b * b * rho;
+    return R * T / ((1.0 - b * rho) * (1.0 - b * rho)) - a * phi(T) * (2.0 * rho * den - rho * rho * dden) / (den * den);
+  }
+  double log_term(double v) const {
+    const double s2b = sqrt(2.0) * b;
+    return log((v + b - s2b) / (v + b + s2b));
+  }
+  double Pi(double v, double T) const { return R * T * log(v - b) - a * phi(T) / (2.0 * sqrt(2.0) * b) * log_term(v); }
+  // antiderivative of T (dp/dT)_v:  T dphi/dT = -kappa alpha(T) sqrt(T/Tc)
+  double Hi(double v, double T) const {
+    const double Tdphi = -kappa * alpha(T) * sqrt(fmax(T, 0.0) / Tc);
+    return R * T * log(v - b) - a * Tdphi / (2.0 * sqrt(2.0) * b) * log_term(v);
+  }
+};
+
+template <typename F>
+double bisect(F f, double lo, double hi) {
+  double flo = f(lo);
+  for (int it = 0; it < 400; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    const double fm = f(mid);
+    if ((fm < 0) == (flo < 0)) {
+      lo = mid;
+      flo = fm;
+    } else {
+      hi = mid;
+    }
+  }
+  return 0.5 * (lo + hi);
+}
+
+// Maxwell equal-area construction: p(v_l) = p(v_v) = p_s and
+// Pi(v_v) - Pi(v_l) = p_s (v_v - v_l).
+bool coexistence(const PRHost& e, double T, double* rl, double* rv, double* hfg) {
+  const double rmax = 0.999999 / e.b;
+  // spinodals: sign changes of dp/drho on a grid, refined by bisection
+  const int NG = 20000;
+  double sp[2];
+  int ns = 0;
+  double prev = e.dp_drho(1e-6, T);
+  for (int k = 1; k <= NG && ns < 2; ++k) {
+    const double r = 1e-6 + (rmax - 1e-6) * k / NG;
+    const double d = e.dp_drho(r, T);
+    if ((d < 0) != (prev < 0)) {
+      const double r0 = 1e-6 + (rmax - 1e-6) * (k - 1) / NG;
+      sp[ns++] = bisect([&](double x) { return e.dp_drho(x, T); }, r0, r);
+    }
+    prev = d;
+  }
+  if (ns < 2) return false;
+  const double s1 = sp[0], s2 = sp[1];
+  const double p_hi = e.p_rho(s1, T);
+  const double p_lo = fmax(e.p_rho(s2, T), 1e-14);
+  auto roots = [&](double ps, double* v_v, double* v_l) {
+    const double r_min = 0.5 * ps / (e.R * T);
+    const double rvap = bisect([&](double r) { return e.p_rho(r, T) - ps; }, r_min, s1);
+    const double rliq = bisect([&](double r) { return e.p_rho(r, T) - ps; }, s2, rmax);
+    *v_v = 1.0 / rvap;
+    *v_l = 1.0 / rliq;
+  };
+  auto area = [&](double ps) {
+    double vv, vl;
+    roots(ps, &vv, &vl);
+    return (e.Pi(vv, T) - e.Pi(vl, T)) - ps * (vv - vl);
+  };
+  const double eps = 1e-12 * (p_hi - p_lo);
+  const double ps = bisect(area, p_lo + eps, p_hi - eps);
+  double vv, vl;
+  roots(ps, &vv, &vl);
+  *rl = 1.0 / vl;
+  *rv = 1.0 / vv;
+  if (hfg) *hfg = e.Hi(vv, T) - e.Hi(vl, T);  // Eq. (14)
+  return true;
+}
+
+PRHost pr_of(const hlb_params* p) {
+  PRHost e;
+  e.a = p->a;
+  e.b = p->b;
+  e.R = p->R;
+  e.kappa = 0.37464 + 1.54226 * p->omega - 0.26992 * p->omega * p->omega;
+  e.Tc = (p->a / p->b) * (0.0778 / 0.45724) / p->R;
+  return e;
+}
+
+bool params_valid(const hlb_params* p) {
+  if (!p) return false;
+  if (p->nx < 4 || p->ny < 6 || p->wall_rows < 1) return false;
+  if (p->top_bc < HLB_TOP_WALL || p->top_bc > HLB_TOP_CONVECTIVE) return false;
+  const int fluid_rows = p->ny - p->wall_rows - (p->top_bc == HLB_TOP_WALL ? 1 : 0);
+  if (fluid_rows < 3) return false;
+  if (p->n_sub != 1) return false;  // the fused kernel's halo is sized for N = 1
+  if (p->storage != HLB_STORE_DEVIATION && p->storage != HLB_STORE_PLAIN) return false;
+  if (!(p->a > 0 && p->b > 0 && p->R > 0 && p->Ts_over_Tc > 0)) return false;
+  if (!(p->s_e > 0 && p->s_e < 2 && p->s_zeta > 0 && p->s_zeta < 2 && p->s_j > 0 && p->s_j < 2 &&
+        p->s_q > 0 && p->s_q < 2))
+    return false;
+  if (!(p->tau_l > 0.5 && p->tau_v > 0.5 && p->cv > 0 && p->k > 0)) return false;
+  if ((long long)p->nx * p->ny > (1LL << 31)) return false;
+  return true;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ handle
+struct hlb_domain {
+  hlb_params p;
+  double Tc = 0, rho_ref = 0;
+  cudaStream_t stream = nullptr;
+  float* f[2] = {nullptr, nullptr};
+  float* T[2] = {nullptr, nullptr};
+  float* Gw = nullptr;
+  float* ftop[2] = {nullptr, nullptr};
+  double* partials = nullptr;
+  DevState* state = nullptr;
+  double* hist = nullptr;
+  int parity = 0;
+  long long steps = 0;
+  bool fields_set = false;
+  int host_flags = 0;
+  long long n_fluid = 0;
+  dim3 grid;
+  size_t smem = 0;
+  StepArgs base;
+  cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+struct Layout {
+  size_t f, T, Gw, ftop, partials, state, hist, total;
+};
+
+Layout layout_of(const hlb_params* p) {
+  Layout L;
+  const size_t N = (size_t)p->nx * p->ny;
+  const size_t nblk = (size_t)((p->nx + TILE_X - 1) / TILE_X) * ((p->ny + TILE_Y - 1) / TILE_Y);
+  size_t o = 0;
+  L.f = o;        o += align_up(2 * 9 * N * sizeof(float));
+  L.T = o;        o += align_up(2 * N * sizeof(float));
+  L.Gw = o;       o += align_up((size_t)p->nx * sizeof(float));
+  L.ftop = o;     o += align_up(2 * 3 * (size_t)p->nx * sizeof(float));
+  L.partials = o; o += align_up((nblk > INIT_BLOCKS ? nblk : INIT_BLOCKS) * NPART * sizeof(double));
+  L.state = o;    o += align_up(sizeof(DevState));
+  L.hist = o;     o += align_up(HIST_CAP * sizeof(double));
+  L.total = o;
+  return L;
+}
+
+size_t smem_bytes() {
+  const int FN = (TILE_X + 2 * HALO) * (TILE_Y + 2 * HALO);
+  return (size_t)(10 * FN + TILE_X * TILE_Y) * sizeof(float);
+}
+
+StepArgs args_for(hlb_domain* d, int par) {
+  StepArgs a = d->base;
+  a.f_in = d->f[par];
+  a.f_out = d->f[par ^ 1];
+  a.T_in = d->T[par];
+  a.T_out = d->T[par ^ 1];
+  a.ftop_in = d->ftop[par];
+  a.ftop_out = d->ftop[par ^ 1];
+  return a;
+}
+
+hlb_status launch_step(hlb_domain* d) {
+  const StepArgs a = args_for(d, d->parity);
+  k_step<TILE_X, TILE_Y><<<d->grid, NTHREADS, d->smem, d->stream>>>(a);
+  k_reduce<<<1, 256, 0, d->stream>>>(d->partials, (int)(d->grid.x * d->grid.y), d->state, 1.0 / (double)d->n_fluid,
+                                     1.0 / (double)d->p.nx, d->hist, HIST_CAP);
+  if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
+  d->parity ^= 1;
+  d->steps += 1;
+  return HLB_OK;
+}
+
+void drop_graph(hlb_domain* d) {
+  if (d->graph) {
+    cudaGraphExecDestroy(d->graph);
+    d->graph = nullptr;
+  }
+}
+
+hlb_status build_graph(hlb_domain* d) {
+  // capture GRAPH_STEPS steps starting from parity 0
+  if (d->parity != 0) return HLB_ESTATE;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HLB_ECUDA;
+  const long long s0 = d->steps;
+  hlb_status st = HLB_OK;
+  for (int k = 0; k < GRAPH_STEPS && st == HLB_OK; ++k) st = launch_step(d);
+  const cudaError_t e = cudaStreamEndCapture(d->stream, &g);
+  d->steps = s0;
+  d->parity = 0;
+  if (st != HLB_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return HLB_ECUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&d->graph, g, 0);
+  cudaGraphDestroy(g);
+  return ei == cudaSuccess ? HLB_OK : HLB_ECUDA;
+}
+
+}  // namespace
+
+namespace {
+// Initial state into buffer set `par` (the other T buffer gets the same T, so
+// that hlb_read after an odd number of steps finds T^n).
+hlb_status set_fields_at(hlb_domain* d, const float* d_rho, const float* d_T, int par) {
+  if (!d || !d_rho || !d_T) return HLB_EINVAL;
+  StepArgs a = args_for(d, par);
+  k_init<<<INIT_BLOCKS, 256, 0, d->stream>>>(a, d_rho, d_T, d->f[par], d->T[par], d->ftop[0], d->ftop[1]);
+  k_init<<<INIT_BLOCKS, 256, 0, d->stream>>>(a, d_rho, d_T, d->f[par ^ 1], d->T[par ^ 1], nullptr, nullptr);
+  k_init_state<<<1, 32, 0, d->stream>>>(d->partials, INIT_BLOCKS, d->state, 1.0 / (double)d->n_fluid);
+  if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
+  d->parity = par;
+  d->steps = 0;
+  d->fields_set = true;
+  d->host_flags = 0;
+  return HLB_OK;
+}
+
+hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_t stream) {
+  const Layout L = layout_of(p);
+  d->p = *p;
+  const PRHost e = pr_of(p);
+  d->Tc = e.Tc;
+  if (!(d->p.rho_l > 0 && d->p.rho_v > 0)) {
+    double rl, rv;
+    if (!coexistence(e, p->Ts_over_Tc * e.Tc, &rl, &rv, nullptr)) return HLB_EINVAL;
+    d->p.rho_l = rl;
+    d->p.rho_v = rv;
+  }
+  hlb_params& q = d->p;
+  if (!(q.rho_w > 0)) q.rho_w = 3.0 * q.rho_l;
+  if (!(q.cv_w > 0)) q.cv_w = q.cv;
+  if (!(q.lambda_w > 0)) q.lambda_w = 3.0 * q.rho_l * q.cv * q.k;
+  d->rho_ref = q.storage == HLB_STORE_DEVIATION ? q.rho_v : 0.0;
+  d->stream = stream;
+
+  const size_t N = (size_t)q.nx * q.ny;
+  d->f[0] = (float*)(ws + L.f);
+  d->f[1] = d->f[0] + 9 * N;
+  d->T[0] = (float*)(ws + L.T);
+  d->T[1] = d->T[0] + N;
+  d->Gw = (float*)(ws + L.Gw);
+  d->ftop[0] = (float*)(ws + L.ftop);
+  d->ftop[1] = d->ftop[0] + 3 * q.nx;
+  d->partials = (double*)(ws + L.partials);
+  d->state = (DevState*)(ws + L.state);
+  d->hist = (double*)(ws + L.hist);
+  const int fluid_rows = q.ny - q.wall_rows - (q.top_bc == HLB_TOP_WALL ? 1 : 0);
+  d->n_fluid = (long long)fluid_rows * q.nx;
+  d->grid = dim3((q.nx + TILE_X - 1) / TILE_X, (q.ny + TILE_Y - 1) / TILE_Y);
+  d->smem = smem_bytes();
+
+  StepArgs& a = d->base;
+  memset(&a, 0, sizeof(a));
+  a.nx = q.nx;
+  a.ny = q.ny;
+  a.W = q.wall_rows;
+  a.top_bc = q.top_bc;
+  a.eos_T_fixed = q.eos_T_fixed;
+  a.plane = (long long)N;
+  a.R = (float)q.R;
+  a.a = (float)q.a;
+  a.b = (float)q.b;
+  a.kappa = (float)e.kappa;
+  a.invTc = (float)(1.0 / e.Tc);
+  a.Ts = (float)(q.Ts_over_Tc * e.Tc);
+  a.G = (float)q.G;
+  a.g_y = (float)q.g_y;
+  const double tau_e = 1.0 / q.s_e, tau_z = 1.0 / q.s_zeta;
+  a.sig_e = (float)((1.0 - 0.5 * q.s_e) * q.sigma_coef * q.sigma / (tau_e - 0.5));
+  a.sig_z = (float)((1.0 - 0.5 * q.s_zeta) * q.sigma_coef * q.sigma / (tau_z - 0.5));
+  a.s_e = (float)q.s_e;
+  a.s_z = (float)q.s_zeta;
+  a.s_j = (float)q.s_j;
+  a.s_q = (float)q.s_q;
+  a.tau_l = (float)q.tau_l;
+  a.tau_v = (float)q.tau_v;
+  a.rho_v = (float)q.rho_v;
+  a.dtau_drho = (float)((q.tau_l - q.tau_v) / (q.rho_l - q.rho_v));
+  a.rho_ref = (float)d->rho_ref;
+  a.cvk = (float)(q.cv * q.k);
+  a.cv = (float)q.cv;
+  a.rcv_w = (float)(q.rho_w * q.cv_w);
+  a.inv_rcv_w = (float)(1.0 / (q.rho_w * q.cv_w));
+  a.lambda_w = (float)q.lambda_w;
+  a.dt = (float)(1.0 / q.n_sub);
+  a.T_bottom = (float)q.T_bottom;
+  a.T_top = (float)q.T_top;
+  a.Gw = d->Gw;
+  a.partials = d->partials;
+  a.state = d->state;
+
+  if (cudaFuncSetAttribute(k_step<TILE_X, TILE_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_step_batch<TILE_X, TILE_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)d->smem) != cudaSuccess)
+    return HLB_ECUDA;
+  // uniform wetting table
+  return hlb_set_nucleation_sites(d, 0, nullptr);
+}
+
+}  // namespace
+
+
+// ------------------------------------------------------------------- batch
+struct hlb_batch {
+  int n = 0;
+  std::vector<hlb_domain> dom;
+  cudaStream_t stream = nullptr;
+  StepArgs* d_desc = nullptr;  // [2][n]: descriptors for batch parity 0 and 1
+  ReduceArgs* d_ra = nullptr;  // [n]
+  int* d_tile_off = nullptr;   // [n + 1]
+  int* d_active = nullptr;     // [n]
+  std::vector<int> tile_off;
+  std::vector<int> active;
+  int total_tiles = 0;
+  int parity = 0;
+  long long steps = 0;
+  size_t smem = 0;
+  cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+struct BatchLayout {
+  std::vector<size_t> dom_off;
+  size_t desc, ra, tile_off, active, total;
+};
+
+BatchLayout batch_layout(int n, const hlb_params* p) {
+  BatchLayout L;
+  size_t o = 0;
+  for (int i = 0; i < n; ++i) {
+    L.dom_off.push_back(o);
+    o += layout_of(p + i).total;
+  }
+  L.desc = o;     o += align_up(2 * (size_t)n * sizeof(StepArgs));
+  L.ra = o;       o += align_up((size_t)n * sizeof(ReduceArgs));
+  L.tile_off = o; o += align_up((size_t)(n + 1) * sizeof(int));
+  L.active = o;   o += align_up((size_t)n * sizeof(int));
+  L.total = o;
+  return L;
+}
+
+hlb_status upload_tables(hlb_batch* b) {
+  std::vector<StepArgs> desc(2 * (size_t)b->n);
+  std::vector<ReduceArgs> ra(b->n);
+  for (int i = 0; i < b->n; ++i) {
+    hlb_domain* d = &b->dom[i];
+    desc[i] = args_for(d, 0);
+    desc[b->n + i] = args_for(d, 1);
+    ra[i].partials = d->partials;
+    ra[i].state = d->state;
+    ra[i].hist = d->hist;
+    ra[i].nblk = (int)(d->grid.x * d->grid.y);
+    ra[i].inv_nfluid = 1.0 / (double)d->n_fluid;
+    ra[i].inv_nx = 1.0 / (double)d->p.nx;
+  }
+  if (cudaMemcpyAsync(b->d_desc, desc.data(), desc.size() * sizeof(StepArgs), cudaMemcpyHostToDevice, b->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(b->d_ra, ra.data(), ra.size() * sizeof(ReduceArgs), cudaMemcpyHostToDevice, b->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(b->d_tile_off, b->tile_off.data(), b->tile_off.size() * sizeof(int), cudaMemcpyHostToDevice,
+                      b->stream) != cudaSuccess ||
+      cudaMemcpyAsync(b->d_active, b->active.data(), b->active.size() * sizeof(int), cudaMemcpyHostToDevice,
+                      b->stream) != cudaSuccess)
+    return HLB_ECUDA;
+  return cudaStreamSynchronize(b->stream) == cudaSuccess ? HLB_OK : HLB_ECUDA;
+}
+
+hlb_status batch_launch(hlb_batch* b, cudaEvent_t before, cudaEvent_t after) {
+  if (before && cudaEventRecord(before, b->stream) != cudaSuccess) return HLB_ECUDA;
+  k_step_batch<TILE_X, TILE_Y><<<b->total_tiles, NTHREADS, b->smem, b->stream>>>(
+      b->d_desc + (size_t)b->parity * b->n, b->d_tile_off, b->d_active, b->n);
+  if (after && cudaEventRecord(after, b->stream) != cudaSuccess) return HLB_ECUDA;
+  k_reduce_batch<<<b->n, 256, 0, b->stream>>>(b->d_ra, b->d_active, HIST_CAP);
+  if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
+  b->parity ^= 1;
+  b->steps += 1;
+  for (int i = 0; i < b->n; ++i) {
+    if (b->active[i]) {
+      b->dom[i].parity ^= 1;
+      b->dom[i].steps += 1;
+    }
+  }
+  return HLB_OK;
+}
+
+void batch_drop_graph(hlb_batch* b) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+}
+
+hlb_status batch_build_graph(hlb_batch* b) {
+  if (b->parity != 0) return HLB_ESTATE;
+  std::vector<int> par(b->n);
+  std::vector<long long> stp(b->n);
+  for (int i = 0; i < b->n; ++i) {
+    par[i] = b->dom[i].parity;
+    stp[i] = b->dom[i].steps;
+  }
+  const long long s0 = b->steps;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HLB_ECUDA;
+  hlb_status st = HLB_OK;
+  for (int k = 0; k < GRAPH_STEPS && st == HLB_OK; ++k) st = batch_launch(b, nullptr, nullptr);
+  const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  b->steps = s0;
+  b->parity = 0;
+  for (int i = 0; i < b->n; ++i) {
+    b->dom[i].parity = par[i];
+    b->dom[i].steps = stp[i];
+  }
+  if (st != HLB_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return HLB_ECUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  return ei == cudaSuccess ? HLB_OK : HLB_ECUDA;
+}
+
+bool batch_ok(const hlb_batch* b, int i) { return b && i >= 0 && i < b->n; }
+
+}  // namespace
+
+extern "C" {
+
+void hlb_params_default(hlb_params* p, int nx, int ny) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->nx = nx;
+  p->ny = ny;
+  p->wall_rows = 1;
+  p->top_bc = HLB_TOP_WALL;
+  p->eos_T_fixed = 0;
+  p->n_sub = 1;
+  p->storage = HLB_STORE_DEVIATION;
+  p->a = 3.0 / 49.0;
+  p->b = 2.0 / 21.0;
+  p->R = 1.0;
+  p->omega = 0.344;
+  p->Ts_over_Tc = 0.86;
+  p->G = -1.0;
+  p->sigma = 0.107;
+  p->sigma_coef = 12.0;
+  p->s_rho = 1.0;
+  p->s_e = 0.8;
+  p->s_zeta = 0.8;
+  p->s_j = 1.0;
+  p->s_q = 1.1;
+  p->tau_l = 0.8;
+  p->tau_v = 1.0;
+  p->cv = 6.0;
+  p->k = 0.1;
+  p->rho_w = 0.0;
+  p->cv_w = 0.0;
+  p->lambda_w = 0.0;
+  p->g_y = 0.0;
+  p->Gw0 = 0.3;
+  p->T_bottom = 0.0;
+  p->T_top = 0.0;
+  p->rho_l = 0.0;
+  p->rho_v = 0.0;
+}
+
+hlb_status hlb_eos_coexistence(const hlb_params* p, double* Tc, double* rho_l, double* rho_v, double* h_fg) {
+  if (!p || !(p->a > 0 && p->b > 0 && p->R > 0 && p->Ts_over_Tc > 0)) return HLB_EINVAL;
+  const PRHost e = pr_of(p);
+  if (Tc) *Tc = e.Tc;
+  double rl, rv, h;
+  if (!coexistence(e, p->Ts_over_Tc * e.Tc, &rl, &rv, &h)) return HLB_EINVAL;
+  if (rho_l) *rho_l = rl;
+  if (rho_v) *rho_v = rv;
+  if (h_fg) *h_fg = h;
+  return HLB_OK;
+}
+
+size_t hlb_workspace_bytes(const hlb_params* p) {
+  if (!params_valid(p)) return 0;
+  return layout_of(p).total;
+}
+
+hlb_status hlb_init(hlb_domain** out, const hlb_params* p, void* d_workspace, size_t workspace_bytes, void* stream) {
+  if (!out || !params_valid(p) || !d_workspace) return HLB_EINVAL;
+  *out = nullptr;
+  if (((uintptr_t)d_workspace & 255) != 0) return HLB_EINVAL;
+  if (workspace_bytes < layout_of(p).total) return HLB_EINVAL;
+  hlb_domain* d = new (std::nothrow) hlb_domain();
+  if (!d) return HLB_EINVAL;
+  const hlb_status st = init_domain(d, p, (char*)d_workspace, (cudaStream_t)stream);
+  if (st != HLB_OK) {
+    delete d;
+    return st;
+  }
+  *out = d;
+  return HLB_OK;
+}
+
+hlb_status hlb_set_fields(hlb_domain* d, const float* d_rho, const float* d_T) {
+  return set_fields_at(d, d_rho, d_T, 0);
+}
+
+hlb_status hlb_set_wall(hlb_domain* d, double T_bottom) {
+  if (!d || !isfinite(T_bottom)) return HLB_EINVAL;
+  d->p.T_bottom = T_bottom;
+  d->base.T_bottom = (float)T_bottom;
+  drop_graph(d);
+  return HLB_OK;
+}
+
+hlb_status hlb_set_nucleation_sites(hlb_domain* d, int n, const hlb_site* sites) {
+  if (!d || n < 0 || (n > 0 && !sites)) return HLB_EINVAL;
+  const int nx = d->p.nx;
+  float* tab = (float*)malloc(sizeof(float) * nx);
+  if (!tab) return HLB_EINVAL;
+  for (int x = 0; x < nx; ++x) {
+    double g = d->p.Gw0;
+    for (int s = 0; s < n; ++s) {
+      const double half = 0.5 * sites[s].width;
+      if (!(half > 0)) {
+        free(tab);
+        return HLB_EINVAL;
+      }
+      double dist = fabs((double)x - sites[s].x_center);
+      dist = fmin(dist, (double)nx - dist);
+      if (dist <= half) {
+        const double v = sites[s].gw_min + (d->p.Gw0 - sites[s].gw_min) * dist / half;
+        g = fmin(g, v);
+      }
+    }
+    tab[x] = (float)g;
+  }
+  const cudaError_t e = cudaMemcpyAsync(d->Gw, tab, sizeof(float) * nx, cudaMemcpyHostToDevice, d->stream);
+  const cudaError_t e2 = cudaStreamSynchronize(d->stream);
+  free(tab);
+  return (e == cudaSuccess && e2 == cudaSuccess) ? HLB_OK : HLB_ECUDA;
+}
+
+hlb_status hlb_step(hlb_domain* d, int nsteps) {
+  if (!d || nsteps < 0) return HLB_EINVAL;
+  if (!d->fields_set) return HLB_ESTATE;
+  if (d->host_flags) return HLB_ESTATE;
+  hlb_status st = HLB_OK;
+  const bool graphs = d->stream != nullptr;
+  while (nsteps > 0 && st == HLB_OK) {
+    if (graphs && d->parity == 0 && nsteps >= GRAPH_STEPS) {
+      if (!d->graph) {
+        st = build_graph(d);
+        if (st != HLB_OK) return st;
+      }
+      if (cudaGraphLaunch(d->graph, d->stream) != cudaSuccess) return HLB_ECUDA;
+      d->steps += GRAPH_STEPS;
+      nsteps -= GRAPH_STEPS;
+    } else {
+      st = launch_step(d);
+      nsteps -= 1;
+    }
+  }
+  return st;
+}
+
+hlb_status hlb_read(hlb_domain* d, float* d_rho, float* d_ux, float* d_uy, float* d_T) {
+  if (!d) return HLB_EINVAL;
+  if (!d->fields_set) return HLB_ESTATE;
+  const int cur = d->parity;
+  StepArgs a = args_for(d, cur ^ 1);
+  // args_for(cur ^ 1) has f_out = f[cur] (the current populations)
+  if (d_rho || d_ux || d_uy) {
+    const float* Tn = d->T[cur ^ 1];  // T^n: the temperature the last step started from
+    k_read<<<INIT_BLOCKS, 256, 0, d->stream>>>(a, d->steps == 0 ? d->T[cur] : Tn, d->steps == 0 ? 1 : 0, d_rho,
+                                                d_ux, d_uy);
+  }
+  if (d_T) {
+    if (cudaMemcpyAsync(d_T, d->T[cur], sizeof(float) * (size_t)d->p.nx * d->p.ny, cudaMemcpyDeviceToDevice,
+                        d->stream) != cudaSuccess)
+      return HLB_ECUDA;
+  }
+  return cudaGetLastError() == cudaSuccess ? HLB_OK : HLB_ECUDA;
+}
+
+hlb_status hlb_diag(hlb_domain* d, hlb_diag_record* out) {
+  if (!d || !out) return HLB_EINVAL;
+  DevState s;
+  if (cudaMemcpyAsync(&s, d->state, sizeof(s), cudaMemcpyDeviceToHost, d->stream) != cudaSuccess) return HLB_ECUDA;
+  if (cudaStreamSynchronize(d->stream) != cudaSuccess) return HLB_ECUDA;
+  out->step = s.step;
+  out->mass = s.mass;
+  out->energy = s.energy;
+  out->q_bottom = s.q_bottom;
+  out->q_top = s.q_top;
+  out->q_interface = s.q_interface;
+  out->rho_ave = s.rho_ave;
+  out->u_top = s.u_top;
+  out->q_bottom_timeavg = s.q_count > 0 ? s.q_sum / (double)s.q_count : 0.0;
+  out->error_flags = s.error_flags;
+  d->host_flags = s.error_flags;
+  if (s.error_flags & ERR_TIMEOUT) return HLB_ETIMEOUT;
+  return s.error_flags ? HLB_EUNSTABLE : HLB_OK;
+}
+
+hlb_status hlb_reset_timeavg(hlb_domain* d) {
+  if (!d) return HLB_EINVAL;
+  const size_t off_sum = offsetof(DevState, q_sum);
+  if (cudaMemsetAsync((char*)d->state + off_sum, 0, sizeof(double) + sizeof(long long), d->stream) != cudaSuccess)
+    return HLB_ECUDA;
+  return HLB_OK;
+}
+
+hlb_status hlb_destroy(hlb_domain* d) {
+  if (!d) return HLB_EINVAL;
+  drop_graph(d);
+  delete d;
+  return HLB_OK;
+}
+
+// ------------------------------------------------------------- batch API
+size_t hlb_batch_workspace_bytes(int n, const hlb_params* p) {
+  if (n < 1 || !p) return 0;
+  for (int i = 0; i < n; ++i)
+    if (!params_valid(p + i)) return 0;
+  return batch_layout(n, p).total;
+}
+
+hlb_status hlb_batch_init(hlb_batch** out, int n, const hlb_params* p, void* d_workspace, size_t workspace_bytes,
+                          void* stream) {
+  if (!out || n < 1 || !p || !d_workspace) return HLB_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (!params_valid(p + i)) return HLB_EINVAL;
+  if (((uintptr_t)d_workspace & 255) != 0) return HLB_EINVAL;
+  const BatchLayout L = batch_layout(n, p);
+  if (workspace_bytes < L.total) return HLB_EINVAL;
+  hlb_batch* b = new (std::nothrow) hlb_batch();
+  if (!b) return HLB_EINVAL;
+  b->n = n;
+  b->stream = (cudaStream_t)stream;
+  b->dom.resize(n);
+  char* ws = (char*)d_workspace;
+  b->tile_off.assign(n + 1, 0);
+  b->active.assign(n, 1);
+  for (int i = 0; i < n; ++i) {
+    const hlb_status st = init_domain(&b->dom[i], p + i, ws + L.dom_off[i], b->stream);
+    if (st != HLB_OK) {
+      delete b;
+      return st;
+    }
+    b->tile_off[i + 1] = b->tile_off[i] + (int)(b->dom[i].grid.x * b->dom[i].grid.y);
+  }
+  b->total_tiles = b->tile_off[n];
+  b->smem = smem_bytes();
+  b->d_desc = (StepArgs*)(ws + L.desc);
+  b->d_ra = (ReduceArgs*)(ws + L.ra);
+  b->d_tile_off = (int*)(ws + L.tile_off);
+  b->d_active = (int*)(ws + L.active);
+  const hlb_status st = upload_tables(b);
+  if (st != HLB_OK) {
+    delete b;
+    return st;
+  }
+  *out = b;
+  return HLB_OK;
+}
+
+hlb_status hlb_batch_set_fields(hlb_batch* b, int i, const float* d_rho, const float* d_T) {
+  if (!batch_ok(b, i)) return HLB_EINVAL;
+  // the domain joins the batch at the batch's current buffer parity
+  const hlb_status st = set_fields_at(&b->dom[i], d_rho, d_T, b->parity);
+  if (st != HLB_OK) return st;
+  if (!b->active[i]) {
+    b->active[i] = 1;
+    const int one = 1;
+    if (cudaMemcpyAsync(b->d_active + i, &one, sizeof(int), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+      return HLB_ECUDA;
+  }
+  return HLB_OK;
+}
+
+hlb_status hlb_batch_set_wall(hlb_batch* b, int i, double T_bottom) {
+  if (!batch_ok(b, i)) return HLB_EINVAL;
+  const hlb_status st = hlb_set_wall(&b->dom[i], T_bottom);
+  if (st != HLB_OK) return st;
+  batch_drop_graph(b);
+  return upload_tables(b);
+}
+
+hlb_status hlb_batch_set_nucleation_sites(hlb_batch* b, int i, int n, const hlb_site* h_sites) {
+  if (!batch_ok(b, i)) return HLB_EINVAL;
+  return hlb_set_nucleation_sites(&b->dom[i], n, h_sites);
+}
+
+hlb_status hlb_batch_step(hlb_batch* b, int nsteps) {
+  if (!b || nsteps < 0) return HLB_EINVAL;
+  for (int i = 0; i < b->n; ++i)
+    if (!b->dom[i].fields_set) return HLB_ESTATE;
+  hlb_status st = HLB_OK;
+  const bool graphs = b->stream != nullptr;
+  while (nsteps > 0 && st == HLB_OK) {
+    if (graphs && b->parity == 0 && nsteps >= GRAPH_STEPS) {
+      if (!b->graph) {
+        st = batch_build_graph(b);
+        if (st != HLB_OK) return st;
+      }
+      if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return HLB_ECUDA;
+      b->steps += GRAPH_STEPS;
+      for (int i = 0; i < b->n; ++i) {
+        if (b->active[i]) b->dom[i].steps += GRAPH_STEPS;  // parity unchanged (even count)
+      }
+      nsteps -= GRAPH_STEPS;
+    } else {
+      st = batch_launch(b, nullptr, nullptr);
+      nsteps -= 1;
+    }
+  }
+  return st;
+}
+
+hlb_status hlb_batch_step_profiled(hlb_batch* b, void* ev_before, void* ev_after) {
+  if (!b) return HLB_EINVAL;
+  for (int i = 0; i < b->n; ++i)
+    if (!b->dom[i].fields_set) return HLB_ESTATE;
+  return batch_launch(b, (cudaEvent_t)ev_before, (cudaEvent_t)ev_after);
+}
+
+hlb_status hlb_batch_read(hlb_batch* b, int i, float* d_rho, float* d_ux, float* d_uy, float* d_T) {
+  if (!batch_ok(b, i)) return HLB_EINVAL;
+  return hlb_read(&b->dom[i], d_rho, d_ux, d_uy, d_T);
+}
+
+hlb_status hlb_batch_diag(hlb_batch* b, int i, hlb_diag_record* h_out) {
+  if (!batch_ok(b, i)) return HLB_EINVAL;
+  return hlb_diag(&b->dom[i], h_out);
+}
+
+hlb_status hlb_batch_flux_history(hlb_batch* b, int i, double* h_out, int max_len, int* h_len) {
+  if (!batch_ok(b, i) || !h_out || max_len < 0 || !h_len) return HLB_EINVAL;
+  hlb_domain* d = &b->dom[i];
+  DevState s;
+  if (cudaMemcpyAsync(&s, d->state, sizeof(s), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return HLB_ECUDA;
+  const int len = s.hist_len < max_len ? s.hist_len : max_len;
+  if (len > 0 && (cudaMemcpyAsync(h_out, d->hist, sizeof(double) * len, cudaMemcpyDeviceToHost, b->stream) !=
+                      cudaSuccess ||
+                  cudaStreamSynchronize(b->stream) != cudaSuccess))
+    return HLB_ECUDA;
+  *h_len = len;
+  return HLB_OK;
+}
+
+hlb_status hlb_batch_stop(hlb_batch* b, int i) {
+  if (!batch_ok(b, i)) return HLB_EINVAL;
+  if (!b->active[i]) return HLB_OK;
+  b->active[i] = 0;
+  const int zero = 0;
+  if (cudaMemcpyAsync(b->d_active + i, &zero, sizeof(int), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return HLB_ECUDA;
+  return HLB_OK;
+}
+
+hlb_status hlb_batch_destroy(hlb_batch* b) {
+  if (!b) return HLB_EINVAL;
+  batch_drop_graph(b);
+  for (auto& d : b->dom) drop_graph(&d);
+  delete b;
+  return HLB_OK;
+}
+
+const char* hlb_strerror(hlb_status s) {
+  switch (s) {
+    case HLB_OK: return "ok";
+    case HLB_EINVAL: return "invalid argument";
+    case HLB_ECUDA: return "CUDA runtime error";
+    case HLB_EUNSTABLE: return "device error word set (non-finite value or psi^2 < 0)";
+    case HLB_ETIMEOUT: return "bounded device wait timed out";
+    case HLB_ESTATE: return "call not valid in the current state";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

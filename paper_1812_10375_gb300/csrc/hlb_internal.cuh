@@ -1,0 +1,57 @@
+// Internal device-side descriptors of the hybrid thermal LB step (arXiv 1812.10375).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hlb {
+
+// Per-block FP64 partial sums written by the step kernel.
+enum { P_MASS = 0, P_ENERGY, P_QB, P_QT, P_QI, P_UTOP, NPART };
+
+// Error word bits (match the header's description).
+enum { ERR_NONFINITE = 1, ERR_PSI_NEG = 2, ERR_TIMEOUT = 4 };
+
+// Device-resident scalars of one domain.  Written only by the reduction kernel
+// (and atomically OR-ed error bits by the step kernel).
+struct DevState {
+  double rho_ave;       // fluid-mean density of the last step (used by the next, Eq. 9)
+  double rho_ave_prev;  // the value the last step used
+  double U;             // lagged convective-outlet velocity (>= 0)
+  double Uc;            // U / (1 + U), formed in FP64 (keeps U's precision when U << 1)
+  long long step;
+  double mass, energy, q_bottom, q_top, q_interface, u_top;
+  double q_sum;
+  long long q_count;
+  int error_flags;
+  int hist_len;
+};
+
+// Everything the fused step kernel needs, passed by value.
+struct StepArgs {
+  int nx, ny, W, top_bc, eos_T_fixed;
+  long long plane;  // nx * ny
+  // Peng-Robinson (Eq. 28)
+  float R, a, b, kappa, invTc, Ts;
+  // forces (Eqs. 6, 9, 10) and forcing (Eq. 8)
+  float G, g_y;
+  float sig_e, sig_z;  // (1 - s/2) * C * sigma / (tau - 1/2) for rows e and zeta
+  // relaxation (Eq. 3)
+  float s_e, s_z, s_j, s_q;
+  float tau_l, tau_v, rho_v, dtau_drho;
+  float rho_ref;  // deviation storage reference
+  // energy (Eq. 17)
+  float cvk, cv, rcv_w, inv_rcv_w, lambda_w, dt;
+  float T_bottom, T_top;
+  // buffers
+  const float* __restrict__ f_in;
+  float* __restrict__ f_out;
+  const float* __restrict__ T_in;
+  float* __restrict__ T_out;
+  const float* __restrict__ Gw;
+  const float* __restrict__ ftop_in;
+  float* __restrict__ ftop_out;
+  double* __restrict__ partials;
+  DevState* state;
+};
+
+}  // namespace hlb

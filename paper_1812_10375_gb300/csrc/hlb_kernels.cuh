@@ -1,0 +1,709 @@
+// Device code of the hybrid thermal LB phase-change step (Hu & Liu, arXiv 1812.10375).
+//
+// One launch of k_step advances one domain by one coupled step:
+//   pull-streaming with halfway bounce-back and open-top rules (Eqs. 1-2,
+//   Sections 3.3, 4.2) -> rho (Eq. 5) -> psi from the Peng-Robinson EOS
+//   (Eqs. 7, 28) -> F = F_m + F_ads + F_b (Eqs. 6, 9, 10) -> u (Eq. 5) ->
+//   MRT collision with Li's forcing (Eqs. 2-4, 8) and the RK4 update of the
+//   energy equation (Eqs. 17-19) with finite-volume harmonic face
+//   conductivities (Eqs. 22-26).
+// The energy update of an output cell depends on u at distance 4 and hence on
+// psi at distance 5 and the populations at distance 6, so each CTA recomputes
+// a ring-6 halo of its tile in shared memory (reads of neighbouring tiles hit
+// L2) and writes only its own tile: 36 B + 36 B of populations and 4 B + 4 B
+// of temperature per cell from HBM.
+#pragma once
+#include "hlb_internal.cuh"
+
+namespace hlb {
+
+enum { TOP_WALL = 0, TOP_CONST_RHO = 1, TOP_CONVECTIVE = 2 };
+
+constexpr int HALO = 6;       // frame halo of the fused kernel
+constexpr int NTHREADS = 256; // threads per CTA of the fused kernel
+
+__device__ __forceinline__ int wrapx(int x, int nx) {
+  int r = x % nx;
+  return r < 0 ? r + nx : r;
+}
+
+__device__ __forceinline__ bool nonfinite(float v) {
+  return (__float_as_uint(v) & 0x7f800000u) == 0x7f800000u;
+}
+
+struct Geo {
+  int nx, ny, W;
+  bool top_wall, top_open;
+  __device__ __forceinline__ bool solid_row(int y) const { return y < W || (top_wall && y == ny - 1); }
+  __device__ __forceinline__ bool dirichlet_row(int y) const { return y == 0 || (top_wall && y == ny - 1); }
+};
+
+__device__ __forceinline__ Geo make_geo(const StepArgs& A) {
+  Geo g;
+  g.nx = A.nx;
+  g.ny = A.ny;
+  g.W = A.W;
+  g.top_wall = A.top_bc == TOP_WALL;
+  g.top_open = A.top_bc != TOP_WALL;
+  return g;
+}
+
+// psi^2 = 2 (rho/3 - p_EOS) with p_EOS of Eq. (28); Eq. (7) with c = 1, G = -1.
+__device__ __forceinline__ float pr_psi2(const StepArgs& A, float rho, float T) {
+  const float sTr = sqrtf(fmaxf(T, 0.f) * A.invTc);
+  const float al = 1.f + A.kappa * (1.f - sTr);
+  const float br = A.b * rho;
+  const float p = rho * A.R * T / (1.f - br) - A.a * al * al * rho * rho / (1.f + 2.f * br - br * br);
+  return 2.f * (rho * (1.f / 3.f) - p);
+}
+
+// Post-streaming populations (deviation form) of fluid node (x, y): pull from
+// x - e_i; halfway bounce-back where x - e_i is solid; populations entering an
+// open top row from above are the rest equilibrium at rho_v (constant density)
+// or the convective-outlet update with the lagged velocity U (Uc = U / (1 + U)).
+// D2Q9 order: 0 rest, 1 (+x), 2 (+y), 3 (-x), 4 (-y), 5 (+x+y), 6 (-x+y), 7 (-x-y), 8 (+x-y).
+__device__ __forceinline__ void pull(const StepArgs& A, const Geo& g, int x, int y, float Uc, float f[9]) {
+  const int nx = g.nx;
+  const int xm = x == 0 ? nx - 1 : x - 1;
+  const int xp = x == nx - 1 ? 0 : x + 1;
+  const long long P = A.plane;
+  const float* __restrict__ F = A.f_in;
+  const long long r0 = (long long)y * nx;
+  const long long rs = r0 - nx;
+  const long long rn = r0 + nx;
+  const bool bb_s = g.solid_row(y - 1);
+  const bool open_n = g.top_open && y == g.ny - 1;
+  const bool bb_n = !open_n && g.solid_row(y + 1);
+  f[0] = __ldg(F + r0 + x);
+  f[1] = __ldg(F + 1 * P + r0 + xm);
+  f[3] = __ldg(F + 3 * P + r0 + xp);
+  if (bb_s) {
+    f[2] = __ldg(F + 4 * P + r0 + x);
+    f[5] = __ldg(F + 7 * P + r0 + x);
+    f[6] = __ldg(F + 8 * P + r0 + x);
+  } else {
+    f[2] = __ldg(F + 2 * P + rs + x);
+    f[5] = __ldg(F + 5 * P + rs + xm);
+    f[6] = __ldg(F + 6 * P + rs + xp);
+  }
+  if (open_n) {
+    if (A.top_bc == TOP_CONST_RHO) {
+      const float d = A.rho_v - A.rho_ref;
+      f[4] = d * (1.f / 9.f);
+      f[7] = d * (1.f / 36.f);
+      f[8] = d * (1.f / 36.f);
+    } else {
+      // f_i(top) = [f_i^{n-1}(top) + U f_i^n(top-1)] / (1 + U), evaluated as
+      // prev + Uc (below - prev) with Uc = U / (1 + U) from FP64: in FP32, 1 + U
+      // would keep only a few digits of U ~ 1e-5.  f_i^n(top-1) is pulled from this row.
+      const float p4 = A.ftop_in[x], p7 = A.ftop_in[nx + x], p8 = A.ftop_in[2 * nx + x];
+      f[4] = p4 + Uc * (__ldg(F + 4 * P + r0 + x) - p4);
+      f[7] = p7 + Uc * (__ldg(F + 7 * P + r0 + xp) - p7);
+      f[8] = p8 + Uc * (__ldg(F + 8 * P + r0 + xm) - p8);
+    }
+  } else if (bb_n) {
+    f[4] = __ldg(F + 2 * P + r0 + x);
+    f[7] = __ldg(F + 5 * P + r0 + x);
+    f[8] = __ldg(F + 6 * P + r0 + x);
+  } else {
+    f[4] = __ldg(F + 4 * P + rn + x);
+    f[7] = __ldg(F + 7 * P + rn + xp);
+    f[8] = __ldg(F + 8 * P + rn + xm);
+  }
+}
+
+__device__ __forceinline__ float sum9(const float f[9]) {
+  return ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+}
+
+// MRT collision with Li's forcing, Eqs. (2)-(4), (8), on deviation populations
+// f~ = f - w rho_ref; moments m~ = M f~ differ from m = M f by rho_ref (1, -2, 1, 0, ...).
+// Applied as an increment f* = f + M^-1 dm with dm = -Lambda (m - m_eq) + (I - Lambda/2) S:
+// the density row of dm is 0 and the momentum rows are exactly F (because
+// j - rho u = -F/2 by Eq. 5), so no rounded 1/9 or 1/6 multiplies rho or j and
+// FP32 rounding cannot bias mass or momentum from step to step.
+// Fm2_psi2 = |F_m|^2 / psi^2.  Writes the nine post-collision values and returns their sum.
+__device__ __forceinline__ float collide_store(const StepArgs& A, const float f[9], float rho, float ux, float uy,
+                                               float Fx, float Fy, float Fm2_psi2, long long off) {
+  const float sa = (f[1] + f[2]) + (f[3] + f[4]);
+  const float sd = (f[5] + f[6]) + (f[7] + f[8]);
+  const float m0 = f[0] + sa + sd;  // rho - rho_ref
+  const float me = -4.f * f[0] - sa + 2.f * sd;
+  const float mz = 4.f * f[0] - 2.f * sa + sd;
+  const float ax = f[1] - f[3], ay = f[2] - f[4];
+  const float cx = (f[5] - f[6]) - (f[7] - f[8]);
+  const float cy = (f[5] + f[6]) - (f[7] + f[8]);
+  const float qx = -2.f * ax + cx;
+  const float qy = -2.f * ay + cy;
+  const float pxx = (f[1] + f[3]) - (f[2] + f[4]);
+  const float pxy = (f[5] + f[7]) - (f[6] + f[8]);
+
+  const float u2 = ux * ux + uy * uy;
+  const float uF = ux * Fx + uy * Fy;
+  float tau = A.tau_v + (rho - A.rho_v) * A.dtau_drho;
+  tau = fminf(fmaxf(tau, fminf(A.tau_l, A.tau_v)), fmaxf(A.tau_l, A.tau_v));
+  const float snu = 1.f / tau;
+
+  const float de = -A.s_e * (me + 2.f * m0 - 3.f * rho * u2) + (1.f - 0.5f * A.s_e) * (6.f * uF) + A.sig_e * Fm2_psi2;
+  const float dz = -A.s_z * (mz - m0 + 3.f * rho * u2) - (1.f - 0.5f * A.s_z) * (6.f * uF) - A.sig_z * Fm2_psi2;
+  const float dqx = -A.s_q * (qx + rho * ux) - (1.f - 0.5f * A.s_q) * Fx;
+  const float dqy = -A.s_q * (qy + rho * uy) - (1.f - 0.5f * A.s_q) * Fy;
+  const float dpxx = -snu * (pxx - rho * (ux * ux - uy * uy)) + (1.f - 0.5f * snu) * 2.f * (ux * Fx - uy * Fy);
+  const float dpxy = -snu * (pxy - rho * ux * uy) + (1.f - 0.5f * snu) * (ux * Fy + uy * Fx);
+
+  // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4); the density component is 0
+  const float r1 = de * (1.f / 36.f), r2 = dz * (1.f / 36.f);
+  const float r3 = Fx * (1.f / 6.f), r4 = dqx * (1.f / 12.f);
+  const float r5 = Fy * (1.f / 6.f), r6 = dqy * (1.f / 12.f);
+  const float r7 = dpxx * 0.25f, r8 = dpxy * 0.25f;
+  const float ba = -r1 - 2.f * r2;
+  const float bd = 2.f * r1 + r2;
+  const float o0 = f[0] + (4.f * (r2 - r1));
+  const float o1 = f[1] + (ba + r3 - 2.f * r4 + r7);
+  const float o2 = f[2] + (ba + r5 - 2.f * r6 - r7);
+  const float o3 = f[3] + (ba - r3 + 2.f * r4 + r7);
+  const float o4 = f[4] + (ba - r5 + 2.f * r6 - r7);
+  const float o5 = f[5] + (bd + r3 + r4 + r5 + r6 + r8);
+  const float o6 = f[6] + (bd - r3 - r4 + r5 + r6 - r8);
+  const float o7 = f[7] + (bd - r3 - r4 - r5 - r6 + r8);
+  const float o8 = f[8] + (bd + r3 + r4 - r5 - r6 - r8);
+  const long long P = A.plane;
+  float* __restrict__ out = A.f_out + off;
+  out[0] = o0;
+  out[P] = o1;
+  out[2 * P] = o2;
+  out[3 * P] = o3;
+  out[4 * P] = o4;
+  out[5 * P] = o5;
+  out[6 * P] = o6;
+  out[7 * P] = o7;
+  out[8 * P] = o8;
+  return o0 + o1 + o2 + o3 + o4 + o5 + o6 + o7 + o8;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Fused coupled step on tile (bx, by) of TX x TY cells.  Shared-memory frame
+// of (TX+12) x (TY+12) cells; ring r of the tile = frame cells within distance r
+// of the tile.  `part` is the tile's slot in the domain's partial-sum array.
+template <int TX, int TY>
+__device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, long long part, float* sm) {
+  constexpr int H = HALO, FW = TX + 2 * H, FH = TY + 2 * H, FN = FW * FH;
+  float* const sT0 = sm;            // T^n, ring 5
+  float* const sRho = sm + FN;      // rho, ring 5      -> stage buffer Ta
+  float* const sPsi = sm + 2 * FN;  // psi, ring 5      -> east-face conductivity
+  float* const sUx = sm + 3 * FN;   // u, ring 4
+  float* const sUy = sm + 4 * FN;
+  float* const sLam = sm + 5 * FN;  // lambda, ring 4   -> stage buffer Tb
+  float* const sLan = sm + 6 * FN;  // north-face conductivity
+  float* const sIrcv = sm + 7 * FN; // 1/(rho cv), ring 3
+  float* const sAs = sm + 8 * FN;   // latent-heat source coefficients, ring 3
+  float* const sBs = sm + 9 * FN;
+  float* const sAcc = sm + 10 * FN; // h1 + 2 h2 + 2 h3 on the tile
+  float* const sLae = sPsi;
+  float* const sTa = sRho;
+  float* const sTb = sLam;
+  __shared__ int s_err;
+  __shared__ double s_red[NTHREADS / 32][NPART];
+
+  const Geo g = make_geo(A);
+  const int x0 = bx * TX, y0 = by * TY;
+  const int tid = threadIdx.x;
+  const int jlo = max(0, H - y0);
+  const int jhi = min(FH - 1, A.ny - 1 - y0 + H);
+  const float Uc = (float)A.state->Uc;
+  const float rho_ave = (float)A.state->rho_ave;
+  if (tid == 0) s_err = 0;
+  __syncthreads();
+  int err = 0;
+  double a_mass = 0.0, a_E = 0.0, a_qb = 0.0, a_qt = 0.0, a_qi = 0.0, a_ut = 0.0;
+
+  // ---- pass A (ring 5): T^n, rho and psi
+  {
+    constexpr int r = 5, w = TX + 2 * r, h = TY + 2 * r;
+    for (int c = tid; c < w * h; c += NTHREADS) {
+      const int i = c % w + (H - r), j = c / w + (H - r);
+      const int gy = y0 - H + j;
+      if (gy < 0 || gy >= A.ny) continue;
+      const int gx = wrapx(x0 - H + i, A.nx);
+      const int idx = j * FW + i;
+      const float T = g.dirichlet_row(gy) ? (gy == 0 ? A.T_bottom : A.T_top)
+                                          : __ldg(A.T_in + (long long)gy * A.nx + gx);
+      sT0[idx] = T;
+      if (g.solid_row(gy)) {
+        sRho[idx] = 0.f;
+        sPsi[idx] = 0.f;
+        continue;
+      }
+      float f[9];
+      pull(A, g, gx, gy, Uc, f);
+      const float rho = A.rho_ref + sum9(f);
+      float p2 = pr_psi2(A, rho, A.eos_T_fixed ? A.Ts : T);
+      if (!(p2 >= 0.f)) {
+        err |= ERR_PSI_NEG;
+        p2 = 0.f;
+      }
+      sRho[idx] = rho;
+      sPsi[idx] = sqrtf(p2);
+    }
+  }
+  __syncthreads();
+
+  // ---- pass B (ring 4): forces, velocity, conductivity; collide the tile
+  {
+    constexpr int r = 4, w = TX + 2 * r, h = TY + 2 * r;
+    for (int c = tid; c < w * h; c += NTHREADS) {
+      const int i = c % w + (H - r), j = c / w + (H - r);
+      const int gy = y0 - H + j;
+      if (gy < 0 || gy >= A.ny) continue;
+      const int idx = j * FW + i;
+      if (g.solid_row(gy)) {
+        sUx[idx] = 0.f;
+        sUy[idx] = 0.f;
+        sLam[idx] = A.lambda_w;
+        continue;
+      }
+      const int gxu = x0 - H + i;
+      const int gx = wrapx(gxu, A.nx);
+      const float psi = sPsi[idx], rho = sRho[idx];
+      const int js = max(j - 1, jlo), jn = min(j + 1, jhi);
+      const bool sol_s = g.solid_row(y0 - H + js);
+      const bool sol_n = g.solid_row(y0 - H + jn);
+      // Eq. (6); a solid neighbour carries psi(x)
+      const float pE = sPsi[idx + 1], pW = sPsi[idx - 1];
+      const float pN = sol_n ? psi : sPsi[jn * FW + i];
+      const float pS = sol_s ? psi : sPsi[js * FW + i];
+      const float pNE = sol_n ? psi : sPsi[jn * FW + i + 1];
+      const float pNW = sol_n ? psi : sPsi[jn * FW + i - 1];
+      const float pSE = sol_s ? psi : sPsi[js * FW + i + 1];
+      const float pSW = sol_s ? psi : sPsi[js * FW + i - 1];
+      const float sx = (pE - pW) * (1.f / 3.f) + ((pNE - pNW) + (pSE - pSW)) * (1.f / 12.f);
+      const float sy = (pN - pS) * (1.f / 3.f) + ((pNE + pNW) - (pSE + pSW)) * (1.f / 12.f);
+      const float Fmx = -A.G * psi * sx;
+      const float Fmy = -A.G * psi * sy;
+      // Eq. (10) with weights omega/3: solid rows are whole rows, so only a
+      // normal component (1/9 + 2/36) (s_N - s_S) remains
+      const float Fay = __ldg(A.Gw + gx) * psi * psi * ((float)sol_n - (float)sol_s) * (1.f / 6.f);
+      const float Fx = Fmx;
+      const float Fy = Fmy + Fay + (rho - rho_ave) * A.g_y;  // Eq. (9)
+      float f[9];
+      pull(A, g, gx, gy, Uc, f);
+      const float jx = (f[1] - f[3]) + ((f[5] - f[6]) - (f[7] - f[8]));
+      const float jy = (f[2] - f[4]) + ((f[5] + f[6]) - (f[7] + f[8]));
+      const float irho = 1.f / rho;
+      const float ux = (jx + 0.5f * Fx) * irho;
+      const float uy = (jy + 0.5f * Fy) * irho;
+      sUx[idx] = ux;
+      sUy[idx] = uy;
+      sLam[idx] = rho * A.cvk;
+      const bool own = i >= H && i < H + TX && j >= H && j < H + TY && gxu < A.nx;
+      if (own) {
+        const long long off = (long long)gy * A.nx + gx;
+        const float fsum = collide_store(A, f, rho, ux, uy, Fx, Fy, A.G * A.G * (sx * sx + sy * sy), off);
+        if (nonfinite(fsum)) err |= ERR_NONFINITE;
+        a_mass += (double)rho;
+        if (gy == A.ny - 2) a_ut += (double)uy;
+        if (A.top_bc == TOP_CONVECTIVE && gy == A.ny - 1) {
+          A.ftop_out[gx] = f[4];
+          A.ftop_out[A.nx + gx] = f[7];
+          A.ftop_out[2 * A.nx + gx] = f[8];
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- pass C: face conductivities (Eq. 25) on ring 4, coefficients on ring 3
+  {
+    constexpr int r = 4, w = TX + 2 * r, h = TY + 2 * r;
+    for (int c = tid; c < w * h; c += NTHREADS) {
+      const int i = c % w + (H - r), j = c / w + (H - r);
+      const int gy = y0 - H + j;
+      if (gy < 0 || gy >= A.ny) continue;
+      const int idx = j * FW + i;
+      const float lam = sLam[idx];
+      if (i + 1 < H + TX + r) {
+        const float le = sLam[idx + 1];
+        sLae[idx] = 2.f * lam * le / (lam + le);
+      }
+      if (j + 1 < H + TY + r) {
+        const float ln = sLam[min(j + 1, jhi) * FW + i];
+        sLan[idx] = 2.f * lam * ln / (lam + ln);
+      }
+    }
+  }
+  {
+    constexpr int r = 3, w = TX + 2 * r, h = TY + 2 * r;
+    for (int c = tid; c < w * h; c += NTHREADS) {
+      const int i = c % w + (H - r), j = c / w + (H - r);
+      const int gy = y0 - H + j;
+      if (gy < 0 || gy >= A.ny) continue;
+      const int idx = j * FW + i;
+      if (g.solid_row(gy)) {
+        sIrcv[idx] = A.inv_rcv_w;
+        sAs[idx] = 0.f;
+        sBs[idx] = 0.f;
+        continue;
+      }
+      const int js = max(j - 1, jlo), jn = min(j + 1, jhi);
+      const float rho = sRho[idx];
+      const float ircv = 1.f / (rho * A.cv);
+      // div u with the isotropic gradient of Eq. (19)
+      const float dux = (sUx[idx + 1] - sUx[idx - 1]) * (1.f / 3.f) +
+                        ((sUx[jn * FW + i + 1] - sUx[js * FW + i - 1]) +
+                         (sUx[js * FW + i + 1] - sUx[jn * FW + i - 1])) * (1.f / 12.f);
+      const float duy = (sUy[jn * FW + i] - sUy[js * FW + i]) * (1.f / 3.f) +
+                        ((sUy[jn * FW + i + 1] - sUy[js * FW + i - 1]) +
+                         (sUy[jn * FW + i - 1] - sUy[js * FW + i + 1])) * (1.f / 12.f);
+      const float divu = dux + duy;
+      const float br = A.b * rho;
+      // T (dp/dT)_rho = As' T + Bs' (1 + kappa (1 - sqrt Tr)) sqrt Tr (Eq. 28)
+      const float Ar = rho * A.R / (1.f - br);
+      const float Br = A.a * rho * rho * A.kappa / (1.f + 2.f * br - br * br);
+      sIrcv[idx] = ircv;
+      sAs[idx] = Ar * ircv * divu;
+      sBs[idx] = Br * ircv * divu;
+    }
+  }
+  __syncthreads();
+
+  // ---- RK4 stages (Eq. 18): stage k on ring 4-k
+  const float dt = A.dt;
+#pragma unroll 1
+  for (int k = 1; k <= 4; ++k) {
+    const float* Tc = k == 1 ? sT0 : (k == 3 ? sTb : sTa);
+    float* Tn = k == 1 ? sTa : (k == 2 ? sTb : sTa);
+    const float cnext = k == 3 ? dt : 0.5f * dt;
+    const float wk = (k == 1 || k == 4) ? dt * (1.f / 6.f) : dt * (2.f / 6.f);
+    const int r = 4 - k, w = TX + 2 * r, h = TY + 2 * r;
+    for (int c = tid; c < w * h; c += NTHREADS) {
+      const int i = c % w + (H - r), j = c / w + (H - r);
+      const int gy = y0 - H + j;
+      if (gy < 0 || gy >= A.ny) continue;
+      const int idx = j * FW + i;
+      const int js = max(j - 1, jlo), jn = min(j + 1, jhi);
+      const float Tp = Tc[idx];
+      float hk = 0.f;
+      if (!g.dirichlet_row(gy)) {
+        const float TE = Tc[idx + 1], TW = Tc[idx - 1], TN = Tc[jn * FW + i], TS = Tc[js * FW + i];
+        // Eqs. (22)-(26): sum of face fluxes over the control volume
+        float kk = sLae[idx] * (TE - Tp) + sLae[idx - 1] * (TW - Tp) + sLan[idx] * (TN - Tp) +
+                   sLan[js * FW + i] * (TS - Tp);
+        kk *= sIrcv[idx];
+        if (!g.solid_row(gy)) {
+          const float TNE = Tc[jn * FW + i + 1], TNW = Tc[jn * FW + i - 1];
+          const float TSE = Tc[js * FW + i + 1], TSW = Tc[js * FW + i - 1];
+          const float gxT = (TE - TW) * (1.f / 3.f) + ((TNE - TSW) + (TSE - TNW)) * (1.f / 12.f);
+          const float gyT = (TN - TS) * (1.f / 3.f) + ((TNE - TSW) + (TNW - TSE)) * (1.f / 12.f);
+          kk -= sUx[idx] * gxT + sUy[idx] * gyT;
+          const float sTr = sqrtf(fmaxf(Tp, 0.f) * A.invTc);
+          kk -= sAs[idx] * Tp + sBs[idx] * (1.f + A.kappa * (1.f - sTr)) * sTr;
+        }
+        hk = kk;
+      }
+      const bool own = r == 0 || (i >= H && i < H + TX && j >= H && j < H + TY);
+      const int gxu = x0 - H + i;
+      if (own && gxu < A.nx) {
+        const int t = (j - H) * TX + (i - H);
+        if (gy == 1) a_qb += (double)(wk * sLan[js * FW + i] * (Tc[js * FW + i] - Tp));
+        if (g.top_wall && gy == A.ny - 2) a_qt += (double)(wk * sLan[idx] * (Tp - Tc[jn * FW + i]));
+        if (gy == A.W) a_qi += (double)(wk * sLan[js * FW + i] * (Tc[js * FW + i] - Tp));
+        if (k == 1) {
+          sAcc[t] = hk;
+        } else if (k < 4) {
+          sAcc[t] += 2.f * hk;
+        } else {
+          const float Tnew = sT0[idx] + dt * (1.f / 6.f) * (sAcc[t] + hk);
+          if (nonfinite(Tnew)) err |= ERR_NONFINITE;
+          A.T_out[(long long)gy * A.nx + wrapx(gxu, A.nx)] = Tnew;
+          a_E += (double)Tnew / (double)sIrcv[idx];
+        }
+      }
+      if (k < 4) Tn[idx] = sT0[idx] + cnext * hk;
+    }
+    __syncthreads();
+  }
+
+  // ---- per-block FP64 partials
+  double v[NPART] = {a_mass, a_E, a_qb, a_qt, a_qi, a_ut};
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int q = 0; q < NPART; ++q) {
+    const double s = warp_sum(v[q]);
+    if (lane == 0) s_red[warp][q] = s;
+  }
+  if (err) atomicOr(&s_err, err);
+  __syncthreads();
+  if (tid < NPART) {
+    double s = 0.0;
+#pragma unroll
+    for (int wgi = 0; wgi < NTHREADS / 32; ++wgi) s += s_red[wgi][tid];
+    A.partials[part * NPART + tid] = s;
+  }
+  if (tid == 0 && s_err) atomicOr(&A.state->error_flags, s_err);
+}
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(NTHREADS, 4) k_step(const StepArgs A) {
+  extern __shared__ float sm[];
+  step_tile<TX, TY>(A, blockIdx.x, blockIdx.y, (long long)blockIdx.y * gridDim.x + blockIdx.x, sm);
+}
+
+// Batched step: the blocks of one launch cover the tiles of every domain of a
+// sweep.  tile_off[d] is the first block of domain d (tile_off[n] = grid size);
+// a block finds its domain by binary search, copies that domain's descriptor
+// to shared memory and runs the same tile step.  Stopped domains are skipped.
+template <int TX, int TY>
+__global__ void __launch_bounds__(NTHREADS, 4) k_step_batch(const StepArgs* __restrict__ desc,
+                                                            const int* __restrict__ tile_off,
+                                                            const int* __restrict__ active, int n) {
+  extern __shared__ float sm[];
+  __shared__ StepArgs sA;
+  __shared__ int s_dom;
+  const int b = blockIdx.x;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_off[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    s_dom = lo;
+  }
+  __syncthreads();
+  const int d = s_dom;
+  if (!active[d]) return;
+  {
+    const int* src = reinterpret_cast<const int*>(desc + d);
+    int* dst = reinterpret_cast<int*>(&sA);
+    for (int q = threadIdx.x; q < (int)(sizeof(StepArgs) / sizeof(int)); q += NTHREADS) dst[q] = src[q];
+  }
+  __syncthreads();
+  const int local = b - tile_off[d];
+  const int tx = (sA.nx + TX - 1) / TX;
+  step_tile<TX, TY>(sA, local % tx, local / tx, (long long)local, sm);
+}
+
+// FP64 reduction of the per-block partials (one CTA); updates the lagged
+// scalars of the next step and the diagnostics record.
+__global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ partials, int nblk, DevState* st,
+                                                 double inv_nfluid, double inv_nx, double* hist, int hist_cap) {
+  __shared__ double s_red[8][NPART];
+  double v[NPART];
+#pragma unroll
+  for (int q = 0; q < NPART; ++q) v[q] = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < NPART; ++q) v[q] += partials[(long long)b * NPART + q];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NPART; ++q) {
+    const double s = warp_sum(v[q]);
+    if (lane == 0) s_red[warp][q] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s[NPART];
+#pragma unroll
+    for (int q = 0; q < NPART; ++q) {
+      s[q] = 0.0;
+      for (int wgi = 0; wgi < 8; ++wgi) s[q] += s_red[wgi][q];
+    }
+    st->rho_ave_prev = st->rho_ave;
+    st->rho_ave = s[P_MASS] * inv_nfluid;
+    const double ut = s[P_UTOP] * inv_nx;
+    st->u_top = ut;
+    st->U = ut > 0.0 ? ut : 0.0;
+    st->Uc = st->U / (1.0 + st->U);
+    st->step += 1;
+    st->mass = s[P_MASS];
+    st->energy = s[P_ENERGY];
+    st->q_bottom = s[P_QB] * inv_nx;
+    st->q_top = s[P_QT] * inv_nx;
+    st->q_interface = s[P_QI] * inv_nx;
+    st->q_sum += st->q_bottom;
+    st->q_count += 1;
+    if (hist && st->hist_len < hist_cap) hist[st->hist_len++] = st->q_bottom;
+  }
+}
+
+// One CTA per domain of a batch: the same reduction as k_reduce.
+struct ReduceArgs {
+  const double* partials;
+  DevState* state;
+  double* hist;
+  int nblk;
+  double inv_nfluid, inv_nx;
+};
+
+__global__ void __launch_bounds__(256) k_reduce_batch(const ReduceArgs* __restrict__ ra,
+                                                       const int* __restrict__ active, int hist_cap) {
+  const int d = blockIdx.x;
+  if (!active[d]) return;
+  const ReduceArgs r = ra[d];
+  __shared__ double s_red[8][NPART];
+  double v[NPART];
+#pragma unroll
+  for (int q = 0; q < NPART; ++q) v[q] = 0.0;
+  for (int b = threadIdx.x; b < r.nblk; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < NPART; ++q) v[q] += r.partials[(long long)b * NPART + q];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NPART; ++q) {
+    const double s = warp_sum(v[q]);
+    if (lane == 0) s_red[warp][q] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s[NPART];
+#pragma unroll
+    for (int q = 0; q < NPART; ++q) {
+      s[q] = 0.0;
+      for (int wgi = 0; wgi < 8; ++wgi) s[q] += s_red[wgi][q];
+    }
+    DevState* st = r.state;
+    st->rho_ave_prev = st->rho_ave;
+    st->rho_ave = s[P_MASS] * r.inv_nfluid;
+    const double ut = s[P_UTOP] * r.inv_nx;
+    st->u_top = ut;
+    st->U = ut > 0.0 ? ut : 0.0;
+    st->Uc = st->U / (1.0 + st->U);
+    st->step += 1;
+    st->mass = s[P_MASS];
+    st->energy = s[P_ENERGY];
+    st->q_bottom = s[P_QB] * r.inv_nx;
+    st->q_top = s[P_QT] * r.inv_nx;
+    st->q_interface = s[P_QI] * r.inv_nx;
+    st->q_sum += st->q_bottom;
+    st->q_count += 1;
+    if (r.hist && st->hist_len < hist_cap) r.hist[st->hist_len++] = st->q_bottom;
+  }
+}
+
+// Initial state: f* = rest equilibrium w_i rho (deviation form), T with the
+// Dirichlet rows set, the convective-outlet memory, and per-block fluid mass.
+__global__ void __launch_bounds__(256) k_init(const StepArgs A, const float* __restrict__ rho0,
+                                              const float* __restrict__ T0, float* __restrict__ f,
+                                              float* __restrict__ T, float* __restrict__ ftop_a,
+                                              float* __restrict__ ftop_b) {
+  const Geo g = make_geo(A);
+  const long long N = A.plane;
+  double mass = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(c / A.nx), x = (int)(c % A.nx);
+    const bool solid = g.solid_row(y);
+    const float d = solid ? 0.f : rho0[c] - A.rho_ref;
+    const float w[9] = {4.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f,
+                        1.f / 36.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f};
+#pragma unroll
+    for (int q = 0; q < 9; ++q) f[q * N + c] = solid ? 0.f : w[q] * d;
+    T[c] = g.dirichlet_row(y) ? (y == 0 ? A.T_bottom : A.T_top) : T0[c];
+    if (!solid) mass += (double)rho0[c];
+    if (y == A.ny - 1 && ftop_a) {
+      ftop_a[x] = w[4] * d;
+      ftop_a[A.nx + x] = w[7] * d;
+      ftop_a[2 * A.nx + x] = w[8] * d;
+      ftop_b[x] = w[4] * d;
+      ftop_b[A.nx + x] = w[7] * d;
+      ftop_b[2 * A.nx + x] = w[8] * d;
+    }
+  }
+  __shared__ double s_red[8];
+  const double s = warp_sum(mass);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += s_red[q];
+    A.partials[(long long)blockIdx.x * NPART + P_MASS] = t;
+  }
+}
+
+__global__ void k_init_state(const double* __restrict__ partials, int nblk, DevState* st, double inv_nfluid) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double m = 0.0;
+    for (int b = 0; b < nblk; ++b) m += partials[(long long)b * NPART + P_MASS];
+    st->rho_ave = m * inv_nfluid;
+    st->rho_ave_prev = st->rho_ave;
+    st->U = 0.0;
+    st->Uc = 0.0;
+    st->step = 0;
+    st->mass = m;
+    st->energy = 0.0;
+    st->q_bottom = st->q_top = st->q_interface = st->u_top = 0.0;
+    st->q_sum = 0.0;
+    st->q_count = 0;
+    st->error_flags = 0;
+    st->hist_len = 0;
+  }
+}
+
+// rho^n and u^n from the stored post-collision populations: collision keeps
+// mass and leaves sum_i e_i f*_i = rho u + F/2 (Eqs. 2, 5, 8), so
+// u = (sum e f* - F/2) / rho with F recomputed from rho^n and T^n.
+__global__ void __launch_bounds__(256) k_read(const StepArgs A, const float* __restrict__ Tn, int zero_u,
+                                              float* rho_out, float* ux_out, float* uy_out) {
+  const Geo g = make_geo(A);
+  const long long N = A.plane;
+  const float rho_ave = (float)A.state->rho_ave_prev;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(c / A.nx), x = (int)(c % A.nx);
+    if (g.solid_row(y)) {
+      if (rho_out) rho_out[c] = 0.f;
+      if (ux_out) ux_out[c] = 0.f;
+      if (uy_out) uy_out[c] = 0.f;
+      continue;
+    }
+    float psi_nb[3][3];
+    float rho = 0.f, jx = 0.f, jy = 0.f;
+    for (int dy = -1; dy <= 1; ++dy) {
+      int yy = y + dy;
+      yy = yy > A.ny - 1 ? A.ny - 1 : yy;  // zero-gradient ghost above an open top
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int xx = wrapx(x + dx, A.nx);
+        float ps = 0.f;
+        if (!g.solid_row(yy)) {
+          const long long o = (long long)yy * A.nx + xx;
+          float f[9];
+#pragma unroll
+          for (int q = 0; q < 9; ++q) f[q] = A.f_out[q * N + o];
+          const float r = A.rho_ref + sum9(f);
+          const float T = A.eos_T_fixed ? A.Ts : Tn[o];
+          ps = sqrtf(fmaxf(pr_psi2(A, r, T), 0.f));
+          if (dx == 0 && dy == 0) {
+            rho = r;
+            jx = (f[1] - f[3]) + ((f[5] - f[6]) - (f[7] - f[8]));
+            jy = (f[2] - f[4]) + ((f[5] + f[6]) - (f[7] + f[8]));
+          }
+        }
+        psi_nb[dy + 1][dx + 1] = ps;
+      }
+    }
+    const float psi = psi_nb[1][1];
+    const bool sol_s = g.solid_row(y - 1);
+    const bool sol_n = g.solid_row(y + 1 > A.ny - 1 ? A.ny - 1 : y + 1);
+    for (int dx = 0; dx < 3; ++dx) {
+      if (sol_s) psi_nb[0][dx] = psi;
+      if (sol_n) psi_nb[2][dx] = psi;
+    }
+    const float sx = (psi_nb[1][2] - psi_nb[1][0]) * (1.f / 3.f) +
+                     ((psi_nb[2][2] - psi_nb[2][0]) + (psi_nb[0][2] - psi_nb[0][0])) * (1.f / 12.f);
+    const float sy = (psi_nb[2][1] - psi_nb[0][1]) * (1.f / 3.f) +
+                     ((psi_nb[2][2] + psi_nb[2][0]) - (psi_nb[0][2] + psi_nb[0][0])) * (1.f / 12.f);
+    const float Fx = -A.G * psi * sx;
+    const float Fy = -A.G * psi * sy + A.Gw[x] * psi * psi * ((float)sol_n - (float)sol_s) * (1.f / 6.f) +
+                     (rho - rho_ave) * A.g_y;
+    if (rho_out) rho_out[c] = rho;
+    if (ux_out) ux_out[c] = zero_u ? 0.f : (jx - 0.5f * Fx) / rho;
+    if (uy_out) uy_out[c] = zero_u ? 0.f : (jy - 0.5f * Fy) / rho;
+  }
+}
+
+}  // namespace hlb

@@ -1,0 +1,69 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol that
+include/hlb.h declares; its host-only thermodynamics agrees with the oracle.
+No kernel is launched here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1812_10375_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    from paper_1812_10375_gb300 import hlb
+    return hlb
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(hlb_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    so = ctypes.CDLL(lib.LIB_PATH)
+    decl = declared_symbols()
+    assert len(decl) >= 12
+    missing = [n for n in decl if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_host_coexistence_matches_oracle(lib):
+    from oracle import eos
+    p = lib.default_params(8, 8)
+    Tc, rl, rv, h = lib.eos_coexistence(p)
+    pr = eos.PR()
+    orl, orv, _ = eos.coexistence(0.86 * pr.Tc, pr)
+    assert Tc == pytest.approx(pr.Tc, rel=1e-14)
+    assert rl == pytest.approx(orl, rel=1e-10)
+    assert rv == pytest.approx(orv, rel=1e-10)
+    assert h == pytest.approx(eos.latent_heat(0.86 * pr.Tc, pr, orl, orv), rel=1e-9)
+
+
+def test_defaults_are_the_paper_values(lib, paper):
+    p = lib.default_params(16, 16)
+    assert p.a == pytest.approx(paper["a"]["value"]) and p.b == pytest.approx(paper["b"]["value"])
+    assert p.Ts_over_Tc == paper["Ts_over_Tc"]["value"] and p.sigma == paper["sigma"]["value"]
+    assert p.cv == paper["cv"]["value"] and p.k == paper["k"]["value"] and p.Gw0 == paper["Gw0"]["value"]
+    # tau = 3 nu + 1/2 (Eq. 3 with dt = 1)
+    assert p.tau_l == pytest.approx(3 * paper["nu_l"]["value"] + 0.5)
+    assert p.tau_v == pytest.approx(3 * paper["nu_v"]["value"] + 0.5)
+
+
+def test_workspace_size_and_rejections(lib):
+    p = lib.default_params(64, 48)
+    n = lib.workspace_bytes(p)
+    assert n >= 2 * 10 * 64 * 48 * 4
+    bad = lib.default_params(2, 48)
+    assert lib.workspace_bytes(bad) == 0
+    p.n_sub = 2
+    assert lib.workspace_bytes(p) == 0

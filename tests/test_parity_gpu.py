@@ -1,0 +1,126 @@
+"""GPU parity: the FP32 CUDA step against the FP64 oracle, element by element on
+the same seeded inputs, through the C ABI.
+
+Tolerance: relative L-infinity error 1e-5.  rho and T are relative to the
+field's maximum.  u is relative to the lattice sound speed c_s = 1/sqrt(3) (the
+Mach-number scale): FP32 populations of order 0.7 resolve the momentum only to
+about 1e-7 absolute, so an error relative to max|u| (printed as u_rel_max) can
+exceed 1e-5 where the flow is nearly at rest.  Solid nodes are excluded from
+rho and u."""
+import numpy as np
+import pytest
+
+from paper_1812_10375_gb300 import workloads as wl
+
+from helpers import coexistence, gpu_domain, oracle_domain, ragged_case, rel_linf
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+CS = 1.0 / np.sqrt(3.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1812_10375_gb300 import build
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def coex():
+    return coexistence()
+
+
+def compare(case, coex, steps, storage=0, tol=TOL, chunks=1):
+    od = oracle_domain(case, coex)
+    gd = gpu_domain(case, coex, storage=storage)
+    per = steps // chunks
+    for _ in range(chunks):
+        od.step(per)
+        gd.step(per)
+    rho_o, ux_o, uy_o, T_o = od.fields()
+    rho_g, ux_g, uy_g, T_g = [t.cpu().numpy() for t in gd.read()]
+    fl = od.fluid
+    umag_o = np.sqrt(ux_o ** 2 + uy_o ** 2)
+    du = max(np.abs(ux_g - ux_o)[fl].max(), np.abs(uy_g - uy_o)[fl].max())
+    err = dict(
+        rho=rel_linf(rho_g, rho_o, fl),
+        u=float(du / CS),
+        T=rel_linf(T_g, T_o),
+    )
+    print(f"{case.name}: u_rel_max {du / umag_o[fl].max():.2e} (max|u| {umag_o[fl].max():.2e})")
+    dg, do = gd.diag(), od.diag()
+    return err, dg, do, gd, od
+
+
+def flux_tol(case, coex, T):
+    """A face flux lambda_f (T_a - T_b) differences two FP32 temperatures, so its
+    tolerance follows from the T tolerance: |dq| <= 2 lambda_f TOL max|T|."""
+    lam_w = 3.0 * coex["rho_l"] * 6.0 * 0.1
+    lam = coex["rho_v"] * 6.0 * 0.1 if case.name == "flat_interface" else lam_w
+    return 2.0 * lam * TOL * float(np.abs(T).max())
+
+
+def test_flat_interface_1000_steps(coex):
+    case = wl.flat_interface()
+    err, dg, do, _, od = compare(case, coex, 1000)
+    print("flat interface errors", err)
+    assert max(err.values()) < TOL, err
+    assert dg.step == 1000 and dg.error_flags == 0
+    assert dg.mass == pytest.approx(do["mass"], rel=1e-6)
+    qt = flux_tol(case, coex, od.T)
+    assert dg.q_bottom == pytest.approx(do["q_bottom"], abs=qt)
+    assert dg.q_top == pytest.approx(do["q_top"], abs=qt)
+    assert dg.energy == pytest.approx(do["energy"], rel=1e-5)
+
+
+def test_ragged_box_sites_gravity_convective(coex):
+    case = ragged_case()
+    err, dg, do, _, od = compare(case, coex, 300)
+    print("ragged errors", err)
+    assert max(err.values()) < TOL, err
+    assert dg.rho_ave == pytest.approx(do["rho_ave"], rel=1e-6)
+    assert dg.q_interface == pytest.approx(do["q_interface"], abs=flux_tol(case, coex, od.T))
+
+
+def test_film_const_rho_top_1000_steps(coex):
+    case = wl.film()
+    err, dg, do, _, od = compare(case, coex, 1000)
+    print("film errors", err)
+    assert max(err.values()) < TOL, err
+    assert dg.q_bottom == pytest.approx(do["q_bottom"], abs=flux_tol(case, coex, od.T))
+
+
+def test_pool_boiling_400x400_short_horizon(coex):
+    err, dg, do, _, _ = compare(wl.pool(), coex, 200)
+    print("pool errors", err)
+    assert max(err.values()) < TOL, err
+
+
+def test_plain_storage_also_matches(coex):
+    err, _, _, _, _ = compare(ragged_case(), coex, 300, storage=1)
+    print("plain-storage ragged errors", err)
+    assert max(err.values()) < TOL, err
+
+
+def test_step_chunks_and_graph_replay_are_identical(coex):
+    """Graph replay (16-step chunks) and single launches give bit-identical fields."""
+    case = ragged_case()
+    a = gpu_domain(case, coex)
+    b = gpu_domain(case, coex)
+    a.step(37)
+    for _ in range(37):
+        b.step(1)
+    for x, y in zip(a.read(), b.read()):
+        assert (x == y).all()
+
+
+def test_read_before_step_returns_initial_fields(coex):
+    case = wl.film(nx=40, ny=60)
+    rho0, T0 = wl.initial_fields(case, coex["rho_l"], coex["rho_v"], coex["Tc"])
+    gd = gpu_domain(case, coex)
+    rho, ux, uy, T = [t.cpu().numpy() for t in gd.read()]
+    fl = np.arange(case.ny)[:, None] >= case.wall_rows
+    np.testing.assert_allclose(rho[fl[:, 0]], rho0[fl[:, 0]], rtol=1e-6)
+    assert np.all(ux == 0) and np.all(uy == 0)
