@@ -205,6 +205,41 @@ hlb_status hlb_batch_stop(hlb_batch* b, int i);
 
 hlb_status hlb_batch_destroy(hlb_batch* b);
 
+/* ------------------------------------------------------- no-allocation step
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory (a plug-in inside an application that owns
+ * every allocation through its own pool, a callback running inside another
+ * component's graph capture or real-time loop).  One coupled step, exactly as
+ * hlb_step performs it, of a domain whose state lives in the caller's buffers:
+ *   d_f_in / d_f_out   9 planes of nx*ny FP32 populations (plane q at offset
+ *                      q*nx*ny), deviations f_q - w_q rho_v for
+ *                      HLB_STORE_DEVIATION or the populations themselves for
+ *                      HLB_STORE_PLAIN; solid rows are ignored;
+ *   d_T_in / d_T_out   nx*ny FP32 temperature;
+ *   d_ftop_in / _out   3*nx FP32 (populations 4, 7, 8 entering the top row at
+ *                      the previous step, same storage form); needed only for
+ *                      HLB_TOP_CONVECTIVE, else may be NULL;
+ *   rho_ave, U         the lagged mean fluid density and outlet velocity
+ *                      (h_out->rho_ave and max(0, h_out->u_top) of the previous
+ *                      call);
+ *   h_out              the step's FP64 diagnostics (synchronises the stream).
+ * Sites (at most HLB_STATIC_MAX_SITES) give the wetting table as in
+ * hlb_set_nucleation_sites.  All scratch (per-block FP64 partials, the device
+ * diagnostics record, the wetting table) lives in one static device array of
+ * HLB_STATIC_SCRATCH_BYTES inside the library, held by every GPU that loads it
+ * until exit; no call allocates.  Limits: nx <= HLB_STATIC_MAX_NX and at most
+ * 20,474 tiles of 32 x 16 cells (about 10.4 million cells); larger lattices
+ * return HLB_EINVAL.  The first call on a device resolves the array's address
+ * with that device current (make that first call before any stream capture).
+ * Every call shares the array and clears what must start at zero; calls that
+ * overlap on the GPU race. */
+#define HLB_STATIC_SCRATCH_BYTES (1u << 20)
+#define HLB_STATIC_MAX_NX 16384
+#define HLB_STATIC_MAX_SITES 32
+hlb_status hlb_step_static(const hlb_params* p, int n_sites, const hlb_site* h_sites, const float* d_f_in,
+                           float* d_f_out, const float* d_T_in, float* d_T_out, const float* d_ftop_in,
+                           float* d_ftop_out, double rho_ave, double U, hlb_diag_record* h_out, void* stream);
+
 const char* hlb_strerror(hlb_status s);
 
 #ifdef __cplusplus

@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -827,3 +828,214 @@ const char* hlb_strerror(hlb_status s) {
 }
 
 }  // extern "C"
+
+// ===================================================================
+// hlb_step_static: one coupled step whose scratch memory is a static device
+// array inside this library, for callers that cannot allocate device memory.
+//
+// Who needs it: code that runs where no allocator is available or allowed --
+// a solver embedded as a plug-in in a host application that owns every device
+// allocation through its own pool, a callback invoked inside someone else's
+// CUDA-graph capture or real-time loop where cudaMalloc would stall or fail, or
+// a process whose device memory is fully reserved up front.  Such a caller can
+// still hand over its own state buffers (inputs and outputs), but cannot give
+// the library a workspace for the per-block FP64 partial sums, the device-side
+// diagnostics record and the wetting table.  This entry point takes those from
+// `g_scratch` below instead, and calls no cudaMalloc, cudaFree or allocating
+// library routine.
+//
+// The scratch array is HLB_STATIC_SCRATCH_BYTES (1 MiB) of device memory that
+// every GPU which loads the library holds until the process exits.  Every call
+// shares it and it keeps the last call's contents; the diagnostics record is
+// cleared at the start of each call and the partial sums are fully rewritten by
+// each step, so no call sees stale values.  Calls that overlap on the GPU (two
+// streams, or two host threads) race on the shared array.
+
+namespace {
+
+constexpr int MAX_DEVICES = 64;
+constexpr size_t STATE_BYTES = 256;
+constexpr size_t GW_BYTES = (size_t)HLB_STATIC_MAX_NX * sizeof(float);
+constexpr size_t PART_BYTES = HLB_STATIC_SCRATCH_BYTES - STATE_BYTES - GW_BYTES;
+constexpr long long MAX_BLOCKS = (long long)(PART_BYTES / (NPART * sizeof(double)));
+static_assert(sizeof(DevState) <= STATE_BYTES, "device record does not fit its slot");
+
+// The scratch itself: [DevState | G_w table | per-block partials].
+static __device__ __align__(256) unsigned char g_scratch[HLB_STATIC_SCRATCH_BYTES];
+
+// Host-side address of g_scratch per device.  In host code the name g_scratch
+// is only a stand-in, not a device address; the real address comes from
+// cudaGetSymbolAddress with the device current.
+void* g_scratch_addr[MAX_DEVICES] = {nullptr};
+std::mutex g_setup_mutex;
+
+struct StaticSites {
+  int n;
+  hlb_site s[HLB_STATIC_MAX_SITES];
+};
+
+// Clear the diagnostics record and set this step's lagged inputs; build the
+// wetting table (Section 4.2, Fig. 6b) from the sites.
+__global__ void k_static_prepare(DevState* st, float* Gw, int nx, double Gw0, StaticSites sites, double rho_ave,
+                                 double U) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) {
+    st->rho_ave = rho_ave;
+    st->rho_ave_prev = rho_ave;
+    st->U = U > 0.0 ? U : 0.0;
+    st->Uc = st->U / (1.0 + st->U);
+    st->step = 0;
+    st->mass = st->energy = st->q_bottom = st->q_top = st->q_interface = st->u_top = 0.0;
+    st->q_sum = 0.0;
+    st->q_count = 0;
+    st->error_flags = 0;
+    st->hist_len = 0;
+  }
+  for (int x = t; x < nx; x += gridDim.x * blockDim.x) {
+    double g = Gw0;
+    for (int k = 0; k < sites.n; ++k) {
+      const double half = 0.5 * sites.s[k].width;
+      double d = fabs((double)x - sites.s[k].x_center);
+      d = fmin(d, (double)nx - d);
+      if (d <= half) g = fmin(g, sites.s[k].gw_min + (Gw0 - sites.s[k].gw_min) * d / half);
+    }
+    Gw[x] = (float)g;
+  }
+}
+
+// Once per device, with that device current: resolve the address of g_scratch
+// and allow this translation unit's step kernel its dynamic shared memory.
+hlb_status setup_device(void** addr) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return HLB_ECUDA;
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return HLB_ECUDA;
+    const int FN = (TILE_X + 2 * HALO) * (TILE_Y + 2 * HALO);
+    const int smem = (10 * FN + TILE_X * TILE_Y) * (int)sizeof(float);
+    if (cudaFuncSetAttribute(k_step<TILE_X, TILE_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+      return HLB_ECUDA;
+    g_scratch_addr[dev] = p;
+  }
+  *addr = g_scratch_addr[dev];
+  return HLB_OK;
+}
+
+}  // namespace
+
+extern "C" hlb_status hlb_step_static(const hlb_params* p, int n_sites, const hlb_site* h_sites,
+                                      const float* d_f_in, float* d_f_out, const float* d_T_in, float* d_T_out,
+                                      const float* d_ftop_in, float* d_ftop_out, double rho_ave, double U,
+                                      hlb_diag_record* h_out, void* stream) {
+  if (!p || !d_f_in || !d_f_out || !d_T_in || !d_T_out || !h_out) return HLB_EINVAL;
+  if (n_sites < 0 || n_sites > HLB_STATIC_MAX_SITES || (n_sites > 0 && !h_sites)) return HLB_EINVAL;
+  if (hlb_workspace_bytes(p) == 0) return HLB_EINVAL;  // the same parameter checks as hlb_init
+  if (p->top_bc == HLB_TOP_CONVECTIVE && (!d_ftop_in || !d_ftop_out)) return HLB_EINVAL;
+  if (p->nx > HLB_STATIC_MAX_NX) return HLB_EINVAL;
+  const long long nblk = (long long)((p->nx + TILE_X - 1) / TILE_X) * ((p->ny + TILE_Y - 1) / TILE_Y);
+  if (nblk > MAX_BLOCKS) return HLB_EINVAL;  // lattice larger than the static scratch serves
+  if (!(rho_ave > 0.0) || !isfinite(U)) return HLB_EINVAL;
+
+  void* base = nullptr;
+  const hlb_status st0 = setup_device(&base);
+  if (st0 != HLB_OK) return st0;
+  unsigned char* scratch = (unsigned char*)base;
+  DevState* state = (DevState*)scratch;
+  float* Gw = (float*)(scratch + STATE_BYTES);
+  double* partials = (double*)(scratch + STATE_BYTES + GW_BYTES);
+  cudaStream_t s = (cudaStream_t)stream;
+
+  // parameters, resolved as hlb_init resolves them (no allocation: host stack only)
+  hlb_params q = *p;
+  double Tc = 0.0;
+  if (!(q.rho_l > 0 && q.rho_v > 0)) {
+    if (hlb_eos_coexistence(p, &Tc, &q.rho_l, &q.rho_v, nullptr) != HLB_OK) return HLB_EINVAL;
+  } else if (hlb_eos_coexistence(p, &Tc, nullptr, nullptr, nullptr) != HLB_OK) {
+    Tc = (q.a / q.b) * (0.0778 / 0.45724) / q.R;
+  }
+  if (!(q.rho_w > 0)) q.rho_w = 3.0 * q.rho_l;
+  if (!(q.cv_w > 0)) q.cv_w = q.cv;
+  if (!(q.lambda_w > 0)) q.lambda_w = 3.0 * q.rho_l * q.cv * q.k;
+  const double kappa = 0.37464 + 1.54226 * q.omega - 0.26992 * q.omega * q.omega;
+
+  StepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.nx = q.nx;
+  a.ny = q.ny;
+  a.W = q.wall_rows;
+  a.top_bc = q.top_bc;
+  a.eos_T_fixed = q.eos_T_fixed;
+  a.plane = (long long)q.nx * q.ny;
+  a.R = (float)q.R;
+  a.a = (float)q.a;
+  a.b = (float)q.b;
+  a.kappa = (float)kappa;
+  a.invTc = (float)(1.0 / Tc);
+  a.Ts = (float)(q.Ts_over_Tc * Tc);
+  a.G = (float)q.G;
+  a.g_y = (float)q.g_y;
+  a.sig_e = (float)((1.0 - 0.5 * q.s_e) * q.sigma_coef * q.sigma / (1.0 / q.s_e - 0.5));
+  a.sig_z = (float)((1.0 - 0.5 * q.s_zeta) * q.sigma_coef * q.sigma / (1.0 / q.s_zeta - 0.5));
+  a.s_e = (float)q.s_e;
+  a.s_z = (float)q.s_zeta;
+  a.s_j = (float)q.s_j;
+  a.s_q = (float)q.s_q;
+  a.tau_l = (float)q.tau_l;
+  a.tau_v = (float)q.tau_v;
+  a.rho_v = (float)q.rho_v;
+  a.dtau_drho = (float)((q.tau_l - q.tau_v) / (q.rho_l - q.rho_v));
+  a.rho_ref = (float)(q.storage == HLB_STORE_DEVIATION ? q.rho_v : 0.0);
+  a.cvk = (float)(q.cv * q.k);
+  a.cv = (float)q.cv;
+  a.rcv_w = (float)(q.rho_w * q.cv_w);
+  a.inv_rcv_w = (float)(1.0 / (q.rho_w * q.cv_w));
+  a.lambda_w = (float)q.lambda_w;
+  a.dt = (float)(1.0 / q.n_sub);
+  a.T_bottom = (float)q.T_bottom;
+  a.T_top = (float)q.T_top;
+  a.f_in = d_f_in;
+  a.f_out = d_f_out;
+  a.T_in = d_T_in;
+  a.T_out = d_T_out;
+  a.Gw = Gw;
+  a.ftop_in = d_ftop_in;
+  a.ftop_out = d_ftop_out;
+  a.partials = partials;
+  a.state = state;
+
+  StaticSites sites;
+  memset(&sites, 0, sizeof(sites));
+  sites.n = n_sites;
+  for (int k = 0; k < n_sites; ++k) {
+    if (!(h_sites[k].width > 0)) return HLB_EINVAL;
+    sites.s[k] = h_sites[k];
+  }
+  const int fluid_rows = q.ny - q.wall_rows - (q.top_bc == HLB_TOP_WALL ? 1 : 0);
+  const double n_fluid = (double)fluid_rows * q.nx;
+
+  k_static_prepare<<<(q.nx + 255) / 256, 256, 0, s>>>(state, Gw, q.nx, q.Gw0, sites, rho_ave, U);
+  const int FN = (TILE_X + 2 * HALO) * (TILE_Y + 2 * HALO);
+  const size_t smem = (size_t)(10 * FN + TILE_X * TILE_Y) * sizeof(float);
+  const dim3 grid((q.nx + TILE_X - 1) / TILE_X, (q.ny + TILE_Y - 1) / TILE_Y);
+  k_step<TILE_X, TILE_Y><<<grid, NTHREADS, smem, s>>>(a);
+  k_reduce<<<1, 256, 0, s>>>(partials, (int)nblk, state, 1.0 / n_fluid, 1.0 / (double)q.nx, nullptr, 0);
+  if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
+
+  DevState out;
+  if (cudaMemcpyAsync(&out, state, sizeof(out), cudaMemcpyDeviceToHost, s) != cudaSuccess) return HLB_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return HLB_ECUDA;
+  h_out->step = out.step;
+  h_out->mass = out.mass;
+  h_out->energy = out.energy;
+  h_out->q_bottom = out.q_bottom;
+  h_out->q_top = out.q_top;
+  h_out->q_interface = out.q_interface;
+  h_out->rho_ave = out.rho_ave;
+  h_out->u_top = out.u_top;
+  h_out->q_bottom_timeavg = out.q_bottom;
+  h_out->error_flags = out.error_flags;
+  if (out.error_flags & ERR_TIMEOUT) return HLB_ETIMEOUT;
+  return out.error_flags ? HLB_EUNSTABLE : HLB_OK;
+}

@@ -82,6 +82,8 @@ def lib() -> C.CDLL:
             "hlb_batch_flux_history": (st, [vp, C.c_int, P(C.c_double), C.c_int, P(C.c_int)]),
             "hlb_batch_stop": (st, [vp, C.c_int]),
             "hlb_batch_destroy": (st, [vp]),
+            "hlb_step_static": (st, [P(hlb_params), C.c_int, P(hlb_site), vp, vp, vp, vp, vp, vp,
+                                     C.c_double, C.c_double, P(hlb_diag_record), vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
