@@ -16,8 +16,11 @@ using namespace hlb;
 
 namespace {
 
-constexpr int TILE_X = 32;
-constexpr int TILE_Y = 16;
+constexpr int TILE_X = TILE_W;  // 52 output columns in a 64-wide frame
+#ifndef HLB_TILE_Y
+#define HLB_TILE_Y 28
+#endif
+constexpr int TILE_Y = HLB_TILE_Y;
 constexpr int GRAPH_STEPS = 16;     // steps per captured graph (even: buffers return to parity 0)
 constexpr int HIST_CAP = 1 << 16;   // wall-flux history entries kept per domain
 constexpr int INIT_BLOCKS = 304;
@@ -189,8 +192,7 @@ Layout layout_of(const hlb_params* p) {
 }
 
 size_t smem_bytes() {
-  const int FN = (TILE_X + 2 * HALO) * (TILE_Y + 2 * HALO);
-  return (size_t)(10 * FN + TILE_X * TILE_Y) * sizeof(float);
+  return (size_t)step_smem_floats<TILE_Y>() * sizeof(float);
 }
 
 StepArgs args_for(hlb_domain* d, int par) {
@@ -206,7 +208,7 @@ StepArgs args_for(hlb_domain* d, int par) {
 
 hlb_status launch_step(hlb_domain* d) {
   const StepArgs a = args_for(d, d->parity);
-  k_step<TILE_X, TILE_Y><<<d->grid, NTHREADS, d->smem, d->stream>>>(a);
+  k_step<TILE_Y><<<d->grid, NTHREADS, d->smem, d->stream>>>(a);
   k_reduce<<<1, 256, 0, d->stream>>>(d->partials, (int)(d->grid.x * d->grid.y), d->state, 1.0 / (double)d->n_fluid,
                                      1.0 / (double)d->p.nx, d->hist, HIST_CAP);
   if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
@@ -335,9 +337,9 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
   a.partials = d->partials;
   a.state = d->state;
 
-  if (cudaFuncSetAttribute(k_step<TILE_X, TILE_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem) !=
+  if (cudaFuncSetAttribute(k_step<TILE_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(k_step_batch<TILE_X, TILE_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_step_batch<TILE_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)d->smem) != cudaSuccess)
     return HLB_ECUDA;
   // uniform wetting table
@@ -415,7 +417,7 @@ hlb_status upload_tables(hlb_batch* b) {
 
 hlb_status batch_launch(hlb_batch* b, cudaEvent_t before, cudaEvent_t after) {
   if (before && cudaEventRecord(before, b->stream) != cudaSuccess) return HLB_ECUDA;
-  k_step_batch<TILE_X, TILE_Y><<<b->total_tiles, NTHREADS, b->smem, b->stream>>>(
+  k_step_batch<TILE_Y><<<b->total_tiles, NTHREADS, b->smem, b->stream>>>(
       b->d_desc + (size_t)b->parity * b->n, b->d_tile_off, b->d_active, b->n);
   if (after && cudaEventRecord(after, b->stream) != cudaSuccess) return HLB_ECUDA;
   k_reduce_batch<<<b->n, 256, 0, b->stream>>>(b->d_ra, b->d_active, HIST_CAP);
@@ -912,9 +914,8 @@ hlb_status setup_device(void** addr) {
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return HLB_ECUDA;
-    const int FN = (TILE_X + 2 * HALO) * (TILE_Y + 2 * HALO);
-    const int smem = (10 * FN + TILE_X * TILE_Y) * (int)sizeof(float);
-    if (cudaFuncSetAttribute(k_step<TILE_X, TILE_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+    const int smem = step_smem_floats<TILE_Y>() * (int)sizeof(float);
+    if (cudaFuncSetAttribute(k_step<TILE_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)
       return HLB_ECUDA;
     g_scratch_addr[dev] = p;
@@ -1016,10 +1017,9 @@ extern "C" hlb_status hlb_step_static(const hlb_params* p, int n_sites, const hl
   const double n_fluid = (double)fluid_rows * q.nx;
 
   k_static_prepare<<<(q.nx + 255) / 256, 256, 0, s>>>(state, Gw, q.nx, q.Gw0, sites, rho_ave, U);
-  const int FN = (TILE_X + 2 * HALO) * (TILE_Y + 2 * HALO);
-  const size_t smem = (size_t)(10 * FN + TILE_X * TILE_Y) * sizeof(float);
+  const size_t smem = (size_t)step_smem_floats<TILE_Y>() * sizeof(float);
   const dim3 grid((q.nx + TILE_X - 1) / TILE_X, (q.ny + TILE_Y - 1) / TILE_Y);
-  k_step<TILE_X, TILE_Y><<<grid, NTHREADS, smem, s>>>(a);
+  k_step<TILE_Y><<<grid, NTHREADS, smem, s>>>(a);
   k_reduce<<<1, 256, 0, s>>>(partials, (int)nblk, state, 1.0 / n_fluid, 1.0 / (double)q.nx, nullptr, 0);
   if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
 

@@ -20,11 +20,20 @@ namespace hlb {
 enum { TOP_WALL = 0, TOP_CONST_RHO = 1, TOP_CONVECTIVE = 2 };
 
 constexpr int HALO = 6;       // frame halo of the fused kernel
-constexpr int NTHREADS = 256; // threads per CTA of the fused kernel
+#ifndef HLB_STEP_MINB
+#define HLB_STEP_MINB 2  // resident CTAs per SM the register budget is sized for
+#endif
+#ifndef HLB_STEP_THREADS
+#define HLB_STEP_THREADS 512
+#endif
+constexpr int NTHREADS = HLB_STEP_THREADS;  // threads per CTA of the fused kernel
 
+// x is at most a frame halo (plus a tile) outside [0, nx): fold it back
+// with additions instead of an integer division.
 __device__ __forceinline__ int wrapx(int x, int nx) {
-  int r = x % nx;
-  return r < 0 ? r + nx : r;
+  while (x < 0) x += nx;
+  while (x >= nx) x -= nx;
+  return x;
 }
 
 __device__ __forceinline__ bool nonfinite(float v) {
@@ -62,15 +71,14 @@ __device__ __forceinline__ float pr_psi2(const StepArgs& A, float rho, float T) 
 // open top row from above are the rest equilibrium at rho_v (constant density)
 // or the convective-outlet update with the lagged velocity U (Uc = U / (1 + U)).
 // D2Q9 order: 0 rest, 1 (+x), 2 (+y), 3 (-x), 4 (-y), 5 (+x+y), 6 (-x+y), 7 (-x-y), 8 (+x-y).
-__device__ __forceinline__ void pull(const StepArgs& A, const Geo& g, int x, int y, float Uc, float f[9]) {
+__device__ __forceinline__ void pull(const StepArgs& A, const Geo& g, int x, int xm, int xp, int y, float Uc,
+                                     float f[9]) {
   const int nx = g.nx;
-  const int xm = x == 0 ? nx - 1 : x - 1;
-  const int xp = x == nx - 1 ? 0 : x + 1;
-  const long long P = A.plane;
+  const int P = (int)A.plane;  // nx * ny < 2^31 (checked at init)
   const float* __restrict__ F = A.f_in;
-  const long long r0 = (long long)y * nx;
-  const long long rs = r0 - nx;
-  const long long rn = r0 + nx;
+  const int r0 = y * nx;
+  const int rs = r0 - nx;
+  const int rn = r0 + nx;
   const bool bb_s = g.solid_row(y - 1);
   const bool open_n = g.top_open && y == g.ny - 1;
   const bool bb_n = !open_n && g.solid_row(y + 1);
@@ -124,7 +132,7 @@ __device__ __forceinline__ float sum9(const float f[9]) {
 // FP32 rounding cannot bias mass or momentum from step to step.
 // Fm2_psi2 = |F_m|^2 / psi^2.  Writes the nine post-collision values and returns their sum.
 __device__ __forceinline__ float collide_store(const StepArgs& A, const float f[9], float rho, float ux, float uy,
-                                               float Fx, float Fy, float Fm2_psi2, long long off) {
+                                               float Fx, float Fy, float Fm2_psi2, int off) {
   const float sa = (f[1] + f[2]) + (f[3] + f[4]);
   const float sd = (f[5] + f[6]) + (f[7] + f[8]);
   const float m0 = f[0] + sa + sd;  // rho - rho_ref
@@ -167,7 +175,7 @@ __device__ __forceinline__ float collide_store(const StepArgs& A, const float f[
   const float o6 = f[6] + (bd - r3 - r4 + r5 + r6 - r8);
   const float o7 = f[7] + (bd - r3 - r4 - r5 - r6 + r8);
   const float o8 = f[8] + (bd + r3 + r4 - r5 - r6 - r8);
-  const long long P = A.plane;
+  const int P = (int)A.plane;
   float* __restrict__ out = A.f_out + off;
   out[0] = o0;
   out[P] = o1;
@@ -188,12 +196,59 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// Fused coupled step on tile (bx, by) of TX x TY cells.  Shared-memory frame
-// of (TX+12) x (TY+12) cells; ring r of the tile = frame cells within distance r
-// of the tile.  `part` is the tile's slot in the domain's partial-sum array.
-template <int TX, int TY>
-__device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, long long part, float* sm) {
-  constexpr int H = HALO, FW = TX + 2 * H, FH = TY + 2 * H, FN = FW * FH;
+// Compensated (float-float) summation: hi + lo carries about twice the
+// precision of FP32, so the per-block partial sums stay accurate to ~1e-14
+// relative while all arithmetic runs in the FP32 pipes (GB300's FP64 pipe
+// runs at 1/64 of the FP32 rate).  TwoSum is exact in round-to-nearest.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += e;
+}
+
+__device__ __forceinline__ void ff_merge(float& hi, float& lo, float h2, float l2) {
+  ff_add(hi, lo, h2);
+  lo += l2;
+  const float s = hi + lo;  // renormalise (|hi| >= |lo|)
+  lo = lo - (s - hi);
+  hi = s;
+}
+
+__device__ __forceinline__ void ff_warp_sum(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+    ff_merge(hi, lo, h2, l2);
+  }
+}
+
+// Geometry of the fused kernel's tile: a frame of FRAME_W = 64 columns (the
+// TILE_W = 52 output columns plus a 6-cell halo on either side) by TY + 12 rows.
+// Each thread owns one frame column (tid & 63) for the whole step and visits
+// every NPH-th frame row (NPH = threads / 64, starting at tid >> 6), so a warp
+// always works on 32 consecutive cells of one row: x-wrapping and the wetting
+// table are resolved once per thread and row properties are uniform across a
+// warp.
+constexpr int FRAME_W = 64;
+constexpr int TILE_W = FRAME_W - 2 * HALO;
+
+template <int TY>
+constexpr int step_smem_floats() {
+  return 10 * FRAME_W * (TY + 2 * HALO);
+}
+
+// Fused coupled step on tile (bx, by).  Ring r of the tile = frame cells within
+// distance r of the tile.  `part` is the tile's slot in the partial-sum array.
+template <int TY>
+__device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int part, float* sm) {
+  constexpr int H = HALO, TX = TILE_W, FW = FRAME_W, FH = TY + 2 * H, FN = FW * FH;
+  constexpr int NPH = NTHREADS / FW;  // row phases
+  constexpr int NJ = FH / NPH;
+  static_assert(NTHREADS % FW == 0, "one thread per frame column and row phase");
+  static_assert(FH % NPH == 0, "frame height must be a multiple of the row phases");
   float* const sT0 = sm;            // T^n, ring 5
   float* const sRho = sm + FN;      // rho, ring 5      -> stage buffer Ta
   float* const sPsi = sm + 2 * FN;  // psi, ring 5      -> east-face conductivity
@@ -204,187 +259,196 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, lon
   float* const sIrcv = sm + 7 * FN; // 1/(rho cv), ring 3
   float* const sAs = sm + 8 * FN;   // latent-heat source coefficients, ring 3
   float* const sBs = sm + 9 * FN;
-  float* const sAcc = sm + 10 * FN; // h1 + 2 h2 + 2 h3 on the tile
   float* const sLae = sPsi;
   float* const sTa = sRho;
   float* const sTb = sLam;
   __shared__ int s_err;
-  __shared__ double s_red[NTHREADS / 32][NPART];
+  __shared__ float s_lag[2];
+  __shared__ float s_red[NTHREADS / 32][NPART][2];
 
   const Geo g = make_geo(A);
+  const int nx = A.nx, ny = A.ny;
   const int x0 = bx * TX, y0 = by * TY;
   const int tid = threadIdx.x;
+  const int i = tid & (FW - 1), jp = tid >> 6;
   const int jlo = max(0, H - y0);
-  const int jhi = min(FH - 1, A.ny - 1 - y0 + H);
-  const float Uc = (float)A.state->Uc;
-  const float rho_ave = (float)A.state->rho_ave;
-  if (tid == 0) s_err = 0;
+  const int jhi = min(FH - 1, ny - 1 - y0 + H);
+  const int gxu = x0 - H + i;
+  const int gx = wrapx(gxu, nx);
+  const int xm = gx == 0 ? nx - 1 : gx - 1;
+  const int xp = gx == nx - 1 ? 0 : gx + 1;
+  const float gw = __ldg(A.Gw + gx);
+  const bool own_col = i >= H && i < H + TX && gxu < nx;
+  if (tid == 0) {
+    s_err = 0;
+    s_lag[0] = (float)A.state->Uc;
+    s_lag[1] = (float)A.state->rho_ave;
+  }
   __syncthreads();
+  const float Uc = s_lag[0];
+  const float rho_ave = s_lag[1];
   int err = 0;
-  double a_mass = 0.0, a_E = 0.0, a_qb = 0.0, a_qt = 0.0, a_qi = 0.0, a_ut = 0.0;
+  // Diagnostics partial sums in compensated FP32 (hi, lo); one thread converts
+  // the block's six totals to FP64.
+  float ah[NPART], al[NPART];
+#pragma unroll
+  for (int q = 0; q < NPART; ++q) ah[q] = al[q] = 0.f;
 
   // ---- pass A (ring 5): T^n, rho and psi
-  {
-    constexpr int r = 5, w = TX + 2 * r, h = TY + 2 * r;
-    for (int c = tid; c < w * h; c += NTHREADS) {
-      const int i = c % w + (H - r), j = c / w + (H - r);
-      const int gy = y0 - H + j;
-      if (gy < 0 || gy >= A.ny) continue;
-      const int gx = wrapx(x0 - H + i, A.nx);
-      const int idx = j * FW + i;
-      const float T = g.dirichlet_row(gy) ? (gy == 0 ? A.T_bottom : A.T_top)
-                                          : __ldg(A.T_in + (long long)gy * A.nx + gx);
-      sT0[idx] = T;
-      if (g.solid_row(gy)) {
-        sRho[idx] = 0.f;
-        sPsi[idx] = 0.f;
-        continue;
-      }
-      float f[9];
-      pull(A, g, gx, gy, Uc, f);
-      const float rho = A.rho_ref + sum9(f);
-      float p2 = pr_psi2(A, rho, A.eos_T_fixed ? A.Ts : T);
-      if (!(p2 >= 0.f)) {
-        err |= ERR_PSI_NEG;
-        p2 = 0.f;
-      }
-      sRho[idx] = rho;
-      sPsi[idx] = sqrtf(p2);
+#pragma unroll 1
+  for (int m = 0; m < NJ; ++m) {
+    const int j = jp + NPH * m;
+    const int gy = y0 - H + j;
+    if (j < H - 5 || j >= H + TY + 5 || gy < 0 || gy >= ny) continue;
+    if (i < H - 5 || i >= H + TX + 5) continue;
+    const int idx = j * FW + i;
+    const float T = g.dirichlet_row(gy) ? (gy == 0 ? A.T_bottom : A.T_top) : __ldg(A.T_in + gy * nx + gx);
+    sT0[idx] = T;
+    if (g.solid_row(gy)) {
+      sRho[idx] = 0.f;
+      sPsi[idx] = 0.f;
+      continue;
+    }
+    float f[9];
+    pull(A, g, gx, xm, xp, gy, Uc, f);
+    const float rho = A.rho_ref + sum9(f);
+    float p2 = pr_psi2(A, rho, A.eos_T_fixed ? A.Ts : T);
+    if (!(p2 >= 0.f)) {
+      err |= ERR_PSI_NEG;
+      p2 = 0.f;
+    }
+    sRho[idx] = rho;
+    sPsi[idx] = sqrtf(p2);
+    // momentum sum e_i f_i of ring-4 cells, parked in the velocity arrays
+    // (pass B replaces it in place by u, so halo cells need no second pull)
+    if (j >= H - 4 && j < H + TY + 4 && i >= H - 4 && i < H + TX + 4) {
+      sUx[idx] = (f[1] - f[3]) + ((f[5] - f[6]) - (f[7] - f[8]));
+      sUy[idx] = (f[2] - f[4]) + ((f[5] + f[6]) - (f[7] + f[8]));
     }
   }
   __syncthreads();
 
   // ---- pass B (ring 4): forces, velocity, conductivity; collide the tile
-  {
-    constexpr int r = 4, w = TX + 2 * r, h = TY + 2 * r;
-    for (int c = tid; c < w * h; c += NTHREADS) {
-      const int i = c % w + (H - r), j = c / w + (H - r);
-      const int gy = y0 - H + j;
-      if (gy < 0 || gy >= A.ny) continue;
-      const int idx = j * FW + i;
-      if (g.solid_row(gy)) {
-        sUx[idx] = 0.f;
-        sUy[idx] = 0.f;
-        sLam[idx] = A.lambda_w;
-        continue;
-      }
-      const int gxu = x0 - H + i;
-      const int gx = wrapx(gxu, A.nx);
-      const float psi = sPsi[idx], rho = sRho[idx];
-      const int js = max(j - 1, jlo), jn = min(j + 1, jhi);
-      const bool sol_s = g.solid_row(y0 - H + js);
-      const bool sol_n = g.solid_row(y0 - H + jn);
-      // Eq. (6); a solid neighbour carries psi(x)
-      const float pE = sPsi[idx + 1], pW = sPsi[idx - 1];
-      const float pN = sol_n ? psi : sPsi[jn * FW + i];
-      const float pS = sol_s ? psi : sPsi[js * FW + i];
-      const float pNE = sol_n ? psi : sPsi[jn * FW + i + 1];
-      const float pNW = sol_n ? psi : sPsi[jn * FW + i - 1];
-      const float pSE = sol_s ? psi : sPsi[js * FW + i + 1];
-      const float pSW = sol_s ? psi : sPsi[js * FW + i - 1];
-      const float sx = (pE - pW) * (1.f / 3.f) + ((pNE - pNW) + (pSE - pSW)) * (1.f / 12.f);
-      const float sy = (pN - pS) * (1.f / 3.f) + ((pNE + pNW) - (pSE + pSW)) * (1.f / 12.f);
-      const float Fmx = -A.G * psi * sx;
-      const float Fmy = -A.G * psi * sy;
-      // Eq. (10) with weights omega/3: solid rows are whole rows, so only a
-      // normal component (1/9 + 2/36) (s_N - s_S) remains
-      const float Fay = __ldg(A.Gw + gx) * psi * psi * ((float)sol_n - (float)sol_s) * (1.f / 6.f);
-      const float Fx = Fmx;
-      const float Fy = Fmy + Fay + (rho - rho_ave) * A.g_y;  // Eq. (9)
+#pragma unroll 1
+  for (int m = 0; m < NJ; ++m) {
+    const int j = jp + NPH * m;
+    const int gy = y0 - H + j;
+    if (j < H - 4 || j >= H + TY + 4 || gy < 0 || gy >= ny) continue;
+    if (i < H - 4 || i >= H + TX + 4) continue;
+    const int idx = j * FW + i;
+    if (g.solid_row(gy)) {
+      sUx[idx] = 0.f;
+      sUy[idx] = 0.f;
+      sLam[idx] = A.lambda_w;
+      continue;
+    }
+    const float psi = sPsi[idx], rho = sRho[idx];
+    const int js = max(j - 1, jlo), jn = min(j + 1, jhi);
+    const bool sol_s = g.solid_row(y0 - H + js);
+    const bool sol_n = g.solid_row(y0 - H + jn);
+    // Eq. (6); a solid neighbour carries psi(x)
+    const float pE = sPsi[idx + 1], pW = sPsi[idx - 1];
+    const float pN = sol_n ? psi : sPsi[jn * FW + i];
+    const float pS = sol_s ? psi : sPsi[js * FW + i];
+    const float pNE = sol_n ? psi : sPsi[jn * FW + i + 1];
+    const float pNW = sol_n ? psi : sPsi[jn * FW + i - 1];
+    const float pSE = sol_s ? psi : sPsi[js * FW + i + 1];
+    const float pSW = sol_s ? psi : sPsi[js * FW + i - 1];
+    const float sx = (pE - pW) * (1.f / 3.f) + ((pNE - pNW) + (pSE - pSW)) * (1.f / 12.f);
+    const float sy = (pN - pS) * (1.f / 3.f) + ((pNE + pNW) - (pSE + pSW)) * (1.f / 12.f);
+    const float Fmx = -A.G * psi * sx;
+    const float Fmy = -A.G * psi * sy;
+    // Eq. (10) with weights omega/3: solid rows are whole rows, so only a
+    // normal component (1/9 + 2/36) (s_N - s_S) remains
+    const float Fay = gw * psi * psi * ((float)sol_n - (float)sol_s) * (1.f / 6.f);
+    const float Fx = Fmx;
+    const float Fy = Fmy + Fay + (rho - rho_ave) * A.g_y;  // Eq. (9)
+    const float irho = 1.f / rho;
+    const float ux = (sUx[idx] + 0.5f * Fx) * irho;
+    const float uy = (sUy[idx] + 0.5f * Fy) * irho;
+    sUx[idx] = ux;
+    sUy[idx] = uy;
+    sLam[idx] = rho * A.cvk;
+    if (own_col && j >= H && j < H + TY) {
       float f[9];
-      pull(A, g, gx, gy, Uc, f);
-      const float jx = (f[1] - f[3]) + ((f[5] - f[6]) - (f[7] - f[8]));
-      const float jy = (f[2] - f[4]) + ((f[5] + f[6]) - (f[7] + f[8]));
-      const float irho = 1.f / rho;
-      const float ux = (jx + 0.5f * Fx) * irho;
-      const float uy = (jy + 0.5f * Fy) * irho;
-      sUx[idx] = ux;
-      sUy[idx] = uy;
-      sLam[idx] = rho * A.cvk;
-      const bool own = i >= H && i < H + TX && j >= H && j < H + TY && gxu < A.nx;
-      if (own) {
-        const long long off = (long long)gy * A.nx + gx;
-        const float fsum = collide_store(A, f, rho, ux, uy, Fx, Fy, A.G * A.G * (sx * sx + sy * sy), off);
-        if (nonfinite(fsum)) err |= ERR_NONFINITE;
-        a_mass += (double)rho;
-        if (gy == A.ny - 2) a_ut += (double)uy;
-        if (A.top_bc == TOP_CONVECTIVE && gy == A.ny - 1) {
-          A.ftop_out[gx] = f[4];
-          A.ftop_out[A.nx + gx] = f[7];
-          A.ftop_out[2 * A.nx + gx] = f[8];
-        }
+      pull(A, g, gx, xm, xp, gy, Uc, f);
+      const float fsum = collide_store(A, f, rho, ux, uy, Fx, Fy, A.G * A.G * (sx * sx + sy * sy), gy * nx + gx);
+      if (nonfinite(fsum)) err |= ERR_NONFINITE;
+      ff_add(ah[P_MASS], al[P_MASS], rho);
+      if (gy == ny - 2) ff_add(ah[P_UTOP], al[P_UTOP], uy);
+      if (A.top_bc == TOP_CONVECTIVE && gy == ny - 1) {
+        A.ftop_out[gx] = f[4];
+        A.ftop_out[nx + gx] = f[7];
+        A.ftop_out[2 * nx + gx] = f[8];
       }
     }
   }
   __syncthreads();
 
   // ---- pass C: face conductivities (Eq. 25) on ring 4, coefficients on ring 3
-  {
-    constexpr int r = 4, w = TX + 2 * r, h = TY + 2 * r;
-    for (int c = tid; c < w * h; c += NTHREADS) {
-      const int i = c % w + (H - r), j = c / w + (H - r);
-      const int gy = y0 - H + j;
-      if (gy < 0 || gy >= A.ny) continue;
-      const int idx = j * FW + i;
-      const float lam = sLam[idx];
-      if (i + 1 < H + TX + r) {
-        const float le = sLam[idx + 1];
-        sLae[idx] = 2.f * lam * le / (lam + le);
-      }
-      if (j + 1 < H + TY + r) {
-        const float ln = sLam[min(j + 1, jhi) * FW + i];
-        sLan[idx] = 2.f * lam * ln / (lam + ln);
-      }
+#pragma unroll 1
+  for (int m = 0; m < NJ; ++m) {
+    const int j = jp + NPH * m;
+    const int gy = y0 - H + j;
+    if (j < H - 4 || j >= H + TY + 4 || gy < 0 || gy >= ny) continue;
+    if (i < H - 4 || i >= H + TX + 4) continue;
+    const int idx = j * FW + i;
+    const float lam = sLam[idx];
+    if (i + 1 < H + TX + 4) {
+      const float le = sLam[idx + 1];
+      sLae[idx] = 2.f * lam * le / (lam + le);
     }
-  }
-  {
-    constexpr int r = 3, w = TX + 2 * r, h = TY + 2 * r;
-    for (int c = tid; c < w * h; c += NTHREADS) {
-      const int i = c % w + (H - r), j = c / w + (H - r);
-      const int gy = y0 - H + j;
-      if (gy < 0 || gy >= A.ny) continue;
-      const int idx = j * FW + i;
-      if (g.solid_row(gy)) {
-        sIrcv[idx] = A.inv_rcv_w;
-        sAs[idx] = 0.f;
-        sBs[idx] = 0.f;
-        continue;
-      }
-      const int js = max(j - 1, jlo), jn = min(j + 1, jhi);
-      const float rho = sRho[idx];
-      const float ircv = 1.f / (rho * A.cv);
-      // div u with the isotropic gradient of Eq. (19)
-      const float dux = (sUx[idx + 1] - sUx[idx - 1]) * (1.f / 3.f) +
-                        ((sUx[jn * FW + i + 1] - sUx[js * FW + i - 1]) +
-                         (sUx[js * FW + i + 1] - sUx[jn * FW + i - 1])) * (1.f / 12.f);
-      const float duy = (sUy[jn * FW + i] - sUy[js * FW + i]) * (1.f / 3.f) +
-                        ((sUy[jn * FW + i + 1] - sUy[js * FW + i - 1]) +
-                         (sUy[jn * FW + i - 1] - sUy[js * FW + i + 1])) * (1.f / 12.f);
-      const float divu = dux + duy;
-      const float br = A.b * rho;
-      // T (dp/dT)_rho = As' T + Bs' (1 + kappa (1 - sqrt Tr)) sqrt Tr (Eq. 28)
-      const float Ar = rho * A.R / (1.f - br);
-      const float Br = A.a * rho * rho * A.kappa / (1.f + 2.f * br - br * br);
-      sIrcv[idx] = ircv;
-      sAs[idx] = Ar * ircv * divu;
-      sBs[idx] = Br * ircv * divu;
+    if (j + 1 < H + TY + 4) {
+      const float ln = sLam[min(j + 1, jhi) * FW + i];
+      sLan[idx] = 2.f * lam * ln / (lam + ln);
     }
+    if (j < H - 3 || j >= H + TY + 3 || i < H - 3 || i >= H + TX + 3) continue;
+    if (g.solid_row(gy)) {
+      sIrcv[idx] = A.inv_rcv_w;
+      sAs[idx] = 0.f;
+      sBs[idx] = 0.f;
+      continue;
+    }
+    const int js = max(j - 1, jlo), jn = min(j + 1, jhi);
+    const float rho = sRho[idx];
+    const float ircv = 1.f / (rho * A.cv);
+    // div u with the isotropic gradient of Eq. (19)
+    const float dux = (sUx[idx + 1] - sUx[idx - 1]) * (1.f / 3.f) +
+                      ((sUx[jn * FW + i + 1] - sUx[js * FW + i - 1]) + (sUx[js * FW + i + 1] - sUx[jn * FW + i - 1])) *
+                          (1.f / 12.f);
+    const float duy = (sUy[jn * FW + i] - sUy[js * FW + i]) * (1.f / 3.f) +
+                      ((sUy[jn * FW + i + 1] - sUy[js * FW + i - 1]) + (sUy[jn * FW + i - 1] - sUy[js * FW + i + 1])) *
+                          (1.f / 12.f);
+    const float divu = dux + duy;
+    const float br = A.b * rho;
+    // T (dp/dT)_rho = As' T + Bs' (1 + kappa (1 - sqrt Tr)) sqrt Tr (Eq. 28)
+    const float Ar = rho * A.R / (1.f - br);
+    const float Br = A.a * rho * rho * A.kappa / (1.f + 2.f * br - br * br);
+    sIrcv[idx] = ircv;
+    sAs[idx] = Ar * ircv * divu;
+    sBs[idx] = Br * ircv * divu;
   }
   __syncthreads();
 
-  // ---- RK4 stages (Eq. 18): stage k on ring 4-k
+  // ---- RK4 stages (Eq. 18): stage k on ring 4-k; h1 + 2 h2 + 2 h3 kept in registers
   const float dt = A.dt;
+  float acc[NJ];
+#pragma unroll
+  for (int m = 0; m < NJ; ++m) acc[m] = 0.f;
 #pragma unroll 1
   for (int k = 1; k <= 4; ++k) {
     const float* Tc = k == 1 ? sT0 : (k == 3 ? sTb : sTa);
     float* Tn = k == 1 ? sTa : (k == 2 ? sTb : sTa);
     const float cnext = k == 3 ? dt : 0.5f * dt;
     const float wk = (k == 1 || k == 4) ? dt * (1.f / 6.f) : dt * (2.f / 6.f);
-    const int r = 4 - k, w = TX + 2 * r, h = TY + 2 * r;
-    for (int c = tid; c < w * h; c += NTHREADS) {
-      const int i = c % w + (H - r), j = c / w + (H - r);
+    const float wacc = (k == 1) ? 1.f : 2.f;
+    const int r = 4 - k;
+#pragma unroll
+    for (int m = 0; m < NJ; ++m) {
+      const int j = jp + NPH * m;
       const int gy = y0 - H + j;
-      if (gy < 0 || gy >= A.ny) continue;
+      if (j < H - r || j >= H + TY + r || gy < 0 || gy >= ny) continue;
+      if (i < H - r || i >= H + TX + r) continue;
       const int idx = j * FW + i;
       const int js = max(j - 1, jlo), jn = min(j + 1, jhi);
       const float Tp = Tc[idx];
@@ -406,22 +470,17 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, lon
         }
         hk = kk;
       }
-      const bool own = r == 0 || (i >= H && i < H + TX && j >= H && j < H + TY);
-      const int gxu = x0 - H + i;
-      if (own && gxu < A.nx) {
-        const int t = (j - H) * TX + (i - H);
-        if (gy == 1) a_qb += (double)(wk * sLan[js * FW + i] * (Tc[js * FW + i] - Tp));
-        if (g.top_wall && gy == A.ny - 2) a_qt += (double)(wk * sLan[idx] * (Tp - Tc[jn * FW + i]));
-        if (gy == A.W) a_qi += (double)(wk * sLan[js * FW + i] * (Tc[js * FW + i] - Tp));
-        if (k == 1) {
-          sAcc[t] = hk;
-        } else if (k < 4) {
-          sAcc[t] += 2.f * hk;
+      if (own_col && j >= H && j < H + TY) {
+        if (gy == 1) ff_add(ah[P_QB], al[P_QB], wk * sLan[js * FW + i] * (Tc[js * FW + i] - Tp));
+        if (g.top_wall && gy == ny - 2) ff_add(ah[P_QT], al[P_QT], wk * sLan[idx] * (Tp - Tc[jn * FW + i]));
+        if (gy == A.W) ff_add(ah[P_QI], al[P_QI], wk * sLan[js * FW + i] * (Tc[js * FW + i] - Tp));
+        if (k < 4) {
+          acc[m] += wacc * hk;
         } else {
-          const float Tnew = sT0[idx] + dt * (1.f / 6.f) * (sAcc[t] + hk);
+          const float Tnew = sT0[idx] + dt * (1.f / 6.f) * (acc[m] + hk);
           if (nonfinite(Tnew)) err |= ERR_NONFINITE;
-          A.T_out[(long long)gy * A.nx + wrapx(gxu, A.nx)] = Tnew;
-          a_E += (double)Tnew / (double)sIrcv[idx];
+          A.T_out[gy * nx + gx] = Tnew;
+          ff_add(ah[P_ENERGY], al[P_ENERGY], Tnew / sIrcv[idx]);
         }
       }
       if (k < 4) Tn[idx] = sT0[idx] + cnext * hk;
@@ -429,37 +488,39 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, lon
     __syncthreads();
   }
 
-  // ---- per-block FP64 partials
-  double v[NPART] = {a_mass, a_E, a_qb, a_qt, a_qi, a_ut};
+  // ---- per-block partials: compensated FP32 through warp and block, FP64 at the end
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int q = 0; q < NPART; ++q) {
-    const double s = warp_sum(v[q]);
-    if (lane == 0) s_red[warp][q] = s;
+    ff_warp_sum(ah[q], al[q]);
+    if (lane == 0) {
+      s_red[warp][q][0] = ah[q];
+      s_red[warp][q][1] = al[q];
+    }
   }
   if (err) atomicOr(&s_err, err);
   __syncthreads();
   if (tid < NPART) {
-    double s = 0.0;
+    float hi = s_red[0][tid][0], lo = s_red[0][tid][1];
 #pragma unroll
-    for (int wgi = 0; wgi < NTHREADS / 32; ++wgi) s += s_red[wgi][tid];
-    A.partials[part * NPART + tid] = s;
+    for (int wgi = 1; wgi < NTHREADS / 32; ++wgi) ff_merge(hi, lo, s_red[wgi][tid][0], s_red[wgi][tid][1]);
+    A.partials[(long long)part * NPART + tid] = (double)hi + (double)lo;
   }
   if (tid == 0 && s_err) atomicOr(&A.state->error_flags, s_err);
 }
 
-template <int TX, int TY>
-__global__ void __launch_bounds__(NTHREADS, 4) k_step(const StepArgs A) {
+template <int TY>
+__global__ void __launch_bounds__(NTHREADS, HLB_STEP_MINB) k_step(const StepArgs A) {
   extern __shared__ float sm[];
-  step_tile<TX, TY>(A, blockIdx.x, blockIdx.y, (long long)blockIdx.y * gridDim.x + blockIdx.x, sm);
+  step_tile<TY>(A, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, sm);
 }
 
 // Batched step: the blocks of one launch cover the tiles of every domain of a
 // sweep.  tile_off[d] is the first block of domain d (tile_off[n] = grid size);
 // a block finds its domain by binary search, copies that domain's descriptor
 // to shared memory and runs the same tile step.  Stopped domains are skipped.
-template <int TX, int TY>
-__global__ void __launch_bounds__(NTHREADS, 4) k_step_batch(const StepArgs* __restrict__ desc,
+template <int TY>
+__global__ void __launch_bounds__(NTHREADS, HLB_STEP_MINB) k_step_batch(const StepArgs* __restrict__ desc,
                                                             const int* __restrict__ tile_off,
                                                             const int* __restrict__ active, int n) {
   extern __shared__ float sm[];
@@ -484,8 +545,8 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_step_batch(const StepArgs* __re
   }
   __syncthreads();
   const int local = b - tile_off[d];
-  const int tx = (sA.nx + TX - 1) / TX;
-  step_tile<TX, TY>(sA, local % tx, local / tx, (long long)local, sm);
+  const int tx = (sA.nx + TILE_W - 1) / TILE_W;
+  step_tile<TY>(sA, local % tx, local / tx, local, sm);
 }
 
 // FP64 reduction of the per-block partials (one CTA); updates the lagged
