@@ -95,6 +95,9 @@ typedef struct {
   double u_top;           /* mean u_y of row ny-2                                */
   double q_bottom_timeavg;/* running mean of q_bottom since the last reset      */
   int error_flags;        /* sticky device error word                            */
+  double vapour_coverage; /* vapour fraction (rho < (rho_l + rho_v)/2) of the
+                             first fluid row above the wall                      */
+  double vapour_coverage_timeavg; /* its running mean since the last reset      */
 } hlb_diag_record;
 
 typedef struct hlb_domain hlb_domain;
@@ -150,7 +153,7 @@ hlb_status hlb_read(hlb_domain* d, float* d_rho, float* d_ux, float* d_uy, float
  * still written). */
 hlb_status hlb_diag(hlb_domain* d, hlb_diag_record* h_out);
 
-/* Restart the running time average of q_bottom at the next step. */
+/* Restart the running time averages (q_bottom, vapour coverage) at the next step. */
 hlb_status hlb_reset_timeavg(hlb_domain* d);
 
 /* Release the handle (the workspace stays the caller's). */

@@ -222,6 +222,7 @@ class Domain:
         self.flags = 0
         self.last = {}
         self.q_bottom_sum = 0.0
+        self.vcov_sum = 0.0
 
     # ------------------------------------------------------------------ flow
     def _stream(self) -> np.ndarray:
@@ -383,6 +384,8 @@ class Domain:
             self.fs = self._collide(f, rho, ux, uy, Fx, Fy, Fmx, Fmy, psi)
         mass = float(rho[fl].sum())
         u_top = float(uy[p.ny - 2].mean())
+        # vapour fraction of the first fluid row above the bottom wall
+        vcov = float(np.mean(rho[p.wall_rows] < 0.5 * (p.rho_l + p.rho_v)))
         self.rho, self.ux, self.uy, self.T = rho, ux, uy, T_new
         if not (np.all(np.isfinite(T_new)) and np.all(np.isfinite(self.fs))):
             self.flags |= FLAG_NONFINITE
@@ -390,10 +393,12 @@ class Domain:
         self.U = max(0.0, u_top)
         self.n += 1
         self.q_bottom_sum += float(q[0])
+        self.vcov_sum += vcov
         self.last = dict(step=self.n, mass=mass, energy=float(np.sum(rcv * T_new)),
                          q_bottom=float(q[0]), q_top=float(q[1]), q_interface=float(q[2]),
                          rho_ave=self.rho_ave, u_top=u_top,
-                         q_bottom_timeavg=self.q_bottom_sum / self.n, error_flags=self.flags)
+                         q_bottom_timeavg=self.q_bottom_sum / self.n, error_flags=self.flags,
+                         vapour_coverage=vcov, vapour_coverage_timeavg=self.vcov_sum / self.n)
 
     # --------------------------------------------------------------- outputs
     def fields(self):

@@ -325,6 +325,7 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
   a.rho_v = (float)q.rho_v;
   a.dtau_drho = (float)((q.tau_l - q.tau_v) / (q.rho_l - q.rho_v));
   a.rho_ref = (float)d->rho_ref;
+  a.rho_mid = (float)(0.5 * (q.rho_l + q.rho_v));
   a.cvk = (float)(q.cv * q.k);
   a.cv = (float)q.cv;
   a.rcv_w = (float)(q.rho_w * q.cv_w);
@@ -642,6 +643,8 @@ hlb_status hlb_diag(hlb_domain* d, hlb_diag_record* out) {
   out->rho_ave = s.rho_ave;
   out->u_top = s.u_top;
   out->q_bottom_timeavg = s.q_count > 0 ? s.q_sum / (double)s.q_count : 0.0;
+  out->vapour_coverage = s.vcov;
+  out->vapour_coverage_timeavg = s.q_count > 0 ? s.vcov_sum / (double)s.q_count : 0.0;
   out->error_flags = s.error_flags;
   d->host_flags = s.error_flags;
   if (s.error_flags & ERR_TIMEOUT) return HLB_ETIMEOUT;
@@ -651,8 +654,8 @@ hlb_status hlb_diag(hlb_domain* d, hlb_diag_record* out) {
 hlb_status hlb_reset_timeavg(hlb_domain* d) {
   if (!d) return HLB_EINVAL;
   const size_t off_sum = offsetof(DevState, q_sum);
-  if (cudaMemsetAsync((char*)d->state + off_sum, 0, sizeof(double) + sizeof(long long), d->stream) != cudaSuccess)
-    return HLB_ECUDA;
+  const size_t len = offsetof(DevState, error_flags) - off_sum;  // q_sum, q_count, vcov, vcov_sum
+  if (cudaMemsetAsync((char*)d->state + off_sum, 0, len, d->stream) != cudaSuccess) return HLB_ECUDA;
   return HLB_OK;
 }
 
@@ -988,6 +991,7 @@ extern "C" hlb_status hlb_step_static(const hlb_params* p, int n_sites, const hl
   a.rho_v = (float)q.rho_v;
   a.dtau_drho = (float)((q.tau_l - q.tau_v) / (q.rho_l - q.rho_v));
   a.rho_ref = (float)(q.storage == HLB_STORE_DEVIATION ? q.rho_v : 0.0);
+  a.rho_mid = (float)(0.5 * (q.rho_l + q.rho_v));
   a.cvk = (float)(q.cv * q.k);
   a.cv = (float)q.cv;
   a.rcv_w = (float)(q.rho_w * q.cv_w);
@@ -1035,6 +1039,8 @@ extern "C" hlb_status hlb_step_static(const hlb_params* p, int n_sites, const hl
   h_out->rho_ave = out.rho_ave;
   h_out->u_top = out.u_top;
   h_out->q_bottom_timeavg = out.q_bottom;
+  h_out->vapour_coverage = out.vcov;
+  h_out->vapour_coverage_timeavg = out.vcov;
   h_out->error_flags = out.error_flags;
   if (out.error_flags & ERR_TIMEOUT) return HLB_ETIMEOUT;
   return out.error_flags ? HLB_EUNSTABLE : HLB_OK;

@@ -6,7 +6,7 @@
 namespace hlb {
 
 // Per-block FP64 partial sums written by the step kernel.
-enum { P_MASS = 0, P_ENERGY, P_QB, P_QT, P_QI, P_UTOP, NPART };
+enum { P_MASS = 0, P_ENERGY, P_QB, P_QT, P_QI, P_UTOP, P_VCOV, NPART };
 
 // Error word bits (match the header's description).
 enum { ERR_NONFINITE = 1, ERR_PSI_NEG = 2, ERR_TIMEOUT = 4 };
@@ -22,6 +22,7 @@ struct DevState {
   double mass, energy, q_bottom, q_top, q_interface, u_top;
   double q_sum;
   long long q_count;
+  double vcov, vcov_sum;  // vapour fraction of the first fluid row, and its running sum
   int error_flags;
   int hist_len;
 };
@@ -39,6 +40,7 @@ struct StepArgs {
   float s_e, s_z, s_j, s_q;
   float tau_l, tau_v, rho_v, dtau_drho;
   float rho_ref;  // deviation storage reference
+  float rho_mid;  // (rho_l + rho_v) / 2: vapour below, liquid above
   // energy (Eq. 17)
   float cvk, cv, rcv_w, inv_rcv_w, lambda_w, dt;
   float T_bottom, T_top;

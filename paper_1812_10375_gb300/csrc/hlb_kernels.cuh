@@ -375,6 +375,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
       const float fsum = collide_store(A, f, rho, ux, uy, Fx, Fy, A.G * A.G * (sx * sx + sy * sy), gy * nx + gx);
       if (nonfinite(fsum)) err |= ERR_NONFINITE;
       ff_add(ah[P_MASS], al[P_MASS], rho);
+      if (gy == A.W && rho < A.rho_mid) ff_add(ah[P_VCOV], al[P_VCOV], 1.f);
       if (gy == ny - 2) ff_add(ah[P_UTOP], al[P_UTOP], uy);
       if (A.top_bc == TOP_CONVECTIVE && gy == ny - 1) {
         A.ftop_out[gx] = f[4];
@@ -589,6 +590,8 @@ __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ parti
     st->q_interface = s[P_QI] * inv_nx;
     st->q_sum += st->q_bottom;
     st->q_count += 1;
+    st->vcov = s[P_VCOV] * inv_nx;
+    st->vcov_sum += st->vcov;
     if (hist && st->hist_len < hist_cap) hist[st->hist_len++] = st->q_bottom;
   }
 }
@@ -644,6 +647,8 @@ __global__ void __launch_bounds__(256) k_reduce_batch(const ReduceArgs* __restri
     st->q_interface = s[P_QI] * r.inv_nx;
     st->q_sum += st->q_bottom;
     st->q_count += 1;
+    st->vcov = s[P_VCOV] * r.inv_nx;
+    st->vcov_sum += st->vcov;
     if (r.hist && st->hist_len < hist_cap) r.hist[st->hist_len++] = st->q_bottom;
   }
 }
@@ -701,6 +706,7 @@ __global__ void k_init_state(const double* __restrict__ partials, int nblk, DevS
     st->q_bottom = st->q_top = st->q_interface = st->u_top = 0.0;
     st->q_sum = 0.0;
     st->q_count = 0;
+    st->vcov = st->vcov_sum = 0.0;
     st->error_flags = 0;
     st->hist_len = 0;
   }

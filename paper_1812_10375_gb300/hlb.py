@@ -35,7 +35,7 @@ class hlb_site(C.Structure):
 class hlb_diag_record(C.Structure):
     _fields_ = [("step", C.c_longlong)] + [(n, C.c_double) for n in (
         "mass", "energy", "q_bottom", "q_top", "q_interface", "rho_ave", "u_top", "q_bottom_timeavg")] + [
-        ("error_flags", C.c_int)]
+        ("error_flags", C.c_int), ("vapour_coverage", C.c_double), ("vapour_coverage_timeavg", C.c_double)]
 
 
 class HlbError(RuntimeError):
@@ -137,6 +137,8 @@ class Diag:
     u_top: float
     q_bottom_timeavg: float
     error_flags: int
+    vapour_coverage: float = 0.0
+    vapour_coverage_timeavg: float = 0.0
 
 
 class Domain:
@@ -203,7 +205,8 @@ class Domain:
         if st not in (HLB_OK, HLB_EUNSTABLE, HLB_ETIMEOUT) or (check_flags and st != HLB_OK):
             check("hlb_diag", st)
         return Diag(rec.step, rec.mass, rec.energy, rec.q_bottom, rec.q_top, rec.q_interface, rec.rho_ave,
-                    rec.u_top, rec.q_bottom_timeavg, rec.error_flags)
+                    rec.u_top, rec.q_bottom_timeavg, rec.error_flags, rec.vapour_coverage,
+                    rec.vapour_coverage_timeavg)
 
     def reset_timeavg(self):
         check("hlb_reset_timeavg", lib().hlb_reset_timeavg(self._h))
@@ -306,7 +309,8 @@ class Batch:
         if st not in (HLB_OK, HLB_EUNSTABLE, HLB_ETIMEOUT) or (check_flags and st != HLB_OK):
             check("hlb_batch_diag", st)
         return Diag(rec.step, rec.mass, rec.energy, rec.q_bottom, rec.q_top, rec.q_interface, rec.rho_ave,
-                    rec.u_top, rec.q_bottom_timeavg, rec.error_flags)
+                    rec.u_top, rec.q_bottom_timeavg, rec.error_flags, rec.vapour_coverage,
+                    rec.vapour_coverage_timeavg)
 
     def flux_history(self, i, max_len=65536):
         import numpy as np

@@ -101,14 +101,19 @@ def draw_sites(rng: np.random.Generator, nx: int, n_sites: int, width: float = S
     if n_sites * spacing > nx:
         raise ValueError("too many sites for this width")
     centres: list[int] = []
-    tries = 0
+    tries = misses = 0
     while len(centres) < n_sites:
         tries += 1
-        if tries > 100000:
+        if tries > 1000000:
             raise RuntimeError("could not place sites")
+        if misses > 2000:  # earlier sites leave no gap wide enough: start over
+            centres, misses = [], 0
         c = int(rng.integers(0, nx))
         if all(min(abs(c - o), nx - abs(c - o)) >= spacing for o in centres):
             centres.append(c)
+            misses = 0
+        else:
+            misses += 1
     centres.sort()
     return [(float(c), float(width), float(minima[j % len(minima)])) for j, c in enumerate(centres)]
 
