@@ -231,7 +231,7 @@ hlb_status hlb_batch_destroy(hlb_batch* b);
  * diagnostics record, the wetting table) lives in one static device array of
  * HLB_STATIC_SCRATCH_BYTES inside the library, held by every GPU that loads it
  * until exit; no call allocates.  Limits: nx <= HLB_STATIC_MAX_NX and at most
- * 20,474 tiles of 32 x 16 cells (about 10.4 million cells); larger lattices
+ * 17,549 tiles of 52 x 28 cells (about 25.5 million cells); larger lattices
  * return HLB_EINVAL.  The first call on a device resolves the array's address
  * with that device current (make that first call before any stream capture).
  * Every call shares the array and clears what must start at zero; calls that
