@@ -208,6 +208,20 @@ hlb_status hlb_batch_stop(hlb_batch* b, int i);
 
 hlb_status hlb_batch_destroy(hlb_batch* b);
 
+/* ------------------------------------------------------------- autotuning
+ * The fused step kernel is compiled for several tile shapes (52 columns by a
+ * few heights, with 256 or 512 threads per CTA).  hlb_tile_variants lists them
+ * (returns their count; arrays may be NULL).  hlb_autotune / hlb_batch_autotune
+ * time steps_per_variant steps of every variant on the handle's own state, keep
+ * the fastest for later steps and report its index in *chosen (and the measured
+ * ms per step in h_ms[0..max_out) if h_ms is not NULL).  The timed steps are
+ * ordinary steps of the simulation: a cell's update does not depend on the tile
+ * shape, so the fields advance exactly as with any variant (only the order of
+ * the FP64 partial sums differs).  Synchronises the stream. */
+int hlb_tile_variants(int* h_tile_w, int* h_tile_h, int* h_threads, int max_out);
+hlb_status hlb_autotune(hlb_domain* d, int steps_per_variant, int* chosen, float* h_ms, int max_out);
+hlb_status hlb_batch_autotune(hlb_batch* b, int steps_per_variant, int* chosen, float* h_ms, int max_out);
+
 /* ------------------------------------------------------- no-allocation step
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory (a plug-in inside an application that owns

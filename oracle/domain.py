@@ -105,10 +105,12 @@ class Params:
     rho_w: float | None = None      # default 3 rho_l
     cv_w: float | None = None       # default cv
     lambda_w: float | None = None   # default 3 rho_l cv k
+    lambda_top: float | None = None # conductivity of a top wall row (default lambda_w)
     g_y: float = 0.0
     Gw: np.ndarray | float = 0.3    # per-column wetting strength or a constant
     rho_l: float | None = None      # coexistence densities at Ts (Maxwell if None)
     rho_v: float | None = None
+    diffusion: str = "fv"          # "fv" (Eqs. 22-26) or "iso" (Eqs. 20-21, the comparison scheme)
 
     def resolved(self) -> "Params":
         p = Params(**{k: getattr(self, k) for k in self.__dataclass_fields__})
@@ -121,6 +123,8 @@ class Params:
             p.cv_w = p.cv
         if p.lambda_w is None:
             p.lambda_w = 3.0 * p.rho_l * p.cv * p.k
+        if p.lambda_top is None:
+            p.lambda_top = p.lambda_w
         p.Gw = np.broadcast_to(np.asarray(p.Gw, dtype=np.float64), (p.nx,)).copy()
         return p
 
@@ -300,10 +304,14 @@ class Domain:
         p = self.p
         fl = self.fluid
         lam = np.where(fl, rho * p.cv * p.k, p.lambda_w)
+        if p.top_bc == TOP_WALL:
+            lam[p.ny - 1] = p.lambda_top
         P = _pad(lam)
         dux, _ = iso_grad(ux)
         _, duy = iso_grad(uy)
+        glx, gly = iso_grad(lam)
         return dict(
+            lam=lam, glx=glx, gly=gly,
             rho=np.where(fl, rho, 1.0), ux=ux, uy=uy, divu=dux + duy,
             rcv=np.where(fl, rho * p.cv, p.rho_w * p.cv_w),
             lam_e=harmonic(lam, _at(P, 1, 0)), lam_w=harmonic(lam, _at(P, -1, 0)),
@@ -312,13 +320,23 @@ class Domain:
     def energy_rhs(self, T, c):
         """K(T), the right-hand side of Eq. (17).
 
-        Diffusion: finite volume with harmonic face conductivities (Eqs. 22-26).
+        Diffusion: finite volume with harmonic face conductivities (Eqs. 22-26),
+        or, with ``diffusion="iso"``, the isotropic central form of Eqs. (20)-(21)
+        that the paper compares against (it is not conservative).
         Advection and div u: isotropic central differences (Eq. 19).  Solid
         nodes carry only diffusion; Dirichlet rows do not change.
         """
         P = _pad(T)
-        diff = (c["lam_e"] * (_at(P, 1, 0) - T) + c["lam_w"] * (_at(P, -1, 0) - T)
-                + c["lam_n"] * (_at(P, 0, 1) - T) + c["lam_s"] * (_at(P, 0, -1) - T))
+        if self.p.diffusion == "iso":
+            # Eq. (21): lambda * laplacian(T) + grad(lambda) . grad(T), with the
+            # isotropic Laplacian of Eq. (20) and the gradients of Eq. (19)
+            lap = (_at(P, 1, 1) + _at(P, -1, 1) + _at(P, 1, -1) + _at(P, -1, -1)
+                   + 4.0 * (_at(P, 1, 0) + _at(P, -1, 0) + _at(P, 0, 1) + _at(P, 0, -1)) - 20.0 * T) / 6.0
+            gTx, gTy = iso_grad(T)
+            diff = c["lam"] * lap + c["glx"] * gTx + c["gly"] * gTy
+        else:
+            diff = (c["lam_e"] * (_at(P, 1, 0) - T) + c["lam_w"] * (_at(P, -1, 0) - T)
+                    + c["lam_n"] * (_at(P, 0, 1) - T) + c["lam_s"] * (_at(P, 0, -1) - T))
         k = diff / c["rcv"]
         gx, gy = iso_grad(T)
         adv = c["ux"] * gx + c["uy"] * gy

@@ -17,10 +17,39 @@ using namespace hlb;
 namespace {
 
 constexpr int TILE_X = TILE_W;  // 52 output columns in a 64-wide frame
-#ifndef HLB_TILE_Y
-#define HLB_TILE_Y 28
-#endif
-constexpr int TILE_Y = HLB_TILE_Y;
+
+// Compiled variants of the fused step kernel (tile height, threads per CTA).
+struct Variant {
+  int ty, nth;
+  size_t smem;
+  const void* single_fn;
+  const void* batch_fn;
+  void (*launch_single)(dim3, size_t, cudaStream_t, const StepArgs&);
+  void (*launch_batch)(int, size_t, cudaStream_t, const StepArgs*, const int*, const int*, int);
+};
+
+template <int TY, int NTH, int MINB>
+void launch_single_v(dim3 grid, size_t smem, cudaStream_t s, const StepArgs& a) {
+  k_step<TY, NTH, MINB><<<grid, NTH, smem, s>>>(a);
+}
+template <int TY, int NTH, int MINB>
+void launch_batch_v(int blocks, size_t smem, cudaStream_t s, const StepArgs* desc, const int* off, const int* act,
+                    int n) {
+  k_step_batch<TY, NTH, MINB><<<blocks, NTH, smem, s>>>(desc, off, act, n);
+}
+
+#define HLB_VARIANT_ENTRY(TY, NTH, MINB)                                                              \
+  Variant{TY, NTH, (size_t)step_smem_floats<TY>() * sizeof(float), (const void*)k_step<TY, NTH, MINB>, \
+          (const void*)k_step_batch<TY, NTH, MINB>, launch_single_v<TY, NTH, MINB>,                   \
+          launch_batch_v<TY, NTH, MINB>},
+const Variant VARIANTS[] = {HLB_STEP_VARIANTS(HLB_VARIANT_ENTRY)};
+constexpr int NVARIANTS = (int)(sizeof(VARIANTS) / sizeof(VARIANTS[0]));
+constexpr int TILE_Y = 28;      // the default variant's tile height (variant 0)
+constexpr int MIN_TILE_Y = 16;  // the shortest variant tile (sizes the partial-sum slots)
+
+dim3 grid_of(int nx, int ny, int v) {
+  return dim3((nx + TILE_X - 1) / TILE_X, (ny + VARIANTS[v].ty - 1) / VARIANTS[v].ty);
+}
 constexpr int GRAPH_STEPS = 16;     // steps per captured graph (even: buffers return to parity 0)
 constexpr int HIST_CAP = 1 << 16;   // wall-flux history entries kept per domain
 constexpr int INIT_BLOCKS = 304;
@@ -165,6 +194,7 @@ struct hlb_domain {
   long long n_fluid = 0;
   dim3 grid;
   size_t smem = 0;
+  int variant = 0;
   StepArgs base;
   cudaGraphExec_t graph = nullptr;
 };
@@ -178,7 +208,7 @@ struct Layout {
 Layout layout_of(const hlb_params* p) {
   Layout L;
   const size_t N = (size_t)p->nx * p->ny;
-  const size_t nblk = (size_t)((p->nx + TILE_X - 1) / TILE_X) * ((p->ny + TILE_Y - 1) / TILE_Y);
+  const size_t nblk = (size_t)((p->nx + TILE_X - 1) / TILE_X) * ((p->ny + MIN_TILE_Y - 1) / MIN_TILE_Y);
   size_t o = 0;
   L.f = o;        o += align_up(2 * 9 * N * sizeof(float));
   L.T = o;        o += align_up(2 * N * sizeof(float));
@@ -192,7 +222,7 @@ Layout layout_of(const hlb_params* p) {
 }
 
 size_t smem_bytes() {
-  return (size_t)step_smem_floats<TILE_Y>() * sizeof(float);
+  return VARIANTS[0].smem;
 }
 
 StepArgs args_for(hlb_domain* d, int par) {
@@ -208,7 +238,7 @@ StepArgs args_for(hlb_domain* d, int par) {
 
 hlb_status launch_step(hlb_domain* d) {
   const StepArgs a = args_for(d, d->parity);
-  k_step<TILE_Y><<<d->grid, NTHREADS, d->smem, d->stream>>>(a);
+  VARIANTS[d->variant].launch_single(d->grid, VARIANTS[d->variant].smem, d->stream, a);
   k_reduce<<<1, 256, 0, d->stream>>>(d->partials, (int)(d->grid.x * d->grid.y), d->state, 1.0 / (double)d->n_fluid,
                                      1.0 / (double)d->p.nx, d->hist, HIST_CAP);
   if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
@@ -294,7 +324,8 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
   d->hist = (double*)(ws + L.hist);
   const int fluid_rows = q.ny - q.wall_rows - (q.top_bc == HLB_TOP_WALL ? 1 : 0);
   d->n_fluid = (long long)fluid_rows * q.nx;
-  d->grid = dim3((q.nx + TILE_X - 1) / TILE_X, (q.ny + TILE_Y - 1) / TILE_Y);
+  d->variant = 0;
+  d->grid = grid_of(q.nx, q.ny, 0);
   d->smem = smem_bytes();
 
   StepArgs& a = d->base;
@@ -338,11 +369,13 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
   a.partials = d->partials;
   a.state = d->state;
 
-  if (cudaFuncSetAttribute(k_step<TILE_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_step_batch<TILE_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)d->smem) != cudaSuccess)
-    return HLB_ECUDA;
+  for (int v = 0; v < NVARIANTS; ++v) {
+    if (cudaFuncSetAttribute(VARIANTS[v].single_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)VARIANTS[v].smem) != cudaSuccess ||
+        cudaFuncSetAttribute(VARIANTS[v].batch_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)VARIANTS[v].smem) != cudaSuccess)
+      return HLB_ECUDA;
+  }
   // uniform wetting table
   return hlb_set_nucleation_sites(d, 0, nullptr);
 }
@@ -365,6 +398,7 @@ struct hlb_batch {
   int parity = 0;
   long long steps = 0;
   size_t smem = 0;
+  int variant = 0;
   cudaGraphExec_t graph = nullptr;
 };
 
@@ -418,8 +452,8 @@ hlb_status upload_tables(hlb_batch* b) {
 
 hlb_status batch_launch(hlb_batch* b, cudaEvent_t before, cudaEvent_t after) {
   if (before && cudaEventRecord(before, b->stream) != cudaSuccess) return HLB_ECUDA;
-  k_step_batch<TILE_Y><<<b->total_tiles, NTHREADS, b->smem, b->stream>>>(
-      b->d_desc + (size_t)b->parity * b->n, b->d_tile_off, b->d_active, b->n);
+  VARIANTS[b->variant].launch_batch(b->total_tiles, VARIANTS[b->variant].smem, b->stream,
+                                    b->d_desc + (size_t)b->parity * b->n, b->d_tile_off, b->d_active, b->n);
   if (after && cudaEventRecord(after, b->stream) != cudaSuccess) return HLB_ECUDA;
   k_reduce_batch<<<b->n, 256, 0, b->stream>>>(b->d_ra, b->d_active, HIST_CAP);
   if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
@@ -820,6 +854,101 @@ hlb_status hlb_batch_destroy(hlb_batch* b) {
   return HLB_OK;
 }
 
+// ------------------------------------------------------------- autotuning
+namespace {
+
+hlb_status set_batch_variant(hlb_batch* b, int v) {
+  b->variant = v;
+  b->tile_off[0] = 0;
+  for (int i = 0; i < b->n; ++i) {
+    hlb_domain* d = &b->dom[i];
+    d->variant = v;
+    d->grid = grid_of(d->p.nx, d->p.ny, v);
+    b->tile_off[i + 1] = b->tile_off[i] + (int)(d->grid.x * d->grid.y);
+  }
+  b->total_tiles = b->tile_off[b->n];
+  b->smem = VARIANTS[v].smem;
+  batch_drop_graph(b);
+  return upload_tables(b);
+}
+
+}  // namespace
+
+hlb_status hlb_autotune(hlb_domain* d, int steps_per_variant, int* chosen, float* h_ms, int max_out) {
+  if (!d || steps_per_variant < 1 || !chosen) return HLB_EINVAL;
+  if (!d->fields_set || d->host_flags) return HLB_ESTATE;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HLB_ECUDA;
+  float best = 1e30f;
+  int best_v = 0;
+  hlb_status st = HLB_OK;
+  for (int v = 0; v < NVARIANTS && st == HLB_OK; ++v) {
+    d->variant = v;
+    d->grid = grid_of(d->p.nx, d->p.ny, v);
+    drop_graph(d);
+    cudaEventRecord(e0, d->stream);
+    for (int k = 0; k < steps_per_variant && st == HLB_OK; ++k) st = launch_step(d);
+    cudaEventRecord(e1, d->stream);
+    float ms = 0.f;
+    if (st == HLB_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      st = HLB_ECUDA;
+    ms /= (float)steps_per_variant;
+    if (h_ms && v < max_out) h_ms[v] = ms;
+    if (ms < best) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  d->variant = best_v;
+  d->grid = grid_of(d->p.nx, d->p.ny, best_v);
+  drop_graph(d);
+  *chosen = best_v;
+  return st;
+}
+
+hlb_status hlb_batch_autotune(hlb_batch* b, int steps_per_variant, int* chosen, float* h_ms, int max_out) {
+  if (!b || steps_per_variant < 1 || !chosen) return HLB_EINVAL;
+  for (int i = 0; i < b->n; ++i)
+    if (!b->dom[i].fields_set) return HLB_ESTATE;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HLB_ECUDA;
+  float best = 1e30f;
+  int best_v = 0;
+  hlb_status st = HLB_OK;
+  for (int v = 0; v < NVARIANTS && st == HLB_OK; ++v) {
+    st = set_batch_variant(b, v);
+    if (st != HLB_OK) break;
+    cudaEventRecord(e0, b->stream);
+    for (int k = 0; k < steps_per_variant && st == HLB_OK; ++k) st = batch_launch(b, nullptr, nullptr);
+    cudaEventRecord(e1, b->stream);
+    float ms = 0.f;
+    if (st == HLB_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      st = HLB_ECUDA;
+    ms /= (float)steps_per_variant;
+    if (h_ms && v < max_out) h_ms[v] = ms;
+    if (ms < best) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const hlb_status st2 = set_batch_variant(b, best_v);
+  *chosen = best_v;
+  return st != HLB_OK ? st : st2;
+}
+
+int hlb_tile_variants(int* h_tile_w, int* h_tile_h, int* h_threads, int max_out) {
+  for (int v = 0; v < NVARIANTS && v < max_out; ++v) {
+    if (h_tile_w) h_tile_w[v] = TILE_X;
+    if (h_tile_h) h_tile_h[v] = VARIANTS[v].ty;
+    if (h_threads) h_threads[v] = VARIANTS[v].nth;
+  }
+  return NVARIANTS;
+}
+
 const char* hlb_strerror(hlb_status s) {
   switch (s) {
     case HLB_OK: return "ok";
@@ -917,9 +1046,8 @@ hlb_status setup_device(void** addr) {
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return HLB_ECUDA;
-    const int smem = step_smem_floats<TILE_Y>() * (int)sizeof(float);
-    if (cudaFuncSetAttribute(k_step<TILE_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(VARIANTS[0].single_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)VARIANTS[0].smem) != cudaSuccess)
       return HLB_ECUDA;
     g_scratch_addr[dev] = p;
   }
@@ -1021,9 +1149,7 @@ extern "C" hlb_status hlb_step_static(const hlb_params* p, int n_sites, const hl
   const double n_fluid = (double)fluid_rows * q.nx;
 
   k_static_prepare<<<(q.nx + 255) / 256, 256, 0, s>>>(state, Gw, q.nx, q.Gw0, sites, rho_ave, U);
-  const size_t smem = (size_t)step_smem_floats<TILE_Y>() * sizeof(float);
-  const dim3 grid((q.nx + TILE_X - 1) / TILE_X, (q.ny + TILE_Y - 1) / TILE_Y);
-  k_step<TILE_Y><<<grid, NTHREADS, smem, s>>>(a);
+  VARIANTS[0].launch_single(grid_of(q.nx, q.ny, 0), VARIANTS[0].smem, s, a);
   k_reduce<<<1, 256, 0, s>>>(partials, (int)nblk, state, 1.0 / n_fluid, 1.0 / (double)q.nx, nullptr, 0);
   if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
 

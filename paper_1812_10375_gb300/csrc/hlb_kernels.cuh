@@ -20,13 +20,9 @@ namespace hlb {
 enum { TOP_WALL = 0, TOP_CONST_RHO = 1, TOP_CONVECTIVE = 2 };
 
 constexpr int HALO = 6;       // frame halo of the fused kernel
-#ifndef HLB_STEP_MINB
-#define HLB_STEP_MINB 2  // resident CTAs per SM the register budget is sized for
-#endif
-#ifndef HLB_STEP_THREADS
-#define HLB_STEP_THREADS 512
-#endif
-constexpr int NTHREADS = HLB_STEP_THREADS;  // threads per CTA of the fused kernel
+// Compiled tile variants of the fused kernel (tile height TY, threads per CTA,
+// CTAs per SM the register budget is sized for); the host autotuner picks one.
+#define HLB_STEP_VARIANTS(X) X(28, 512, 2) X(16, 256, 3) X(20, 512, 2)
 
 // x is at most a frame halo (plus a tile) outside [0, nx): fold it back
 // with additions instead of an integer division.
@@ -242,7 +238,7 @@ constexpr int step_smem_floats() {
 
 // Fused coupled step on tile (bx, by).  Ring r of the tile = frame cells within
 // distance r of the tile.  `part` is the tile's slot in the partial-sum array.
-template <int TY>
+template <int TY, int NTHREADS>
 __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int part, float* sm) {
   constexpr int H = HALO, TX = TILE_W, FW = FRAME_W, FH = TY + 2 * H, FN = FW * FH;
   constexpr int NPH = NTHREADS / FW;  // row phases
@@ -510,18 +506,18 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   if (tid == 0 && s_err) atomicOr(&A.state->error_flags, s_err);
 }
 
-template <int TY>
-__global__ void __launch_bounds__(NTHREADS, HLB_STEP_MINB) k_step(const StepArgs A) {
+template <int TY, int NTH, int MINB>
+__global__ void __launch_bounds__(NTH, MINB) k_step(const StepArgs A) {
   extern __shared__ float sm[];
-  step_tile<TY>(A, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, sm);
+  step_tile<TY, NTH>(A, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, sm);
 }
 
 // Batched step: the blocks of one launch cover the tiles of every domain of a
 // sweep.  tile_off[d] is the first block of domain d (tile_off[n] = grid size);
 // a block finds its domain by binary search, copies that domain's descriptor
 // to shared memory and runs the same tile step.  Stopped domains are skipped.
-template <int TY>
-__global__ void __launch_bounds__(NTHREADS, HLB_STEP_MINB) k_step_batch(const StepArgs* __restrict__ desc,
+template <int TY, int NTH, int MINB>
+__global__ void __launch_bounds__(NTH, MINB) k_step_batch(const StepArgs* __restrict__ desc,
                                                             const int* __restrict__ tile_off,
                                                             const int* __restrict__ active, int n) {
   extern __shared__ float sm[];
@@ -542,12 +538,12 @@ __global__ void __launch_bounds__(NTHREADS, HLB_STEP_MINB) k_step_batch(const St
   {
     const int* src = reinterpret_cast<const int*>(desc + d);
     int* dst = reinterpret_cast<int*>(&sA);
-    for (int q = threadIdx.x; q < (int)(sizeof(StepArgs) / sizeof(int)); q += NTHREADS) dst[q] = src[q];
+    for (int q = threadIdx.x; q < (int)(sizeof(StepArgs) / sizeof(int)); q += NTH) dst[q] = src[q];
   }
   __syncthreads();
   const int local = b - tile_off[d];
   const int tx = (sA.nx + TILE_W - 1) / TILE_W;
-  step_tile<TY>(sA, local % tx, local / tx, local, sm);
+  step_tile<TY, NTH>(sA, local % tx, local / tx, local, sm);
 }
 
 // FP64 reduction of the per-block partials (one CTA); updates the lagged

@@ -82,6 +82,9 @@ def lib() -> C.CDLL:
             "hlb_batch_flux_history": (st, [vp, C.c_int, P(C.c_double), C.c_int, P(C.c_int)]),
             "hlb_batch_stop": (st, [vp, C.c_int]),
             "hlb_batch_destroy": (st, [vp]),
+            "hlb_tile_variants": (C.c_int, [P(C.c_int), P(C.c_int), P(C.c_int), C.c_int]),
+            "hlb_autotune": (st, [vp, C.c_int, P(C.c_int), P(C.c_float), C.c_int]),
+            "hlb_batch_autotune": (st, [vp, C.c_int, P(C.c_int), P(C.c_float), C.c_int]),
             "hlb_step_static": (st, [P(hlb_params), C.c_int, P(hlb_site), vp, vp, vp, vp, vp, vp,
                                      C.c_double, C.c_double, P(hlb_diag_record), vp]),
         }
@@ -139,6 +142,23 @@ class Diag:
     error_flags: int
     vapour_coverage: float = 0.0
     vapour_coverage_timeavg: float = 0.0
+
+
+def tile_variants():
+    n = lib().hlb_tile_variants(None, None, None, 0)
+    w, h, t = (C.c_int * n)(), (C.c_int * n)(), (C.c_int * n)()
+    lib().hlb_tile_variants(w, h, t, n)
+    return [(w[k], h[k], t[k]) for k in range(n)]
+
+
+def _autotune(fn, handle, steps, stream):
+    import torch
+    torch.cuda.current_stream().synchronize()
+    n = lib().hlb_tile_variants(None, None, None, 0)
+    ms = (C.c_float * n)()
+    chosen = C.c_int()
+    check("autotune", fn(handle, int(steps), C.byref(chosen), ms, n))
+    return chosen.value, [ms[k] for k in range(n)]
 
 
 class Domain:
@@ -210,6 +230,10 @@ class Domain:
 
     def reset_timeavg(self):
         check("hlb_reset_timeavg", lib().hlb_reset_timeavg(self._h))
+
+    def autotune(self, steps_per_variant=8):
+        """Time every compiled tile variant on this domain and keep the fastest."""
+        return _autotune(lib().hlb_autotune, self._h, steps_per_variant, self.stream)
 
     def close(self):
         if self._h:
@@ -322,6 +346,10 @@ class Batch:
 
     def stop(self, i):
         check("hlb_batch_stop", lib().hlb_batch_stop(self._h, i))
+
+    def autotune(self, steps_per_variant=8):
+        """Time every compiled tile variant on this batch and keep the fastest."""
+        return _autotune(lib().hlb_batch_autotune, self._h, steps_per_variant, self.stream)
 
     def close(self):
         if self._h:

@@ -83,3 +83,24 @@ def test_stop_and_reuse_slot(coex):
     for x, y in zip(b.read(1), d2.read()):
         assert (x == y).all()
     assert b.diag(1).step == 7
+
+
+def test_autotune_picks_a_variant_and_keeps_results(coex):
+    """The timed autotuning steps are ordinary steps: fields after autotune + k
+    steps equal an untuned run of the same length (tile shape changes only the
+    order of the FP64 partial sums)."""
+    from paper_1812_10375_gb300 import hlb
+    cases = _cases()
+    a = _batch(cases, coex)
+    b = _batch(cases, coex)
+    nv = len(hlb.tile_variants())
+    chosen, ms = a.autotune(steps_per_variant=4)
+    assert 0 <= chosen < nv and len(ms) == nv and all(m > 0 for m in ms)
+    assert ms[chosen] == min(ms)
+    a.step(20)
+    b.step(4 * nv + 20)
+    for i in range(len(cases)):
+        assert a.diag(i).step == b.diag(i).step == 4 * nv + 20
+        for x, y in zip(a.read(i), b.read(i)):
+            x, y = x.cpu().numpy(), y.cpu().numpy()
+            assert np.abs(x - y).max() <= 1e-6 * max(np.abs(y).max(), 1e-30)

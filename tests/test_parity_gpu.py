@@ -82,6 +82,9 @@ def test_ragged_box_sites_gravity_convective(coex):
     assert max(err.values()) < TOL, err
     assert dg.rho_ave == pytest.approx(do["rho_ave"], rel=1e-6)
     assert dg.q_interface == pytest.approx(do["q_interface"], abs=flux_tol(case, coex, od.T))
+    # vapour fraction of the wall row: a count, equal up to cells at the threshold
+    assert abs(dg.vapour_coverage - do["vapour_coverage"]) <= 1.0 / case.nx
+    assert abs(dg.vapour_coverage_timeavg - do["vapour_coverage_timeavg"]) <= 1.0 / case.nx
 
 
 def test_film_const_rho_top_1000_steps(coex):
