@@ -25,7 +25,7 @@ struct Variant {
   const void* single_fn;
   const void* batch_fn;
   void (*launch_single)(dim3, size_t, cudaStream_t, const StepArgs&);
-  void (*launch_batch)(int, size_t, cudaStream_t, const StepArgs*, const int*, const int*, int);
+  void (*launch_batch)(int, size_t, cudaStream_t, const StepArgs&, const DomArgs*, const int*, const int*, int);
 };
 
 template <int TY, int NTH, int MINB>
@@ -33,9 +33,9 @@ void launch_single_v(dim3 grid, size_t smem, cudaStream_t s, const StepArgs& a) 
   k_step<TY, NTH, MINB><<<grid, NTH, smem, s>>>(a);
 }
 template <int TY, int NTH, int MINB>
-void launch_batch_v(int blocks, size_t smem, cudaStream_t s, const StepArgs* desc, const int* off, const int* act,
-                    int n) {
-  k_step_batch<TY, NTH, MINB><<<blocks, NTH, smem, s>>>(desc, off, act, n);
+void launch_batch_v(int blocks, size_t smem, cudaStream_t s, const StepArgs& phys, const DomArgs* desc,
+                    const int* off, const int* act, int n) {
+  k_step_batch<TY, NTH, MINB><<<blocks, NTH, smem, s>>>(phys, desc, off, act, n);
 }
 
 #define HLB_VARIANT_ENTRY(TY, NTH, MINB)                                                              \
@@ -388,7 +388,8 @@ struct hlb_batch {
   int n = 0;
   std::vector<hlb_domain> dom;
   cudaStream_t stream = nullptr;
-  StepArgs* d_desc = nullptr;  // [2][n]: descriptors for batch parity 0 and 1
+  DomArgs* d_desc = nullptr;   // [2][n]: per-domain descriptors for batch parity 0 and 1
+  StepArgs phys;               // model parameters shared by the batch
   ReduceArgs* d_ra = nullptr;  // [n]
   int* d_tile_off = nullptr;   // [n + 1]
   int* d_active = nullptr;     // [n]
@@ -416,7 +417,7 @@ BatchLayout batch_layout(int n, const hlb_params* p) {
     L.dom_off.push_back(o);
     o += layout_of(p + i).total;
   }
-  L.desc = o;     o += align_up(2 * (size_t)n * sizeof(StepArgs));
+  L.desc = o;     o += align_up(2 * (size_t)n * sizeof(DomArgs));
   L.ra = o;       o += align_up((size_t)n * sizeof(ReduceArgs));
   L.tile_off = o; o += align_up((size_t)(n + 1) * sizeof(int));
   L.active = o;   o += align_up((size_t)n * sizeof(int));
@@ -424,13 +425,48 @@ BatchLayout batch_layout(int n, const hlb_params* p) {
   return L;
 }
 
+DomArgs dom_args(const StepArgs& a) {
+  DomArgs d;
+  d.nx = a.nx;
+  d.ny = a.ny;
+  d.W = a.W;
+  d.top_bc = a.top_bc;
+  d.eos_T_fixed = a.eos_T_fixed;
+  d.plane = a.plane;
+  d.T_bottom = a.T_bottom;
+  d.T_top = a.T_top;
+  d.f_in = a.f_in;
+  d.f_out = a.f_out;
+  d.T_in = a.T_in;
+  d.T_out = a.T_out;
+  d.Gw = a.Gw;
+  d.ftop_in = a.ftop_in;
+  d.ftop_out = a.ftop_out;
+  d.partials = a.partials;
+  d.state = a.state;
+  return d;
+}
+
+// The model parameters of a StepArgs (everything DomArgs does not carry).
+StepArgs physics_of(const StepArgs& a) {
+  StepArgs p = a;
+  p.nx = p.ny = p.W = p.top_bc = p.eos_T_fixed = 0;
+  p.plane = 0;
+  p.T_bottom = p.T_top = 0.f;
+  p.f_in = p.T_in = p.Gw = p.ftop_in = nullptr;
+  p.f_out = p.T_out = p.ftop_out = nullptr;
+  p.partials = nullptr;
+  p.state = nullptr;
+  return p;
+}
+
 hlb_status upload_tables(hlb_batch* b) {
-  std::vector<StepArgs> desc(2 * (size_t)b->n);
+  std::vector<DomArgs> desc(2 * (size_t)b->n);
   std::vector<ReduceArgs> ra(b->n);
   for (int i = 0; i < b->n; ++i) {
     hlb_domain* d = &b->dom[i];
-    desc[i] = args_for(d, 0);
-    desc[b->n + i] = args_for(d, 1);
+    desc[i] = dom_args(args_for(d, 0));
+    desc[b->n + i] = dom_args(args_for(d, 1));
     ra[i].partials = d->partials;
     ra[i].state = d->state;
     ra[i].hist = d->hist;
@@ -438,7 +474,7 @@ hlb_status upload_tables(hlb_batch* b) {
     ra[i].inv_nfluid = 1.0 / (double)d->n_fluid;
     ra[i].inv_nx = 1.0 / (double)d->p.nx;
   }
-  if (cudaMemcpyAsync(b->d_desc, desc.data(), desc.size() * sizeof(StepArgs), cudaMemcpyHostToDevice, b->stream) !=
+  if (cudaMemcpyAsync(b->d_desc, desc.data(), desc.size() * sizeof(DomArgs), cudaMemcpyHostToDevice, b->stream) !=
           cudaSuccess ||
       cudaMemcpyAsync(b->d_ra, ra.data(), ra.size() * sizeof(ReduceArgs), cudaMemcpyHostToDevice, b->stream) !=
           cudaSuccess ||
@@ -452,7 +488,7 @@ hlb_status upload_tables(hlb_batch* b) {
 
 hlb_status batch_launch(hlb_batch* b, cudaEvent_t before, cudaEvent_t after) {
   if (before && cudaEventRecord(before, b->stream) != cudaSuccess) return HLB_ECUDA;
-  VARIANTS[b->variant].launch_batch(b->total_tiles, VARIANTS[b->variant].smem, b->stream,
+  VARIANTS[b->variant].launch_batch(b->total_tiles, VARIANTS[b->variant].smem, b->stream, b->phys,
                                     b->d_desc + (size_t)b->parity * b->n, b->d_tile_off, b->d_active, b->n);
   if (after && cudaEventRecord(after, b->stream) != cudaSuccess) return HLB_ECUDA;
   k_reduce_batch<<<b->n, 256, 0, b->stream>>>(b->d_ra, b->d_active, HIST_CAP);
@@ -735,7 +771,15 @@ hlb_status hlb_batch_init(hlb_batch** out, int n, const hlb_params* p, void* d_w
   }
   b->total_tiles = b->tile_off[n];
   b->smem = smem_bytes();
-  b->d_desc = (StepArgs*)(ws + L.desc);
+  b->phys = physics_of(b->dom[0].base);
+  for (int i = 1; i < n; ++i) {
+    const StepArgs pi = physics_of(b->dom[i].base);
+    if (memcmp(&pi, &b->phys, sizeof(StepArgs)) != 0) {
+      delete b;  // a batch shares its model parameters; domains differ in geometry and walls
+      return HLB_EINVAL;
+    }
+  }
+  b->d_desc = (DomArgs*)(ws + L.desc);
   b->d_ra = (ReduceArgs*)(ws + L.ra);
   b->d_tile_off = (int*)(ws + L.tile_off);
   b->d_active = (int*)(ws + L.active);

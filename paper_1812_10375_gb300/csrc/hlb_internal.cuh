@@ -56,4 +56,22 @@ struct StepArgs {
   DevState* state;
 };
 
+// The per-domain part of StepArgs for the batched kernel (geometry, wall
+// temperatures, buffers); the model parameters are shared by the batch and
+// reach the kernel as a by-value argument.
+struct DomArgs {
+  int nx, ny, W, top_bc, eos_T_fixed;
+  long long plane;
+  float T_bottom, T_top;
+  const float* f_in;
+  float* f_out;
+  const float* T_in;
+  float* T_out;
+  const float* Gw;
+  const float* ftop_in;
+  float* ftop_out;
+  double* partials;
+  DevState* state;
+};
+
 }  // namespace hlb

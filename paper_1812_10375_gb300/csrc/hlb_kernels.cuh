@@ -514,14 +514,16 @@ __global__ void __launch_bounds__(NTH, MINB) k_step(const StepArgs A) {
 
 // Batched step: the blocks of one launch cover the tiles of every domain of a
 // sweep.  tile_off[d] is the first block of domain d (tile_off[n] = grid size);
-// a block finds its domain by binary search, copies that domain's descriptor
-// to shared memory and runs the same tile step.  Stopped domains are skipped.
+// a block finds its domain by binary search, takes that domain's geometry and
+// buffers from the descriptor table and the shared model parameters from its
+// by-value argument (constant bank), and runs the same tile step.  Stopped
+// domains are skipped.
 template <int TY, int NTH, int MINB>
-__global__ void __launch_bounds__(NTH, MINB) k_step_batch(const StepArgs* __restrict__ desc,
-                                                            const int* __restrict__ tile_off,
-                                                            const int* __restrict__ active, int n) {
+__global__ void __launch_bounds__(NTH, MINB) k_step_batch(const StepArgs P, const DomArgs* __restrict__ desc,
+                                                          const int* __restrict__ tile_off,
+                                                          const int* __restrict__ active, int n) {
   extern __shared__ float sm[];
-  __shared__ StepArgs sA;
+  __shared__ DomArgs sD;
   __shared__ int s_dom;
   const int b = blockIdx.x;
   if (threadIdx.x == 0) {
@@ -537,13 +539,31 @@ __global__ void __launch_bounds__(NTH, MINB) k_step_batch(const StepArgs* __rest
   if (!active[d]) return;
   {
     const int* src = reinterpret_cast<const int*>(desc + d);
-    int* dst = reinterpret_cast<int*>(&sA);
-    for (int q = threadIdx.x; q < (int)(sizeof(StepArgs) / sizeof(int)); q += NTH) dst[q] = src[q];
+    int* dst = reinterpret_cast<int*>(&sD);
+    for (int q = threadIdx.x; q < (int)(sizeof(DomArgs) / sizeof(int)); q += NTH) dst[q] = src[q];
   }
   __syncthreads();
+  StepArgs A = P;
+  A.nx = sD.nx;
+  A.ny = sD.ny;
+  A.W = sD.W;
+  A.top_bc = sD.top_bc;
+  A.eos_T_fixed = sD.eos_T_fixed;
+  A.plane = sD.plane;
+  A.T_bottom = sD.T_bottom;
+  A.T_top = sD.T_top;
+  A.f_in = sD.f_in;
+  A.f_out = sD.f_out;
+  A.T_in = sD.T_in;
+  A.T_out = sD.T_out;
+  A.Gw = sD.Gw;
+  A.ftop_in = sD.ftop_in;
+  A.ftop_out = sD.ftop_out;
+  A.partials = sD.partials;
+  A.state = sD.state;
   const int local = b - tile_off[d];
-  const int tx = (sA.nx + TILE_W - 1) / TILE_W;
-  step_tile<TY, NTH>(sA, local % tx, local / tx, local, sm);
+  const int tx = (A.nx + TILE_W - 1) / TILE_W;
+  step_tile<TY, NTH>(A, local % tx, local / tx, local, sm);
 }
 
 // FP64 reduction of the per-block partials (one CTA); updates the lagged
