@@ -1,0 +1,106 @@
+"""Physics checks of the GPU step that need long runs: conservation of the
+finite-volume energy update across a conjugate solid-liquid interface
+(Sections 2.3, 3.3), the film evaporation rate of Eq. (29), and statistical
+parity of the time-averaged wall heat flux of a boiling run with the FP64
+oracle (Sections 4.3-4.4)."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_1812_10375_gb300 import workloads as wl
+
+from helpers import coexistence, gpu_domain, oracle_domain
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1812_10375_gb300 import build
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def coex():
+    return coexistence()
+
+
+def test_conjugate_conduction_conserves_energy_fp32(coex):
+    """Uniform liquid at rest on a heater of three times its conductivity, walls
+    at two temperatures: with no forces the flow stays at rest, and the change of
+    sum(rho cv T) must equal the heat through the two Dirichlet faces (the
+    finite-volume fluxes telescope across the solid-liquid face)."""
+    Tc, Ts = coex["Tc"], coex["Ts"]
+    case = wl.Case("conjugate", nx=64, ny=80, wall_rows=12, top_bc="wall", T_bottom_over_Tc=0.86 + 0.1,
+                   T_top_over_Tc=0.86, eos_T_fixed=True, g_y=0.0, Gw0=0.0)
+    rho0 = np.full((case.ny, case.nx), coex["rho_l"])
+    T0 = wl.layered_T(case.ny, case.nx, case.wall_rows, case.T_bottom(Tc), Ts)
+    net = 0.0
+    d2 = gpu_domain(case, coex, rho0=rho0, T0=T0)
+    d2.step(1)
+    E1 = d2.diag().energy
+    for _ in range(2000):
+        d2.step(1)
+        g = d2.diag()
+        net += case.nx * (g.q_bottom - g.q_top)
+    dE = d2.diag().energy - E1
+    _, ux, uy, _ = [t.cpu().numpy() for t in d2.read()]
+    print(f"conjugate conduction: dE {dE:.6e}, heat in {net:.6e}, relative imbalance {abs(dE - net) / abs(net):.2e}")
+    assert np.abs(ux).max() == 0.0 and np.abs(uy).max() == 0.0
+    assert abs(net) > 1e-3 * abs(E1) * 1e-2
+    assert abs(dE - net) <= 1e-3 * abs(net)
+
+
+def test_film_evaporation_rate_matches_eq29(coex):
+    """Eq. (29): at quasi-steady state the evaporated mass flux is m'' = q / h_fg.
+    The film of Section 3.3 (40 x 120, 20-row wall, 30-row film) is heated at
+    Ts + 0.05 Tc; m'' is measured from the loss of liquid volume over the last
+    5000 of 60,000 steps and q is the time-averaged wall heat flux."""
+    from paper_1812_10375_gb300 import hlb
+    from paper_1812_10375_gb300.config import params_for
+    case = wl.film(nx=40, ny=120)
+    p, _ = params_for(case, rho_l=coex["rho_l"], rho_v=coex["rho_v"])
+    h_fg = hlb.eos_coexistence(p)[3]
+    d = gpu_domain(case, coex)
+    rl, rv = coex["rho_l"], coex["rho_v"]
+
+    def liquid_volume():
+        rho = d.read()[0].cpu().numpy().astype(np.float64)[case.wall_rows:]
+        return float(np.sum(np.clip((rho - rv) / (rl - rv), 0.0, 1.0)))
+
+    d.step(55000)
+    d.reset_timeavg()
+    V0 = liquid_volume()
+    d.step(5000)
+    V1 = liquid_volume()
+    q = d.diag().q_bottom_timeavg
+    m = -(V1 - V0) * rl / 5000 / case.nx
+    print(f"film evaporation: m'' h_fg / q = {m * h_fg / q:.4f} (q = {q:.4e}, h_fg = {h_fg:.4f})")
+    assert m * h_fg / q == pytest.approx(1.0, abs=0.05)
+
+
+def test_boiling_time_averaged_flux_matches_oracle(coex):
+    """A boiling pool (96 x 120, 10-row heater at Ts + 0.15 Tc, 3 sites): the
+    wall heat flux averaged over steps 3000-6000 and the wall vapour coverage
+    agree with the FP64 oracle within 3%."""
+    case = wl.pool(nx=96, ny=120, n_sites=3, heater_rows=10, superheat=0.15, seed=5)
+    od = oracle_domain(case, coex)
+    gd = gpu_domain(case, coex)
+    od.step(3000)
+    gd.step(3000)
+    gd.reset_timeavg()
+    qo, co = [], []
+    for _ in range(3000):
+        od.step(1)
+        qo.append(od.diag()["q_bottom"])
+        co.append(od.diag()["vapour_coverage"])
+    gd.step(3000)
+    dg = gd.diag()
+    print(f"boiling pool: time-averaged q oracle {np.mean(qo):.5e} gpu {dg.q_bottom_timeavg:.5e}; "
+          f"coverage oracle {np.mean(co):.3f} gpu {dg.vapour_coverage_timeavg:.3f}")
+    assert np.mean(co) > 0.05  # it boils
+    assert dg.q_bottom_timeavg == pytest.approx(np.mean(qo), rel=0.03)
+    assert dg.vapour_coverage_timeavg == pytest.approx(np.mean(co), rel=0.03, abs=0.01)
