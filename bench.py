@@ -124,6 +124,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate(elapsed_ms: float, cells_per_rank: int, steps: int, dist=None):
+    """Whole-job throughput of independent replicas: the slowest rank's time and
+    the cells of all ranks.  Returns (ms_per_step, MLUPS)."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([elapsed_ms], dtype=torch.float64)
+        if dist.get_backend() == "nccl":
+            t = t.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / steps
+    return ms_per_step, world * cells_per_rank / (ms_per_step * 1e-3) / 1e6
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -287,12 +303,7 @@ def run_ours(args):
         dist.barrier()
     elapsed_ms = start.elapsed_time(end)
     kern_ms = [ev_b[k].elapsed_time(ev_a[k]) for k in range(args.steps)]
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    ms_per_step = elapsed_ms / args.steps
-    value = world * cells / (ms_per_step * 1e-3) / 1e6
+    ms_per_step, value = aggregate(elapsed_ms, cells, args.steps, dist)
     kern_avg_ms = sum(kern_ms) / len(kern_ms)
     diag0 = batch.diag(0, check_flags=False)
 

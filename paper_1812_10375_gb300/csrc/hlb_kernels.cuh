@@ -489,7 +489,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int q = 0; q < NPART; ++q) {
-    ff_warp_sum(ah[q], al[q]);
+    // wall- and top-row quantities are zero in most warps: skip their reduction there
+    if (__any_sync(0xffffffffu, ah[q] != 0.f || al[q] != 0.f)) ff_warp_sum(ah[q], al[q]);
     if (lane == 0) {
       s_red[warp][q][0] = ah[q];
       s_red[warp][q][1] = al[q];

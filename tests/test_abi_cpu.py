@@ -67,3 +67,15 @@ def test_workspace_size_and_rejections(lib):
     assert lib.workspace_bytes(bad) == 0
     p.n_sub = 2
     assert lib.workspace_bytes(p) == 0
+
+
+def test_init_rejects_invalid_parameters_without_a_gpu(lib):
+    import ctypes as C
+    p = lib.default_params(2, 64)  # nx below the minimum
+    h = C.c_void_p()
+    st = lib.lib().hlb_init(C.byref(h), C.byref(p), C.c_void_p(256), 1 << 20, None)
+    assert st == lib.HLB_EINVAL and not h.value
+    q = lib.default_params(64, 64)
+    q.n_sub = 3
+    assert lib.lib().hlb_init(C.byref(h), C.byref(q), C.c_void_p(256), 1 << 30, None) == lib.HLB_EINVAL
+    assert lib.lib().hlb_strerror(lib.HLB_EUNSTABLE).decode().startswith("device error word")

@@ -104,3 +104,31 @@ def test_autotune_picks_a_variant_and_keeps_results(coex):
         for x, y in zip(a.read(i), b.read(i)):
             x, y = x.cpu().numpy(), y.cpu().numpy()
             assert np.abs(x - y).max() <= 1e-6 * max(np.abs(y).max(), 1e-30)
+
+
+def test_nonfinite_input_is_reported_and_blocks_steps(coex):
+    """A NaN injected on the host into the initial temperature sets the device
+    error word: hlb_diag returns HLB_EUNSTABLE and further steps HLB_ESTATE
+    (no GPU fault, the context stays usable)."""
+    import torch
+    from paper_1812_10375_gb300 import hlb
+    from paper_1812_10375_gb300.config import params_for
+    case = ragged_case()
+    p, Tc = params_for(case, rho_l=coex["rho_l"], rho_v=coex["rho_v"])
+    d = hlb.Domain(p)
+    rho0, T0 = wl.initial_fields(case, coex["rho_l"], coex["rho_v"], Tc)
+    T0[20, 10] = np.nan
+    d.set_fields(torch.tensor(rho0, dtype=torch.float32, device="cuda"),
+                 torch.tensor(T0, dtype=torch.float32, device="cuda"))
+    d.step(3)
+    with pytest.raises(hlb.HlbError) as e:
+        d.diag()
+    assert e.value.status == hlb.HLB_EUNSTABLE
+    assert d.diag(check_flags=False).error_flags & 1
+    with pytest.raises(hlb.HlbError) as e2:
+        d.step(1)
+    assert e2.value.status == hlb.HLB_ESTATE
+    # the context is still usable: a fresh domain steps normally
+    ok = gpu_domain(case, coex)
+    ok.step(5)
+    assert ok.diag().error_flags == 0
