@@ -267,8 +267,14 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   const int x0 = bx * TX, y0 = by * TY;
   const int tid = threadIdx.x;
   const int i = tid & (FW - 1), jp = tid >> 6;
-  const int jlo = max(0, H - y0);
-  const int jhi = min(FH - 1, ny - 1 - y0 + H);
+  // Frame rows above the lattice's top row (gy >= ny) hold copies of that row
+  // (the zero-gradient ghost of an open top; unused above a top wall), so
+  // every stencil reads its north and south neighbours at fixed offsets.
+  const int jtop = ny - 1 - y0 + H;  // frame row of gy = ny - 1
+  const bool has_ghost = jtop < FH - 1;
+  auto fill_ghost = [&](float* a) {
+    for (int j = jtop + 1 + jp; j < FH; j += NPH) a[j * FW + i] = a[jtop * FW + i];
+  };
   const int gxu = x0 - H + i;
   const int gx = wrapx(gxu, nx);
   const int xm = gx == 0 ? nx - 1 : gx - 1;
@@ -323,6 +329,12 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
     }
   }
   __syncthreads();
+  if (has_ghost) {
+    fill_ghost(sT0);
+    fill_ghost(sRho);
+    fill_ghost(sPsi);
+    __syncthreads();
+  }
 
   // ---- pass B (ring 4): forces, velocity, conductivity; collide the tile
 #pragma unroll 1
@@ -339,7 +351,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
       continue;
     }
     const float psi = sPsi[idx], rho = sRho[idx];
-    const int js = max(j - 1, jlo), jn = min(j + 1, jhi);
+    const int js = j - 1, jn = j + 1;
     const bool sol_s = g.solid_row(y0 - H + js);
     const bool sol_n = g.solid_row(y0 - H + jn);
     // Eq. (6); a solid neighbour carries psi(x)
@@ -381,6 +393,12 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
     }
   }
   __syncthreads();
+  if (has_ghost) {
+    fill_ghost(sUx);
+    fill_ghost(sUy);
+    fill_ghost(sLam);
+    __syncthreads();
+  }
 
   // ---- pass C: face conductivities (Eq. 25) on ring 4, coefficients on ring 3
 #pragma unroll 1
@@ -396,7 +414,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
       sLae[idx] = 2.f * lam * le / (lam + le);
     }
     if (j + 1 < H + TY + 4) {
-      const float ln = sLam[min(j + 1, jhi) * FW + i];
+      const float ln = sLam[idx + FW];
       sLan[idx] = 2.f * lam * ln / (lam + ln);
     }
     if (j < H - 3 || j >= H + TY + 3 || i < H - 3 || i >= H + TX + 3) continue;
@@ -406,7 +424,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
       sBs[idx] = 0.f;
       continue;
     }
-    const int js = max(j - 1, jlo), jn = min(j + 1, jhi);
+    const int js = j - 1, jn = j + 1;
     const float rho = sRho[idx];
     const float ircv = 1.f / (rho * A.cv);
     // div u with the isotropic gradient of Eq. (19)
@@ -432,7 +450,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   float acc[NJ];
 #pragma unroll
   for (int m = 0; m < NJ; ++m) acc[m] = 0.f;
-#pragma unroll 1
+#pragma unroll
   for (int k = 1; k <= 4; ++k) {
     const float* Tc = k == 1 ? sT0 : (k == 3 ? sTb : sTa);
     float* Tn = k == 1 ? sTa : (k == 2 ? sTb : sTa);
@@ -447,7 +465,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
       if (j < H - r || j >= H + TY + r || gy < 0 || gy >= ny) continue;
       if (i < H - r || i >= H + TX + r) continue;
       const int idx = j * FW + i;
-      const int js = max(j - 1, jlo), jn = min(j + 1, jhi);
+      const int js = j - 1, jn = j + 1;
       const float Tp = Tc[idx];
       float hk = 0.f;
       if (!g.dirichlet_row(gy)) {
@@ -483,6 +501,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
       if (k < 4) Tn[idx] = sT0[idx] + cnext * hk;
     }
     __syncthreads();
+    if (k < 4 && has_ghost) {
+      fill_ghost(Tn);
+      __syncthreads();
+    }
   }
 
   // ---- per-block partials: compensated FP32 through warp and block, FP64 at the end
