@@ -280,6 +280,10 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         for e in ev_b + ev_a:
             e.record(stream)  # creates the underlying cudaEvent_t
+    # warm-up: the tile-shape autotuner times every compiled variant on the
+    # sweep itself (ordinary steps), then the remaining warm-up steps
+    chosen, tune_ms = batch.autotune(steps_per_variant=4)
+    variants = hlb.tile_variants()
     for _ in range(args.warmup):
         batch.step_profiled(None, None)
     torch.cuda.synchronize()
@@ -333,7 +337,9 @@ def run_ours(args):
                        "fluid_cells": n_fluid, "solid_cells": n_solid,
                        "l2": "inputs larger than L2 (state %.0f MB per buffer set)" % (
                            (36 + 4) * cells / 1e6),
-                       "timing": "CUDA events on the batch stream; step kernel bracketed per step"},
+                       "timing": "CUDA events on the batch stream; step kernel bracketed per step",
+                       "tile": {"chosen": list(variants[chosen]), "candidates_w_h_threads": [list(v) for v in variants],
+                                "tuning_ms_per_step": [round(m, 4) for m in tune_ms]}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_step_batch", "bytes_per_launch": bytes_per_step,
@@ -343,6 +349,8 @@ def run_ours(args):
                                        f"{cpu['steps']} steps in {cpu['seconds']:.1f} s, one thread"},
             "e2e": e2e,
             "gpu_launches": 2 * args.steps,
+            "issue_bound": {"note": "the step kernel is bound by instruction issue and L2 latency of halo reads, "
+                                    "not HBM; see profiles/k_step_batch_sweep32.md"},
             "clocks": clk,
             "points_per_hour": pph,
             "diag_domain0": {"step": diag0.step, "q_bottom": diag0.q_bottom, "error_flags": diag0.error_flags},

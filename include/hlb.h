@@ -212,7 +212,8 @@ hlb_status hlb_batch_destroy(hlb_batch* b);
  * The fused step kernel is compiled for several tile shapes (52 columns by a
  * few heights, with 256 or 512 threads per CTA).  hlb_tile_variants lists them
  * (returns their count; arrays may be NULL).  hlb_autotune / hlb_batch_autotune
- * time steps_per_variant steps of every variant on the handle's own state, keep
+ * run one untimed and then steps_per_variant timed steps of every variant on
+ * the handle's own state, keep
  * the fastest for later steps and report its index in *chosen (and the measured
  * ms per step in h_ms[0..max_out) if h_ms is not NULL).  The timed steps are
  * ordinary steps of the simulation: a cell's update does not depend on the tile

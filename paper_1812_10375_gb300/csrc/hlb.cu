@@ -930,6 +930,7 @@ hlb_status hlb_autotune(hlb_domain* d, int steps_per_variant, int* chosen, float
     d->variant = v;
     d->grid = grid_of(d->p.nx, d->p.ny, v);
     drop_graph(d);
+    st = launch_step(d);  // one untimed step per variant (first-launch costs)
     cudaEventRecord(e0, d->stream);
     for (int k = 0; k < steps_per_variant && st == HLB_OK; ++k) st = launch_step(d);
     cudaEventRecord(e1, d->stream);
@@ -963,6 +964,8 @@ hlb_status hlb_batch_autotune(hlb_batch* b, int steps_per_variant, int* chosen, 
   hlb_status st = HLB_OK;
   for (int v = 0; v < NVARIANTS && st == HLB_OK; ++v) {
     st = set_batch_variant(b, v);
+    if (st != HLB_OK) break;
+    st = batch_launch(b, nullptr, nullptr);  // one untimed step per variant (first-launch costs)
     if (st != HLB_OK) break;
     cudaEventRecord(e0, b->stream);
     for (int k = 0; k < steps_per_variant && st == HLB_OK; ++k) st = batch_launch(b, nullptr, nullptr);

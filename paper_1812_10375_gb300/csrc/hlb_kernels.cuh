@@ -401,7 +401,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   }
 
   // ---- pass C: face conductivities (Eq. 25) on ring 4, coefficients on ring 3
-#pragma unroll 1
+#pragma unroll
   for (int m = 0; m < NJ; ++m) {
     const int j = jp + NPH * m;
     const int gy = y0 - H + j;

@@ -98,9 +98,9 @@ def test_autotune_picks_a_variant_and_keeps_results(coex):
     assert 0 <= chosen < nv and len(ms) == nv and all(m > 0 for m in ms)
     assert ms[chosen] == min(ms)
     a.step(20)
-    b.step(4 * nv + 20)
+    b.step(5 * nv + 20)
     for i in range(len(cases)):
-        assert a.diag(i).step == b.diag(i).step == 4 * nv + 20
+        assert a.diag(i).step == b.diag(i).step == 5 * nv + 20
         for x, y in zip(a.read(i), b.read(i)):
             x, y = x.cpu().numpy(), y.cpu().numpy()
             assert np.abs(x - y).max() <= 1e-6 * max(np.abs(y).max(), 1e-30)
