@@ -39,18 +39,21 @@ BYTES_FLUID = 80  # f read 36 + f write 36 + T read 4 + T write 4
 BYTES_SOLID = 8   # T read + write (no populations in solid rows)
 
 
+KERNEL_SOURCES = ("hlb_internal.cuh", "hlb_kernels.cuh")  # the step kernel's device code
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1812_10375_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    for fn in KERNEL_SOURCES:
         with open(os.path.join(csrc, fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def read_traffic():
+def read_traffic(tile):
     """DRAM bytes per launch of the step kernel from the committed ncu summary, if it
-    was taken on the current kernel source."""
+    was taken on the current kernel source and the same tile variant."""
     path = os.path.join(ROOT, "profiles", "k_step_batch_sweep32.md")
     if not os.path.exists(path):
         return None
@@ -61,6 +64,8 @@ def read_traffic():
                 k, v = line[2:].split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    if vals.get("tile_variant") != "x".join(str(t) for t in tile):
         return None
     try:
         return float(vals["dram_bytes_per_launch_full_sweep"])
@@ -85,7 +90,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
             return
@@ -281,9 +286,14 @@ def run_ours(args):
         for e in ev_b + ev_a:
             e.record(stream)  # creates the underlying cudaEvent_t
     # warm-up: the tile-shape autotuner times every compiled variant on the
-    # sweep itself (ordinary steps), then the remaining warm-up steps
-    chosen, tune_ms = batch.autotune(steps_per_variant=4)
+    # sweep itself (ordinary steps), then the remaining warm-up steps; a fixed
+    # --tile-variant skips the tuning (profiler runs, where tuning times are distorted)
     variants = hlb.tile_variants()
+    if args.tile_variant is None:
+        chosen, tune_ms = batch.autotune(steps_per_variant=4)
+    else:
+        chosen, tune_ms = args.tile_variant, []
+        batch.set_tile_variant(chosen)
     for _ in range(args.warmup):
         batch.step_profiled(None, None)
     torch.cuda.synchronize()
@@ -324,7 +334,7 @@ def run_ours(args):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
     achieved = bytes_per_step / (kern_avg_ms * 1e-3) / 1e9
-    traffic = read_traffic()
+    traffic = read_traffic(variants[chosen])
 
     line = None
     if rank == 0:
@@ -456,9 +466,11 @@ def points_per_hour(hlb, plist, fields, cases, steps=400, full_steps=40000):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--tile-variant", type=int, default=None,
+                    help="index into the compiled tile variants; default: autotune during warm-up")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -223,6 +223,13 @@ int hlb_tile_variants(int* h_tile_w, int* h_tile_h, int* h_threads, int max_out)
 hlb_status hlb_autotune(hlb_domain* d, int steps_per_variant, int* chosen, float* h_ms, int max_out);
 hlb_status hlb_batch_autotune(hlb_batch* b, int steps_per_variant, int* chosen, float* h_ms, int max_out);
 
+/* Select tile variant v (0 <= v < hlb_tile_variants(...)) for later steps
+ * without timing anything, e.g. to reproduce a launch configuration under a
+ * profiler.  HLB_EINVAL for a NULL handle or v out of range.  Fields advance
+ * identically under every variant. */
+hlb_status hlb_set_tile_variant(hlb_domain* d, int v);
+hlb_status hlb_batch_set_tile_variant(hlb_batch* b, int v);
+
 /* ------------------------------------------------------- no-allocation step
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory (a plug-in inside an application that owns

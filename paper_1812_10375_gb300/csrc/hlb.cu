@@ -987,6 +987,19 @@ hlb_status hlb_batch_autotune(hlb_batch* b, int steps_per_variant, int* chosen, 
   return st != HLB_OK ? st : st2;
 }
 
+hlb_status hlb_set_tile_variant(hlb_domain* d, int v) {
+  if (!d || v < 0 || v >= NVARIANTS) return HLB_EINVAL;
+  d->variant = v;
+  d->grid = grid_of(d->p.nx, d->p.ny, v);
+  drop_graph(d);
+  return HLB_OK;
+}
+
+hlb_status hlb_batch_set_tile_variant(hlb_batch* b, int v) {
+  if (!b || v < 0 || v >= NVARIANTS) return HLB_EINVAL;
+  return set_batch_variant(b, v);
+}
+
 int hlb_tile_variants(int* h_tile_w, int* h_tile_h, int* h_threads, int max_out) {
   for (int v = 0; v < NVARIANTS && v < max_out; ++v) {
     if (h_tile_w) h_tile_w[v] = TILE_X;

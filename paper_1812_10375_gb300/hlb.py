@@ -85,6 +85,8 @@ def lib() -> C.CDLL:
             "hlb_tile_variants": (C.c_int, [P(C.c_int), P(C.c_int), P(C.c_int), C.c_int]),
             "hlb_autotune": (st, [vp, C.c_int, P(C.c_int), P(C.c_float), C.c_int]),
             "hlb_batch_autotune": (st, [vp, C.c_int, P(C.c_int), P(C.c_float), C.c_int]),
+            "hlb_set_tile_variant": (st, [vp, C.c_int]),
+            "hlb_batch_set_tile_variant": (st, [vp, C.c_int]),
             "hlb_step_static": (st, [P(hlb_params), C.c_int, P(hlb_site), vp, vp, vp, vp, vp, vp,
                                      C.c_double, C.c_double, P(hlb_diag_record), vp]),
         }
@@ -235,6 +237,10 @@ class Domain:
         """Time every compiled tile variant on this domain and keep the fastest."""
         return _autotune(lib().hlb_autotune, self._h, steps_per_variant, self.stream)
 
+    def set_tile_variant(self, v):
+        """Use compiled tile variant v (an index into tile_variants()) for later steps."""
+        check("hlb_set_tile_variant", lib().hlb_set_tile_variant(self._h, int(v)))
+
     def close(self):
         if self._h:
             lib().hlb_destroy(self._h)
@@ -350,6 +356,10 @@ class Batch:
     def autotune(self, steps_per_variant=8):
         """Time every compiled tile variant on this batch and keep the fastest."""
         return _autotune(lib().hlb_batch_autotune, self._h, steps_per_variant, self.stream)
+
+    def set_tile_variant(self, v):
+        """Use compiled tile variant v (an index into tile_variants()) for later steps."""
+        check("hlb_batch_set_tile_variant", lib().hlb_batch_set_tile_variant(self._h, int(v)))
 
     def close(self):
         if self._h:

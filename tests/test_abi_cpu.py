@@ -79,3 +79,13 @@ def test_init_rejects_invalid_parameters_without_a_gpu(lib):
     q.n_sub = 3
     assert lib.lib().hlb_init(C.byref(h), C.byref(q), C.c_void_p(256), 1 << 30, None) == lib.HLB_EINVAL
     assert lib.lib().hlb_strerror(lib.HLB_EUNSTABLE).decode().startswith("device error word")
+
+
+def test_tile_variant_entry_points_reject_bad_arguments(lib):
+    import ctypes as C
+    n = lib.lib().hlb_tile_variants(None, None, None, 0)
+    assert n >= 1 and len(lib.tile_variants()) == n
+    L = lib.lib()
+    assert L.hlb_set_tile_variant(None, 0) == lib.HLB_EINVAL
+    assert L.hlb_batch_set_tile_variant(None, 0) == lib.HLB_EINVAL
+    assert L.hlb_autotune(None, 4, None, None, 0) == lib.HLB_EINVAL

@@ -106,6 +106,31 @@ def test_autotune_picks_a_variant_and_keeps_results(coex):
             assert np.abs(x - y).max() <= 1e-6 * max(np.abs(y).max(), 1e-30)
 
 
+def test_set_tile_variant_keeps_fields(coex):
+    """Each compiled tile variant, selected directly, advances the fields like
+    the default one (the tile shape changes only the order of the FP64 partial
+    sums of the domain-mean density)."""
+    from paper_1812_10375_gb300 import hlb
+    cases = _cases()
+    ref = _batch(cases, coex)
+    ref.step(9)
+    nv = len(hlb.tile_variants())
+    for v in range(nv):
+        b = _batch(cases, coex)
+        b.set_tile_variant(v)
+        b.step(4)
+        b.set_tile_variant((v + 1) % nv)
+        b.step(5)
+        for i in range(len(cases)):
+            assert b.diag(i).step == 9
+            for x, y in zip(b.read(i), ref.read(i)):
+                x, y = x.cpu().numpy(), y.cpu().numpy()
+                assert np.abs(x - y).max() <= 1e-6 * max(np.abs(y).max(), 1e-30)
+        with pytest.raises(hlb.HlbError):
+            b.set_tile_variant(nv)
+        b.close()
+
+
 def test_nonfinite_input_is_reported_and_blocks_steps(coex):
     """A NaN injected on the host into the initial temperature sets the device
     error word: hlb_diag returns HLB_EUNSTABLE and further steps HLB_ESTATE
