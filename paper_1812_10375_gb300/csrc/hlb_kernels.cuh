@@ -67,17 +67,17 @@ __device__ __forceinline__ float pr_psi2(const StepArgs& A, float rho, float T) 
 // open top row from above are the rest equilibrium at rho_v (constant density)
 // or the convective-outlet update with the lagged velocity U (Uc = U / (1 + U)).
 // D2Q9 order: 0 rest, 1 (+x), 2 (+y), 3 (-x), 4 (-y), 5 (+x+y), 6 (-x+y), 7 (-x-y), 8 (+x-y).
-__device__ __forceinline__ void pull(const StepArgs& A, const Geo& g, int x, int xm, int xp, int y, float Uc,
-                                     float f[9]) {
+// bb_s / sol_n: the rows below / above y are solid.
+__device__ __forceinline__ void pull(const StepArgs& A, const Geo& g, int x, int xm, int xp, int y, bool bb_s,
+                                     bool sol_n, float Uc, float f[9]) {
   const int nx = g.nx;
   const int P = (int)A.plane;  // nx * ny < 2^31 (checked at init)
   const float* __restrict__ F = A.f_in;
   const int r0 = y * nx;
   const int rs = r0 - nx;
   const int rn = r0 + nx;
-  const bool bb_s = g.solid_row(y - 1);
   const bool open_n = g.top_open && y == g.ny - 1;
-  const bool bb_n = !open_n && g.solid_row(y + 1);
+  const bool bb_n = !open_n && sol_n;
   f[0] = __ldg(F + r0 + x);
   f[1] = __ldg(F + 1 * P + r0 + xm);
   f[3] = __ldg(F + 3 * P + r0 + xp);
@@ -231,10 +231,17 @@ __device__ __forceinline__ void ff_warp_sum(float& hi, float& lo) {
 constexpr int FRAME_W = 64;
 constexpr int TILE_W = FRAME_W - 2 * HALO;
 
+// Ten frame arrays; during passes A and B the last five of them (and a tail
+// beyond them where needed) hold the tile's post-streaming populations.
 template <int TY>
 constexpr int step_smem_floats() {
-  return 10 * FRAME_W * (TY + 2 * HALO);
+  constexpr int fn = FRAME_W * (TY + 2 * HALO);
+  constexpr int frames = 10 * fn, stash = 5 * fn + 9 * TY * TILE_W;
+  return frames > stash ? frames : stash;
 }
+
+// Bit m of byte k of a row-flag word describes the thread's m-th frame row.
+__device__ __forceinline__ bool rowbit(unsigned w, int k, int m) { return (w >> (8 * k + m)) & 1u; }
 
 // Fused coupled step on tile (bx, by).  Ring r of the tile = frame cells within
 // distance r of the tile.  `part` is the tile's slot in the partial-sum array.
@@ -243,21 +250,23 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   constexpr int H = HALO, TX = TILE_W, FW = FRAME_W, FH = TY + 2 * H, FN = FW * FH;
   constexpr int NPH = NTHREADS / FW;  // row phases
   constexpr int NJ = FH / NPH;
+  constexpr int TSZ = TY * TX;
   static_assert(NTHREADS % FW == 0, "one thread per frame column and row phase");
   static_assert(FH % NPH == 0, "frame height must be a multiple of the row phases");
+  static_assert(NJ <= 8, "row flags hold eight rows per byte");
   float* const sT0 = sm;            // T^n, ring 5
   float* const sRho = sm + FN;      // rho, ring 5      -> stage buffer Ta
   float* const sPsi = sm + 2 * FN;  // psi, ring 5      -> east-face conductivity
   float* const sUx = sm + 3 * FN;   // u, ring 4
   float* const sUy = sm + 4 * FN;
-  float* const sLam = sm + 5 * FN;  // lambda, ring 4   -> stage buffer Tb
+  float* const sTb = sm + 5 * FN;   // stage buffer Tb
   float* const sLan = sm + 6 * FN;  // north-face conductivity
   float* const sIrcv = sm + 7 * FN; // 1/(rho cv), ring 3
   float* const sAs = sm + 8 * FN;   // latent-heat source coefficients, ring 3
   float* const sBs = sm + 9 * FN;
+  float* const sF = sm + 5 * FN;    // passes A-B: populations of the tile, 9 planes of TSZ
   float* const sLae = sPsi;
   float* const sTa = sRho;
-  float* const sTb = sLam;
   __shared__ int s_err;
   __shared__ float s_lag[2];
   __shared__ float s_red[NTHREADS / 32][NPART][2];
@@ -281,6 +290,29 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   const int xp = gx == nx - 1 ? 0 : gx + 1;
   const float gw = __ldg(A.Gw + gx);
   const bool own_col = i >= H && i < H + TX && gxu < nx;
+  // Row flags of the thread's frame rows j = jp + NPH m for passes A and B,
+  // built once.  rf byte 0: ring 4; byte 1: ring 5 (frame cells within that
+  // distance of the tile, in the lattice rows); byte 2: an output cell of this
+  // tile; byte 3: a row that carries a diagnostic (gy = 1, W, ny - 2, ny - 1).
+  // fl byte 0: solid row; 1: Dirichlet row; 2: row below solid; 3: row above
+  // solid (the row index clamped to the lattice, as the ghost rows are).
+  unsigned rf = 0, fl = 0;
+  const int di = max(max(H - i, i - (H + TX - 1)), 0);
+#pragma unroll
+  for (int m = 0; m < NJ; ++m) {
+    const int j = jp + NPH * m;
+    const int gy = y0 - H + j;
+    const bool inlat = gy >= 0 && gy < ny;
+    const int d = max(di, max(max(H - j, j - (H + TY - 1)), 0));  // distance from the tile
+    if (inlat && d <= 4) rf |= 1u << m;
+    if (inlat && d <= 5) rf |= 1u << (8 + m);
+    if (inlat && own_col && d == 0) rf |= 1u << (16 + m);
+    if (gy == 1 || gy == A.W || gy == ny - 2 || gy == ny - 1) rf |= 1u << (24 + m);
+    if (g.solid_row(gy < ny ? gy : ny - 1)) fl |= 1u << m;
+    if (g.dirichlet_row(gy)) fl |= 1u << (8 + m);
+    if (g.solid_row(gy - 1)) fl |= 1u << (16 + m);
+    if (g.solid_row(gy + 1 < ny ? gy + 1 : ny - 1)) fl |= 1u << (24 + m);
+  }
   if (tid == 0) {
     s_err = 0;
     s_lag[0] = (float)A.state->Uc;
@@ -296,23 +328,24 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
 #pragma unroll
   for (int q = 0; q < NPART; ++q) ah[q] = al[q] = 0.f;
 
-  // ---- pass A (ring 5): T^n, rho and psi
-#pragma unroll 1
-  for (int m = 0; m < NJ; ++m) {
+  // ---- pass A (ring 5): T^n, rho and psi; the tile's own populations are stashed.
+  // This pass waits on L2 and HBM: rows go in pairs whose loads are all issued
+  // before either row is used, which doubles the loads in flight per thread.
+  auto fetch = [&](int m, float f[9]) -> float {
+    const int gy = y0 - H + jp + NPH * m;
+    const float T = rowbit(fl, 1, m) ? (gy == 0 ? A.T_bottom : A.T_top) : __ldg(A.T_in + gy * nx + gx);
+    if (!rowbit(fl, 0, m)) pull(A, g, gx, xm, xp, gy, rowbit(fl, 2, m), rowbit(fl, 3, m), Uc, f);
+    return T;
+  };
+  auto settle = [&](int m, const float f[9], float T) {
     const int j = jp + NPH * m;
-    const int gy = y0 - H + j;
-    if (j < H - 5 || j >= H + TY + 5 || gy < 0 || gy >= ny) continue;
-    if (i < H - 5 || i >= H + TX + 5) continue;
     const int idx = j * FW + i;
-    const float T = g.dirichlet_row(gy) ? (gy == 0 ? A.T_bottom : A.T_top) : __ldg(A.T_in + gy * nx + gx);
     sT0[idx] = T;
-    if (g.solid_row(gy)) {
+    if (rowbit(fl, 0, m)) {  // solid row: no populations
       sRho[idx] = 0.f;
       sPsi[idx] = 0.f;
-      continue;
+      return;
     }
-    float f[9];
-    pull(A, g, gx, xm, xp, gy, Uc, f);
     const float rho = A.rho_ref + sum9(f);
     float p2 = pr_psi2(A, rho, A.eos_T_fixed ? A.Ts : T);
     if (!(p2 >= 0.f)) {
@@ -323,9 +356,30 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
     sPsi[idx] = sqrtf(p2);
     // momentum sum e_i f_i of ring-4 cells, parked in the velocity arrays
     // (pass B replaces it in place by u, so halo cells need no second pull)
-    if (j >= H - 4 && j < H + TY + 4 && i >= H - 4 && i < H + TX + 4) {
+    if (rowbit(rf, 0, m)) {
       sUx[idx] = (f[1] - f[3]) + ((f[5] - f[6]) - (f[7] - f[8]));
       sUy[idx] = (f[2] - f[4]) + ((f[5] + f[6]) - (f[7] + f[8]));
+    }
+    if (rowbit(rf, 2, m)) {
+      const int c = (j - H) * TX + (i - H);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) sF[q * TSZ + c] = f[q];
+    }
+  };
+#pragma unroll 1
+  for (unsigned mm = (rf >> 8) & 0xffu; mm;) {
+    const int m1 = __ffs(mm) - 1;
+    mm &= mm - 1;
+    float f1[9], f2[9];
+    const float T1 = fetch(m1, f1);
+    if (mm) {
+      const int m2 = __ffs(mm) - 1;
+      mm &= mm - 1;
+      const float T2 = fetch(m2, f2);
+      settle(m1, f1, T1);
+      settle(m2, f2, T2);
+    } else {
+      settle(m1, f1, T1);
     }
   }
   __syncthreads();
@@ -336,24 +390,21 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
     __syncthreads();
   }
 
-  // ---- pass B (ring 4): forces, velocity, conductivity; collide the tile
+  // ---- pass B (ring 4): forces and velocity; collide the tile
 #pragma unroll 1
-  for (int m = 0; m < NJ; ++m) {
+  for (unsigned mm = rf & 0xffu; mm; mm &= mm - 1) {
+    const int m = __ffs(mm) - 1;
     const int j = jp + NPH * m;
-    const int gy = y0 - H + j;
-    if (j < H - 4 || j >= H + TY + 4 || gy < 0 || gy >= ny) continue;
-    if (i < H - 4 || i >= H + TX + 4) continue;
     const int idx = j * FW + i;
-    if (g.solid_row(gy)) {
+    if (rowbit(fl, 0, m)) {
       sUx[idx] = 0.f;
       sUy[idx] = 0.f;
-      sLam[idx] = A.lambda_w;
       continue;
     }
     const float psi = sPsi[idx], rho = sRho[idx];
     const int js = j - 1, jn = j + 1;
-    const bool sol_s = g.solid_row(y0 - H + js);
-    const bool sol_n = g.solid_row(y0 - H + jn);
+    const bool sol_s = rowbit(fl, 2, m);
+    const bool sol_n = rowbit(fl, 3, m);
     // Eq. (6); a solid neighbour carries psi(x)
     const float pE = sPsi[idx + 1], pW = sPsi[idx - 1];
     const float pN = sol_n ? psi : sPsi[jn * FW + i];
@@ -376,49 +427,69 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
     const float uy = (sUy[idx] + 0.5f * Fy) * irho;
     sUx[idx] = ux;
     sUy[idx] = uy;
-    sLam[idx] = rho * A.cvk;
-    if (own_col && j >= H && j < H + TY) {
+    if (rowbit(rf, 2, m)) {
+      const int gy = y0 - H + j;
+      const int c = (j - H) * TX + (i - H);
       float f[9];
-      pull(A, g, gx, xm, xp, gy, Uc, f);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) f[q] = sF[q * TSZ + c];
       const float fsum = collide_store(A, f, rho, ux, uy, Fx, Fy, A.G * A.G * (sx * sx + sy * sy), gy * nx + gx);
       if (nonfinite(fsum)) err |= ERR_NONFINITE;
       ff_add(ah[P_MASS], al[P_MASS], rho);
-      if (gy == A.W && rho < A.rho_mid) ff_add(ah[P_VCOV], al[P_VCOV], 1.f);
-      if (gy == ny - 2) ff_add(ah[P_UTOP], al[P_UTOP], uy);
-      if (A.top_bc == TOP_CONVECTIVE && gy == ny - 1) {
-        A.ftop_out[gx] = f[4];
-        A.ftop_out[nx + gx] = f[7];
-        A.ftop_out[2 * nx + gx] = f[8];
+      if (rowbit(rf, 3, m)) {
+        if (gy == A.W && rho < A.rho_mid) ff_add(ah[P_VCOV], al[P_VCOV], 1.f);
+        if (gy == ny - 2) ff_add(ah[P_UTOP], al[P_UTOP], uy);
+        if (A.top_bc == TOP_CONVECTIVE && gy == ny - 1) {
+          A.ftop_out[gx] = f[4];
+          A.ftop_out[nx + gx] = f[7];
+          A.ftop_out[2 * nx + gx] = f[8];
+        }
       }
     }
   }
+  // the pass-B partial sums are complete: reduce them over the warp now so that
+  // their registers are free during the energy stages
+  const int lane = tid & 31, warp = tid >> 5;
+  auto warp_flush = [&](int q) {
+    // wall- and top-row quantities are zero in most warps: skip their reduction there
+    if (__any_sync(0xffffffffu, ah[q] != 0.f || al[q] != 0.f)) ff_warp_sum(ah[q], al[q]);
+    if (lane == 0) {
+      s_red[warp][q][0] = ah[q];
+      s_red[warp][q][1] = al[q];
+    }
+  };
+  warp_flush(P_MASS);
+  warp_flush(P_VCOV);
+  warp_flush(P_UTOP);
   __syncthreads();
   if (has_ghost) {
     fill_ghost(sUx);
     fill_ghost(sUy);
-    fill_ghost(sLam);
     __syncthreads();
   }
 
-  // ---- pass C: face conductivities (Eq. 25) on ring 4, coefficients on ring 3
+  // ---- pass C: face conductivities (Eq. 25) on ring 4, coefficients on ring 3;
+  // lambda = rho cv k in the fluid (Section 2.2), lambda_w in solid rows
+  const float lam_w = A.lambda_w, cvk = A.cvk;
 #pragma unroll
   for (int m = 0; m < NJ; ++m) {
     const int j = jp + NPH * m;
-    const int gy = y0 - H + j;
+    const int gy = y0 - H + j;  // (row tests as in the stages)
     if (j < H - 4 || j >= H + TY + 4 || gy < 0 || gy >= ny) continue;
     if (i < H - 4 || i >= H + TX + 4) continue;
     const int idx = j * FW + i;
-    const float lam = sLam[idx];
+    const bool solid = g.solid_row(gy);
+    const float lam = solid ? lam_w : sRho[idx] * cvk;
     if (i + 1 < H + TX + 4) {
-      const float le = sLam[idx + 1];
+      const float le = solid ? lam_w : sRho[idx + 1] * cvk;
       sLae[idx] = 2.f * lam * le / (lam + le);
     }
     if (j + 1 < H + TY + 4) {
-      const float ln = sLam[idx + FW];
+      const float ln = g.solid_row(gy + 1 < ny ? gy + 1 : ny - 1) ? lam_w : sRho[idx + FW] * cvk;
       sLan[idx] = 2.f * lam * ln / (lam + ln);
     }
     if (j < H - 3 || j >= H + TY + 3 || i < H - 3 || i >= H + TX + 3) continue;
-    if (g.solid_row(gy)) {
+    if (solid) {
       sIrcv[idx] = A.inv_rcv_w;
       sAs[idx] = 0.f;
       sBs[idx] = 0.f;
@@ -445,7 +516,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   }
   __syncthreads();
 
-  // ---- RK4 stages (Eq. 18): stage k on ring 4-k; h1 + 2 h2 + 2 h3 kept in registers
+  // ---- RK4 stages (Eq. 18): stage k on ring 4-k (stage 4 on the output cells
+  // only); h1 + 2 h2 + 2 h3 kept in registers
   const float dt = A.dt;
   float acc[NJ];
 #pragma unroll
@@ -458,12 +530,15 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
     const float wk = (k == 1 || k == 4) ? dt * (1.f / 6.f) : dt * (2.f / 6.f);
     const float wacc = (k == 1) ? 1.f : 2.f;
     const int r = 4 - k;
+    // (tested per row rather than through the row flags: these tests use only
+    // warp-uniform values and keep the stages within the register budget)
 #pragma unroll
     for (int m = 0; m < NJ; ++m) {
       const int j = jp + NPH * m;
       const int gy = y0 - H + j;
       if (j < H - r || j >= H + TY + r || gy < 0 || gy >= ny) continue;
       if (i < H - r || i >= H + TX + r) continue;
+      if (k == 4 && !own_col) continue;
       const int idx = j * FW + i;
       const int js = j - 1, jn = j + 1;
       const float Tp = Tc[idx];
@@ -508,16 +583,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   }
 
   // ---- per-block partials: compensated FP32 through warp and block, FP64 at the end
-  const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-  for (int q = 0; q < NPART; ++q) {
-    // wall- and top-row quantities are zero in most warps: skip their reduction there
-    if (__any_sync(0xffffffffu, ah[q] != 0.f || al[q] != 0.f)) ff_warp_sum(ah[q], al[q]);
-    if (lane == 0) {
-      s_red[warp][q][0] = ah[q];
-      s_red[warp][q][1] = al[q];
-    }
-  }
+  warp_flush(P_ENERGY);
+  warp_flush(P_QB);
+  warp_flush(P_QT);
+  warp_flush(P_QI);
   if (err) atomicOr(&s_err, err);
   __syncthreads();
   if (tid < NPART) {
