@@ -25,7 +25,8 @@ struct Variant {
   const void* single_fn;
   const void* batch_fn;
   void (*launch_single)(dim3, size_t, cudaStream_t, const StepArgs&);
-  void (*launch_batch)(int, size_t, cudaStream_t, const StepArgs&, const DomArgs*, const int*, const int*, int);
+  void (*launch_batch)(int, size_t, cudaStream_t, const StepArgs&, const DomArgs*, const int2*, const int*,
+                       const float2*);
 };
 
 template <int TY, int NTH, int MINB>
@@ -34,8 +35,8 @@ void launch_single_v(dim3 grid, size_t smem, cudaStream_t s, const StepArgs& a) 
 }
 template <int TY, int NTH, int MINB>
 void launch_batch_v(int blocks, size_t smem, cudaStream_t s, const StepArgs& phys, const DomArgs* desc,
-                    const int* off, const int* act, int n) {
-  k_step_batch<TY, NTH, MINB><<<blocks, NTH, smem, s>>>(phys, desc, off, act, n);
+                    const int2* blk, const int* act, const float2* lag) {
+  k_step_batch<TY, NTH, MINB><<<blocks, NTH, smem, s>>>(phys, desc, blk, act, lag);
 }
 
 #define HLB_VARIANT_ENTRY(TY, NTH, MINB)                                                              \
@@ -391,8 +392,9 @@ struct hlb_batch {
   DomArgs* d_desc = nullptr;   // [2][n]: per-domain descriptors for batch parity 0 and 1
   StepArgs phys;               // model parameters shared by the batch
   ReduceArgs* d_ra = nullptr;  // [n]
-  int* d_tile_off = nullptr;   // [n + 1]
+  int2* d_blk = nullptr;       // [blocks]: (domain, tile within the domain) of each step block
   int* d_active = nullptr;     // [n]
+  float2* d_lag = nullptr;     // [n]: lagged U/(1+U) and mean density, written by the reduction
   std::vector<int> tile_off;
   std::vector<int> active;
   int total_tiles = 0;
@@ -407,20 +409,22 @@ namespace {
 
 struct BatchLayout {
   std::vector<size_t> dom_off;
-  size_t desc, ra, tile_off, active, total;
+  size_t desc, ra, blk, active, lag, total;
 };
 
 BatchLayout batch_layout(int n, const hlb_params* p) {
   BatchLayout L;
-  size_t o = 0;
+  size_t o = 0, max_blocks = 0;
   for (int i = 0; i < n; ++i) {
     L.dom_off.push_back(o);
     o += layout_of(p + i).total;
+    max_blocks += (size_t)((p[i].nx + TILE_X - 1) / TILE_X) * ((p[i].ny + MIN_TILE_Y - 1) / MIN_TILE_Y);
   }
   L.desc = o;     o += align_up(2 * (size_t)n * sizeof(DomArgs));
   L.ra = o;       o += align_up((size_t)n * sizeof(ReduceArgs));
-  L.tile_off = o; o += align_up((size_t)(n + 1) * sizeof(int));
+  L.blk = o;      o += align_up(max_blocks * sizeof(int2));
   L.active = o;   o += align_up((size_t)n * sizeof(int));
+  L.lag = o;      o += align_up((size_t)n * sizeof(float2));
   L.total = o;
   return L;
 }
@@ -463,6 +467,9 @@ StepArgs physics_of(const StepArgs& a) {
 hlb_status upload_tables(hlb_batch* b) {
   std::vector<DomArgs> desc(2 * (size_t)b->n);
   std::vector<ReduceArgs> ra(b->n);
+  std::vector<int2> blk((size_t)b->total_tiles);
+  for (int i = 0; i < b->n; ++i)
+    for (int t = b->tile_off[i]; t < b->tile_off[i + 1]; ++t) blk[t] = make_int2(i, t - b->tile_off[i]);
   for (int i = 0; i < b->n; ++i) {
     hlb_domain* d = &b->dom[i];
     desc[i] = dom_args(args_for(d, 0));
@@ -478,8 +485,8 @@ hlb_status upload_tables(hlb_batch* b) {
           cudaSuccess ||
       cudaMemcpyAsync(b->d_ra, ra.data(), ra.size() * sizeof(ReduceArgs), cudaMemcpyHostToDevice, b->stream) !=
           cudaSuccess ||
-      cudaMemcpyAsync(b->d_tile_off, b->tile_off.data(), b->tile_off.size() * sizeof(int), cudaMemcpyHostToDevice,
-                      b->stream) != cudaSuccess ||
+      cudaMemcpyAsync(b->d_blk, blk.data(), blk.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream) !=
+          cudaSuccess ||
       cudaMemcpyAsync(b->d_active, b->active.data(), b->active.size() * sizeof(int), cudaMemcpyHostToDevice,
                       b->stream) != cudaSuccess)
     return HLB_ECUDA;
@@ -489,9 +496,9 @@ hlb_status upload_tables(hlb_batch* b) {
 hlb_status batch_launch(hlb_batch* b, cudaEvent_t before, cudaEvent_t after) {
   if (before && cudaEventRecord(before, b->stream) != cudaSuccess) return HLB_ECUDA;
   VARIANTS[b->variant].launch_batch(b->total_tiles, VARIANTS[b->variant].smem, b->stream, b->phys,
-                                    b->d_desc + (size_t)b->parity * b->n, b->d_tile_off, b->d_active, b->n);
+                                    b->d_desc + (size_t)b->parity * b->n, b->d_blk, b->d_active, b->d_lag);
   if (after && cudaEventRecord(after, b->stream) != cudaSuccess) return HLB_ECUDA;
-  k_reduce_batch<<<b->n, 256, 0, b->stream>>>(b->d_ra, b->d_active, HIST_CAP);
+  k_reduce_batch<<<b->n, 256, 0, b->stream>>>(b->d_ra, b->d_active, b->d_lag, HIST_CAP);
   if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
   b->parity ^= 1;
   b->steps += 1;
@@ -781,8 +788,9 @@ hlb_status hlb_batch_init(hlb_batch** out, int n, const hlb_params* p, void* d_w
   }
   b->d_desc = (DomArgs*)(ws + L.desc);
   b->d_ra = (ReduceArgs*)(ws + L.ra);
-  b->d_tile_off = (int*)(ws + L.tile_off);
+  b->d_blk = (int2*)(ws + L.blk);
   b->d_active = (int*)(ws + L.active);
+  b->d_lag = (float2*)(ws + L.lag);
   const hlb_status st = upload_tables(b);
   if (st != HLB_OK) {
     delete b;
@@ -797,6 +805,8 @@ hlb_status hlb_batch_set_fields(hlb_batch* b, int i, const float* d_rho, const f
   // the domain joins the batch at the batch's current buffer parity
   const hlb_status st = set_fields_at(&b->dom[i], d_rho, d_T, b->parity);
   if (st != HLB_OK) return st;
+  k_lag_from_state<<<1, 32, 0, b->stream>>>(b->dom[i].state, b->d_lag + i);
+  if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
   if (!b->active[i]) {
     b->active[i] = 1;
     const int one = 1;

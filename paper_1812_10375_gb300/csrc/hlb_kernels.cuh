@@ -245,8 +245,10 @@ __device__ __forceinline__ bool rowbit(unsigned w, int k, int m) { return (w >> 
 
 // Fused coupled step on tile (bx, by).  Ring r of the tile = frame cells within
 // distance r of the tile.  `part` is the tile's slot in the partial-sum array.
+// Uc, rho_ave: the lagged outlet factor U/(1+U) and mean density of the domain.
 template <int TY, int NTHREADS>
-__device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int part, float* sm) {
+__device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int part, float* sm, float Uc,
+                                          float rho_ave) {
   constexpr int H = HALO, TX = TILE_W, FW = FRAME_W, FH = TY + 2 * H, FN = FW * FH;
   constexpr int NPH = NTHREADS / FW;  // row phases
   constexpr int NJ = FH / NPH;
@@ -268,8 +270,11 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   float* const sLae = sPsi;
   float* const sTa = sRho;
   __shared__ int s_err;
-  __shared__ float s_lag[2];
   __shared__ float s_red[NTHREADS / 32][NPART][2];
+  // Wall-flux partials (q_bottom, q_top, q_interface) per frame column as
+  // compensated (hi, lo): each lies on one lattice row, so one thread owns each
+  // entry and no register carries it through the stages.
+  __shared__ float s_q[3][2][FW];
 
   const Geo g = make_geo(A);
   const int nx = A.nx, ny = A.ny;
@@ -313,14 +318,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
     if (g.solid_row(gy - 1)) fl |= 1u << (16 + m);
     if (g.solid_row(gy + 1 < ny ? gy + 1 : ny - 1)) fl |= 1u << (24 + m);
   }
-  if (tid == 0) {
-    s_err = 0;
-    s_lag[0] = (float)A.state->Uc;
-    s_lag[1] = (float)A.state->rho_ave;
-  }
-  __syncthreads();
-  const float Uc = s_lag[0];
-  const float rho_ave = s_lag[1];
+  if (tid == 0) s_err = 0;  // read after the barriers below
+  for (int t = tid; t < 3 * 2 * FW; t += NTHREADS) (&s_q[0][0][0])[t] = 0.f;
   int err = 0;
   // Diagnostics partial sums in compensated FP32 (hi, lo); one thread converts
   // the block's six totals to FP64.
@@ -561,9 +560,15 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
         hk = kk;
       }
       if (own_col && j >= H && j < H + TY) {
-        if (gy == 1) ff_add(ah[P_QB], al[P_QB], wk * sLan[js * FW + i] * (Tc[js * FW + i] - Tp));
-        if (g.top_wall && gy == ny - 2) ff_add(ah[P_QT], al[P_QT], wk * sLan[idx] * (Tp - Tc[jn * FW + i]));
-        if (gy == A.W) ff_add(ah[P_QI], al[P_QI], wk * sLan[js * FW + i] * (Tc[js * FW + i] - Tp));
+        auto qadd = [&](int q, float x) {
+          float h = s_q[q][0][i], l = s_q[q][1][i];
+          ff_add(h, l, x);
+          s_q[q][0][i] = h;
+          s_q[q][1][i] = l;
+        };
+        if (gy == 1) qadd(0, wk * sLan[js * FW + i] * (Tc[js * FW + i] - Tp));
+        if (g.top_wall && gy == ny - 2) qadd(1, wk * sLan[idx] * (Tp - Tc[jn * FW + i]));
+        if (gy == A.W) qadd(2, wk * sLan[js * FW + i] * (Tc[js * FW + i] - Tp));
         if (k < 4) {
           acc[m] += wacc * hk;
         } else {
@@ -584,6 +589,13 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
 
   // ---- per-block partials: compensated FP32 through warp and block, FP64 at the end
   warp_flush(P_ENERGY);
+  // the wall-flux column partials enter through the first row phase's lanes
+  // (the stages' last barrier orders their smem updates before these reads)
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    ah[P_QB + q] = jp == 0 ? s_q[q][0][i] : 0.f;
+    al[P_QB + q] = jp == 0 ? s_q[q][1][i] : 0.f;
+  }
   warp_flush(P_QB);
   warp_flush(P_QT);
   warp_flush(P_QI);
@@ -601,40 +613,40 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
 template <int TY, int NTH, int MINB>
 __global__ void __launch_bounds__(NTH, MINB) k_step(const StepArgs A) {
   extern __shared__ float sm[];
-  step_tile<TY, NTH>(A, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, sm);
+  step_tile<TY, NTH>(A, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, sm, (float)A.state->Uc,
+                     (float)A.state->rho_ave);
 }
 
 // Batched step: the blocks of one launch cover the tiles of every domain of a
-// sweep.  tile_off[d] is the first block of domain d (tile_off[n] = grid size);
-// a block finds its domain by binary search, takes that domain's geometry and
-// buffers from the descriptor table and the shared model parameters from its
-// by-value argument (constant bank), and runs the same tile step.  Stopped
-// domains are skipped.
+// sweep.  blk[b] = (domain, tile within the domain) of block b; the block takes
+// that domain's geometry and buffers from the descriptor table, its lagged
+// scalars from lag[d] (U/(1+U), mean density) and the shared model parameters
+// from its by-value argument (constant bank), and runs the same tile step.
+// Stopped domains are skipped.  Two dependent rounds of small loads precede
+// the tile.
 template <int TY, int NTH, int MINB>
 __global__ void __launch_bounds__(NTH, MINB) k_step_batch(const StepArgs P, const DomArgs* __restrict__ desc,
-                                                          const int* __restrict__ tile_off,
-                                                          const int* __restrict__ active, int n) {
+                                                          const int2* __restrict__ blk,
+                                                          const int* __restrict__ active,
+                                                          const float2* __restrict__ lag) {
   extern __shared__ float sm[];
   __shared__ DomArgs sD;
-  __shared__ int s_dom;
-  const int b = blockIdx.x;
-  if (threadIdx.x == 0) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (tile_off[mid] <= b) lo = mid; else hi = mid - 1;
-    }
-    s_dom = lo;
-  }
-  __syncthreads();
-  const int d = s_dom;
-  if (!active[d]) return;
+  __shared__ int s_act;
+  __shared__ int2 s_bl;
+  __shared__ float2 s_lg;
   {
-    const int* src = reinterpret_cast<const int*>(desc + d);
+    const int2 bl = blk[blockIdx.x];
+    const int* src = reinterpret_cast<const int*>(desc + bl.x);
     int* dst = reinterpret_cast<int*>(&sD);
     for (int q = threadIdx.x; q < (int)(sizeof(DomArgs) / sizeof(int)); q += NTH) dst[q] = src[q];
+    if (threadIdx.x == NTH - 1) {
+      s_bl = bl;
+      s_act = active[bl.x];
+      s_lg = lag[bl.x];
+    }
   }
   __syncthreads();
+  if (!s_act) return;
   StepArgs A = P;
   A.nx = sD.nx;
   A.ny = sD.ny;
@@ -653,9 +665,14 @@ __global__ void __launch_bounds__(NTH, MINB) k_step_batch(const StepArgs P, cons
   A.ftop_out = sD.ftop_out;
   A.partials = sD.partials;
   A.state = sD.state;
-  const int local = b - tile_off[d];
+  const int local = s_bl.y;
   const int tx = (A.nx + TILE_W - 1) / TILE_W;
-  step_tile<TY, NTH>(A, local % tx, local / tx, local, sm);
+  step_tile<TY, NTH>(A, local % tx, local / tx, local, sm, s_lg.x, s_lg.y);
+}
+
+// The lagged scalars of a domain as the batched step reads them.
+__global__ void k_lag_from_state(const DevState* st, float2* lag) {
+  if (threadIdx.x == 0) *lag = make_float2((float)st->Uc, (float)st->rho_ave);
 }
 
 // FP64 reduction of the per-block partials (one CTA); updates the lagged
@@ -714,7 +731,7 @@ struct ReduceArgs {
 };
 
 __global__ void __launch_bounds__(256) k_reduce_batch(const ReduceArgs* __restrict__ ra,
-                                                       const int* __restrict__ active, int hist_cap) {
+                                                       const int* __restrict__ active, float2* lag, int hist_cap) {
   const int d = blockIdx.x;
   if (!active[d]) return;
   const ReduceArgs r = ra[d];
@@ -758,6 +775,7 @@ __global__ void __launch_bounds__(256) k_reduce_batch(const ReduceArgs* __restri
     st->vcov = s[P_VCOV] * r.inv_nx;
     st->vcov_sum += st->vcov;
     if (r.hist && st->hist_len < hist_cap) r.hist[st->hist_len++] = st->q_bottom;
+    lag[d] = make_float2((float)st->Uc, (float)st->rho_ave);
   }
 }
 
