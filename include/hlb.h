@@ -114,7 +114,9 @@ hlb_status hlb_eos_coexistence(const hlb_params* p, double* Tc, double* rho_l, d
                                double* h_fg);
 
 /* Device bytes one domain needs (fields double-buffered, per-block FP64 partials,
- * site table, flux history).  0 on invalid parameters. */
+ * site table, flux history).  0 on invalid parameters, which include lattices
+ * whose nine population planes would exceed 2^31 floats (about 238 million
+ * cells, e.g. 15,000 x 15,000 fits, 16,384 x 16,384 does not). */
 size_t hlb_workspace_bytes(const hlb_params* p);
 
 /* Create a domain inside the caller's device workspace (>= hlb_workspace_bytes

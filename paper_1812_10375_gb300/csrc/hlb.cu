@@ -157,6 +157,10 @@ PRHost pr_of(const hlb_params* p) {
   return e;
 }
 
+// Stride of the population planes in floats: nx ny rounded up to whole
+// 128-byte lines, so that every plane starts on a line.
+size_t plane_stride(size_t N) { return (N + 31) / 32 * 32; }
+
 bool params_valid(const hlb_params* p) {
   if (!p) return false;
   if (p->nx < 4 || p->ny < 6 || p->wall_rows < 1) return false;
@@ -170,7 +174,9 @@ bool params_valid(const hlb_params* p) {
         p->s_q > 0 && p->s_q < 2))
     return false;
   if (!(p->tau_l > 0.5 && p->tau_v > 0.5 && p->cv > 0 && p->k > 0)) return false;
-  if ((long long)p->nx * p->ny > (1LL << 31)) return false;
+  // the kernels address a cell's nine populations with 32-bit offsets (q plane + cell)
+  if (p->nx > (1 << 20) || p->ny > (1 << 20)) return false;
+  if (9 * (long long)plane_stride((size_t)p->nx * p->ny) >= (1LL << 31)) return false;
   return true;
 }
 
@@ -209,9 +215,10 @@ struct Layout {
 Layout layout_of(const hlb_params* p) {
   Layout L;
   const size_t N = (size_t)p->nx * p->ny;
+  const size_t PS = plane_stride(N);
   const size_t nblk = (size_t)((p->nx + TILE_X - 1) / TILE_X) * ((p->ny + MIN_TILE_Y - 1) / MIN_TILE_Y);
   size_t o = 0;
-  L.f = o;        o += align_up(2 * 9 * N * sizeof(float));
+  L.f = o;        o += align_up(2 * 9 * PS * sizeof(float));
   L.T = o;        o += align_up(2 * N * sizeof(float));
   L.Gw = o;       o += align_up((size_t)p->nx * sizeof(float));
   L.ftop = o;     o += align_up(2 * 3 * (size_t)p->nx * sizeof(float));
@@ -314,7 +321,7 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
 
   const size_t N = (size_t)q.nx * q.ny;
   d->f[0] = (float*)(ws + L.f);
-  d->f[1] = d->f[0] + 9 * N;
+  d->f[1] = d->f[0] + 9 * plane_stride(N);
   d->T[0] = (float*)(ws + L.T);
   d->T[1] = d->T[0] + N;
   d->Gw = (float*)(ws + L.Gw);
@@ -336,7 +343,7 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
   a.W = q.wall_rows;
   a.top_bc = q.top_bc;
   a.eos_T_fixed = q.eos_T_fixed;
-  a.plane = (long long)N;
+  a.plane = (long long)plane_stride(N);
   a.R = (float)q.R;
   a.a = (float)q.a;
   a.b = (float)q.b;

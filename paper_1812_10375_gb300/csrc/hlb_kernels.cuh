@@ -71,7 +71,7 @@ __device__ __forceinline__ float pr_psi2(const StepArgs& A, float rho, float T) 
 __device__ __forceinline__ void pull(const StepArgs& A, const Geo& g, int x, int xm, int xp, int y, bool bb_s,
                                      bool sol_n, float Uc, float f[9]) {
   const int nx = g.nx;
-  const int P = (int)A.plane;  // nx * ny < 2^31 (checked at init)
+  const int P = (int)A.plane;  // 9 planes < 2^31 floats (checked at init)
   const float* __restrict__ F = A.f_in;
   const int r0 = y * nx;
   const int rs = r0 - nx;
@@ -296,28 +296,33 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   const float gw = __ldg(A.Gw + gx);
   const bool own_col = i >= H && i < H + TX && gxu < nx;
   // Row flags of the thread's frame rows j = jp + NPH m for passes A and B,
-  // built once.  rf byte 0: ring 4; byte 1: ring 5 (frame cells within that
-  // distance of the tile, in the lattice rows); byte 2: an output cell of this
-  // tile; byte 3: a row that carries a diagnostic (gy = 1, W, ny - 2, ny - 1).
-  // fl byte 0: solid row; 1: Dirichlet row; 2: row below solid; 3: row above
-  // solid (the row index clamped to the lattice, as the ghost rows are).
-  unsigned rf = 0, fl = 0;
-  const int di = max(max(H - i, i - (H + TX - 1)), 0);
-#pragma unroll
-  for (int m = 0; m < NJ; ++m) {
-    const int j = jp + NPH * m;
-    const int gy = y0 - H + j;
-    const bool inlat = gy >= 0 && gy < ny;
-    const int d = max(di, max(max(H - j, j - (H + TY - 1)), 0));  // distance from the tile
-    if (inlat && d <= 4) rf |= 1u << m;
-    if (inlat && d <= 5) rf |= 1u << (8 + m);
-    if (inlat && own_col && d == 0) rf |= 1u << (16 + m);
-    if (gy == 1 || gy == A.W || gy == ny - 2 || gy == ny - 1) rf |= 1u << (24 + m);
-    if (g.solid_row(gy < ny ? gy : ny - 1)) fl |= 1u << m;
-    if (g.dirichlet_row(gy)) fl |= 1u << (8 + m);
-    if (g.solid_row(gy - 1)) fl |= 1u << (16 + m);
-    if (g.solid_row(gy + 1 < ny ? gy + 1 : ny - 1)) fl |= 1u << (24 + m);
-  }
+  // built once from prefix masks.  rf byte 0: a lattice row within distance 4
+  // of the tile; byte 1: within distance 5 (passes A and B evaluate every
+  // column of such rows, so their loops stay warp-uniform; columns outside the
+  // ring are never read later); byte 2: an output cell of this tile; byte 3: a
+  // row that carries a diagnostic (gy = 1, W, ny - 2, ny - 1).  fl byte 0:
+  // solid row; 1: Dirichlet row; 2: row below solid; 3: row above solid (the
+  // row index clamped to the lattice, as the ghost rows are).
+  static_assert(NPH == 4 || NPH == 8 || NPH == 16, "row phases must be a power of two");
+  constexpr int SH = NPH == 4 ? 2 : (NPH == 8 ? 3 : 4);
+  constexpr unsigned ALL = (1u << NJ) - 1u;
+  const int g0 = y0 - H + jp;  // lattice row of the thread's first frame row
+  // masks of the thread's rows with gy < v and with frame row j < v
+  auto lt = [&](int v) -> unsigned { return (1u << min(max((v - g0 + NPH - 1) >> SH, 0), NJ)) - 1u; };
+  auto ltj = [&](int v) -> unsigned { return (1u << min(max((v - jp + NPH - 1) >> SH, 0), NJ)) - 1u; };
+  auto eq = [&](int v) -> unsigned { return lt(v + 1) & ~lt(v); };
+  const unsigned lat = lt(ny) & ~lt(0);
+  const unsigned ring4 = ltj(H + TY + 4) & ~ltj(H - 4) & lat;
+  const unsigned ring5 = ltj(H + TY + 5) & ~ltj(H - 5) & lat;
+  const unsigned ownr = own_col ? ltj(H + TY) & ~ltj(H) & lat : 0u;
+  const unsigned diag = eq(1) | eq(A.W) | eq(ny - 2) | eq(ny - 1);
+  const bool tw = g.top_wall;
+  const unsigned solid = lt(A.W) | (tw ? ALL & ~lt(ny - 1) : 0u);      // solid_row(min(gy, ny - 1))
+  const unsigned dirich = eq(0) | (tw ? eq(ny - 1) : 0u);                // dirichlet_row(gy)
+  const unsigned sol_below = lt(A.W + 1) | (tw ? eq(ny) : 0u);          // solid_row(gy - 1)
+  const unsigned sol_above = lt(A.W - 1) | (tw ? ALL & ~lt(ny - 2) : 0u);  // solid_row(min(gy + 1, ny - 1))
+  const unsigned rf = ring4 | ring5 << 8 | ownr << 16 | diag << 24;
+  const unsigned fl = solid | dirich << 8 | sol_below << 16 | sol_above << 24;
   if (tid == 0) s_err = 0;  // read after the barriers below
   for (int t = tid; t < 3 * 2 * FW; t += NTHREADS) (&s_q[0][0][0])[t] = 0.f;
   int err = 0;
@@ -330,10 +335,33 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   // ---- pass A (ring 5): T^n, rho and psi; the tile's own populations are stashed.
   // This pass waits on L2 and HBM: rows go in pairs whose loads are all issued
   // before either row is used, which doubles the loads in flight per thread.
+  // interior rows (no solid row next to them, not the open top row) pull at
+  // fixed offsets from one row pointer
+  const int P = (int)A.plane;
+  const int o1 = P + xm - gx, o3 = 3 * P + xp - gx;
+  const int o2 = 2 * P - nx, o5 = 5 * P - nx + xm - gx, o6 = 6 * P - nx + xp - gx;
+  const int o4 = 4 * P + nx, o7 = 7 * P + nx + xp - gx, o8 = 8 * P + nx + xm - gx;
   auto fetch = [&](int m, float f[9]) -> float {
     const int gy = y0 - H + jp + NPH * m;
-    const float T = rowbit(fl, 1, m) ? (gy == 0 ? A.T_bottom : A.T_top) : __ldg(A.T_in + gy * nx + gx);
-    if (!rowbit(fl, 0, m)) pull(A, g, gx, xm, xp, gy, rowbit(fl, 2, m), rowbit(fl, 3, m), Uc, f);
+    const int c = gy * nx + gx;
+    const float T = rowbit(fl, 1, m) ? (gy == 0 ? A.T_bottom : A.T_top) : __ldg(A.T_in + c);
+    if (!rowbit(fl, 0, m)) {
+      const bool sol_s = rowbit(fl, 2, m), sol_n = rowbit(fl, 3, m);
+      if (!sol_s && !sol_n && !(g.top_open && gy == ny - 1)) {
+        const float* __restrict__ F = A.f_in + c;
+        f[0] = __ldg(F);
+        f[1] = __ldg(F + o1);
+        f[3] = __ldg(F + o3);
+        f[2] = __ldg(F + o2);
+        f[5] = __ldg(F + o5);
+        f[6] = __ldg(F + o6);
+        f[4] = __ldg(F + o4);
+        f[7] = __ldg(F + o7);
+        f[8] = __ldg(F + o8);
+      } else {
+        pull(A, g, gx, xm, xp, gy, sol_s, sol_n, Uc, f);
+      }
+    }
     return T;
   };
   auto settle = [&](int m, const float f[9], float T) {
@@ -467,19 +495,19 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
     __syncthreads();
   }
 
-  // ---- pass C: face conductivities (Eq. 25) on ring 4, coefficients on ring 3;
-  // lambda = rho cv k in the fluid (Section 2.2), lambda_w in solid rows
+  // ---- pass C: face conductivities (Eq. 25) on the rows of ring 4, coefficients
+  // on the rows of ring 3 (every column, as in the stages); lambda = rho cv k in
+  // the fluid (Section 2.2), lambda_w in solid rows
   const float lam_w = A.lambda_w, cvk = A.cvk;
 #pragma unroll
   for (int m = 0; m < NJ; ++m) {
     const int j = jp + NPH * m;
-    const int gy = y0 - H + j;  // (row tests as in the stages)
+    const int gy = y0 - H + j;
     if (j < H - 4 || j >= H + TY + 4 || gy < 0 || gy >= ny) continue;
-    if (i < H - 4 || i >= H + TX + 4) continue;
     const int idx = j * FW + i;
     const bool solid = g.solid_row(gy);
     const float lam = solid ? lam_w : sRho[idx] * cvk;
-    if (i + 1 < H + TX + 4) {
+    {
       const float le = solid ? lam_w : sRho[idx + 1] * cvk;
       sLae[idx] = 2.f * lam * le / (lam + le);
     }
@@ -487,7 +515,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
       const float ln = g.solid_row(gy + 1 < ny ? gy + 1 : ny - 1) ? lam_w : sRho[idx + FW] * cvk;
       sLan[idx] = 2.f * lam * ln / (lam + ln);
     }
-    if (j < H - 3 || j >= H + TY + 3 || i < H - 3 || i >= H + TX + 3) continue;
+    if (j < H - 3 || j >= H + TY + 3) continue;
     if (solid) {
       sIrcv[idx] = A.inv_rcv_w;
       sAs[idx] = 0.f;
@@ -535,9 +563,11 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
     for (int m = 0; m < NJ; ++m) {
       const int j = jp + NPH * m;
       const int gy = y0 - H + j;
+      // rows outside ring r are skipped (warp-uniform); every column of a row
+      // is evaluated (columns outside the ring are never read later), and only
+      // the tile's own cells store or accumulate
       if (j < H - r || j >= H + TY + r || gy < 0 || gy >= ny) continue;
-      if (i < H - r || i >= H + TX + r) continue;
-      if (k == 4 && !own_col) continue;
+      const bool own = own_col && j >= H && j < H + TY;
       const int idx = j * FW + i;
       const int js = j - 1, jn = j + 1;
       const float Tp = Tc[idx];
@@ -559,7 +589,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
         }
         hk = kk;
       }
-      if (own_col && j >= H && j < H + TY) {
+      if (k < 4) acc[m] += wacc * hk;
+      if (own) {
         auto qadd = [&](int q, float x) {
           float h = s_q[q][0][i], l = s_q[q][1][i];
           ff_add(h, l, x);
@@ -569,9 +600,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
         if (gy == 1) qadd(0, wk * sLan[js * FW + i] * (Tc[js * FW + i] - Tp));
         if (g.top_wall && gy == ny - 2) qadd(1, wk * sLan[idx] * (Tp - Tc[jn * FW + i]));
         if (gy == A.W) qadd(2, wk * sLan[js * FW + i] * (Tc[js * FW + i] - Tp));
-        if (k < 4) {
-          acc[m] += wacc * hk;
-        } else {
+        if (k == 4) {
           const float Tnew = sT0[idx] + dt * (1.f / 6.f) * (acc[m] + hk);
           if (nonfinite(Tnew)) err |= ERR_NONFINITE;
           A.T_out[gy * nx + gx] = Tnew;
@@ -786,9 +815,10 @@ __global__ void __launch_bounds__(256) k_init(const StepArgs A, const float* __r
                                               float* __restrict__ T, float* __restrict__ ftop_a,
                                               float* __restrict__ ftop_b) {
   const Geo g = make_geo(A);
-  const long long N = A.plane;
+  const long long N = A.plane;  // population plane stride (>= nx ny)
+  const long long NC = (long long)A.nx * A.ny;
   double mass = 0.0;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < NC; c += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(c / A.nx), x = (int)(c % A.nx);
     const bool solid = g.solid_row(y);
     const float d = solid ? 0.f : rho0[c] - A.rho_ref;
@@ -844,9 +874,10 @@ __global__ void k_init_state(const double* __restrict__ partials, int nblk, DevS
 __global__ void __launch_bounds__(256) k_read(const StepArgs A, const float* __restrict__ Tn, int zero_u,
                                               float* rho_out, float* ux_out, float* uy_out) {
   const Geo g = make_geo(A);
-  const long long N = A.plane;
+  const long long N = A.plane;  // population plane stride (>= nx ny)
+  const long long NC = (long long)A.nx * A.ny;
   const float rho_ave = (float)A.state->rho_ave_prev;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < NC; c += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(c / A.nx), x = (int)(c % A.nx);
     if (g.solid_row(y)) {
       if (rho_out) rho_out[c] = 0.f;

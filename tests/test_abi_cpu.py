@@ -67,6 +67,9 @@ def test_workspace_size_and_rejections(lib):
     assert lib.workspace_bytes(bad) == 0
     p.n_sub = 2
     assert lib.workspace_bytes(p) == 0
+    # nine population planes must stay below 2^31 floats (32-bit offsets in the kernels)
+    assert lib.workspace_bytes(lib.default_params(15000, 15000)) > 0
+    assert lib.workspace_bytes(lib.default_params(16384, 16384)) == 0
 
 
 def test_init_rejects_invalid_parameters_without_a_gpu(lib):
