@@ -39,7 +39,7 @@ BYTES_FLUID = 80  # f read 36 + f write 36 + T read 4 + T write 4
 BYTES_SOLID = 8   # T read + write (no populations in solid rows)
 
 
-KERNEL_SOURCES = ("hlb_internal.cuh", "hlb_kernels.cuh")  # the step kernel's device code
+KERNEL_SOURCES = ("hlb_internal.cuh", "hlb_kernels.cuh", "hlb_march.cuh")  # the step kernels' device code
 
 
 def kernel_source_hash() -> str:
@@ -51,10 +51,24 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def kernel_name(tile):
+    """The step kernel a tile variant launches: row-marching variants report a
+    tile width of 0 (full width)."""
+    return "k_march_batch" if tile[0] == 0 else "k_step_batch"
+
+
+def step_launches(cases, tile):
+    """Step-kernel launches per step: one for a tiled variant, one per distinct
+    row stride (width rounded up to 32) for a row-marching variant."""
+    if tile[0] != 0:
+        return 1
+    return len({(c.nx + 31) // 32 for c in cases})
+
+
 def read_traffic(tile):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it
-    was taken on the current kernel source and the same tile variant."""
-    path = os.path.join(ROOT, "profiles", "k_step_batch_sweep32.md")
+    """DRAM bytes per step of the step kernel(s) from the committed ncu summary, if
+    it was taken on the current kernel source and the same tile variant."""
+    path = os.path.join(ROOT, "profiles", kernel_name(tile) + "_sweep32.md")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -352,13 +366,13 @@ def run_ours(args):
                                 "tuning_ms_per_step": [round(m, 4) for m in tune_ms]}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_step_batch", "bytes_per_launch": bytes_per_step,
+                         "kernel": kernel_name(variants[chosen]), "bytes_per_launch": bytes_per_step,
                          "kernel_ms": kern_avg_ms, "peak_source": peak_src},
             "cpu_baseline": {"value": cpu["mlups"], "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"FP64 oracle, sweep domain 0 ({cpu['nx']}x{cpu['ny']}), "
                                        f"{cpu['steps']} steps in {cpu['seconds']:.1f} s, one thread"},
             "e2e": e2e,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": (step_launches(cases, variants[chosen]) + 1) * args.steps,
             "issue_bound": {"note": "the step kernel is bound by instruction issue and L2 latency of halo reads, "
                                     "not HBM; see profiles/k_step_batch_sweep32.md"},
             "clocks": clk,

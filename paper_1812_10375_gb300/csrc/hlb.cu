@@ -11,6 +11,7 @@
 
 #include "hlb.h"
 #include "hlb_kernels.cuh"
+#include "hlb_march.cuh"
 
 using namespace hlb;
 
@@ -48,7 +49,19 @@ constexpr int NVARIANTS = (int)(sizeof(VARIANTS) / sizeof(VARIANTS[0]));
 constexpr int TILE_Y = 28;      // the default variant's tile height (variant 0)
 constexpr int MIN_TILE_Y = 16;  // the shortest variant tile (sizes the partial-sum slots)
 
+// Row-marching variants (k_march*): variant NVARIANTS + k walks segments of
+// MARCH_SEGS[k] rows with one thread per column; only for nx <= MARCH_MAX_NX.
+#define HLB_MARCH_ENTRY(S) S,
+constexpr int MARCH_SEGS[] = {HLB_MARCH_SEGMENTS(HLB_MARCH_ENTRY)};
+constexpr int NMARCH = (int)(sizeof(MARCH_SEGS) / sizeof(MARCH_SEGS[0]));
+constexpr int NV_ALL = NVARIANTS + NMARCH;
+static_assert(MARCH_SEGS[0] >= MIN_TILE_Y, "march segments must not outnumber the partial-sum slots");
+bool is_march(int v) { return v >= NVARIANTS; }
+int march_seg(int v) { return MARCH_SEGS[v - NVARIANTS]; }
+size_t march_smem(int nx) { return (size_t)march_smem_floats(nx) * sizeof(float); }
+
 dim3 grid_of(int nx, int ny, int v) {
+  if (is_march(v)) return dim3((ny + march_seg(v) - 1) / march_seg(v), 1);
   return dim3((nx + TILE_X - 1) / TILE_X, (ny + VARIANTS[v].ty - 1) / VARIANTS[v].ty);
 }
 constexpr int GRAPH_STEPS = 16;     // steps per captured graph (even: buffers return to parity 0)
@@ -246,7 +259,10 @@ StepArgs args_for(hlb_domain* d, int par) {
 
 hlb_status launch_step(hlb_domain* d) {
   const StepArgs a = args_for(d, d->parity);
-  VARIANTS[d->variant].launch_single(d->grid, VARIANTS[d->variant].smem, d->stream, a);
+  if (is_march(d->variant))
+    k_march<<<d->grid, march_row_stride(d->p.nx), march_smem(d->p.nx), d->stream>>>(a, march_seg(d->variant));
+  else
+    VARIANTS[d->variant].launch_single(d->grid, VARIANTS[d->variant].smem, d->stream, a);
   k_reduce<<<1, 256, 0, d->stream>>>(d->partials, (int)(d->grid.x * d->grid.y), d->state, 1.0 / (double)d->n_fluid,
                                      1.0 / (double)d->p.nx, d->hist, HIST_CAP);
   if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
@@ -333,7 +349,7 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
   const int fluid_rows = q.ny - q.wall_rows - (q.top_bc == HLB_TOP_WALL ? 1 : 0);
   d->n_fluid = (long long)fluid_rows * q.nx;
   d->variant = 0;
-  d->grid = grid_of(q.nx, q.ny, 0);
+  d->grid = grid_of(q.nx, q.ny, d->variant);
   d->smem = smem_bytes();
 
   StepArgs& a = d->base;
@@ -384,6 +400,11 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
                              (int)VARIANTS[v].smem) != cudaSuccess)
       return HLB_ECUDA;
   }
+  if (cudaFuncSetAttribute(k_march, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem(MARCH_MAX_NX)) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_march_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)march_smem(MARCH_MAX_NX)) != cudaSuccess)
+    return HLB_ECUDA;
   // uniform wetting table
   return hlb_set_nucleation_sites(d, 0, nullptr);
 }
@@ -410,6 +431,22 @@ struct hlb_batch {
   size_t smem = 0;
   int variant = 0;
   cudaGraphExec_t graph = nullptr;
+  std::vector<int2> blk;  // host copy of d_blk
+  // row-marching variants: one launch per group of domains with the same row
+  // stride (block size), each on its own stream forked from and joined to the
+  // batch stream, so that the groups' blocks share the GPU
+  struct Group {
+    int ns, off, count;
+  };
+  std::vector<Group> groups;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev_join;
+  cudaEvent_t ev_fork = nullptr;
+  ~hlb_batch() {
+    for (cudaStream_t s : side) cudaStreamDestroy(s);
+    for (cudaEvent_t e : ev_join) cudaEventDestroy(e);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+  }
 };
 
 namespace {
@@ -474,9 +511,7 @@ StepArgs physics_of(const StepArgs& a) {
 hlb_status upload_tables(hlb_batch* b) {
   std::vector<DomArgs> desc(2 * (size_t)b->n);
   std::vector<ReduceArgs> ra(b->n);
-  std::vector<int2> blk((size_t)b->total_tiles);
-  for (int i = 0; i < b->n; ++i)
-    for (int t = b->tile_off[i]; t < b->tile_off[i + 1]; ++t) blk[t] = make_int2(i, t - b->tile_off[i]);
+  const std::vector<int2>& blk = b->blk;
   for (int i = 0; i < b->n; ++i) {
     hlb_domain* d = &b->dom[i];
     desc[i] = dom_args(args_for(d, 0));
@@ -502,8 +537,23 @@ hlb_status upload_tables(hlb_batch* b) {
 
 hlb_status batch_launch(hlb_batch* b, cudaEvent_t before, cudaEvent_t after) {
   if (before && cudaEventRecord(before, b->stream) != cudaSuccess) return HLB_ECUDA;
-  VARIANTS[b->variant].launch_batch(b->total_tiles, VARIANTS[b->variant].smem, b->stream, b->phys,
-                                    b->d_desc + (size_t)b->parity * b->n, b->d_blk, b->d_active, b->d_lag);
+  const DomArgs* desc = b->d_desc + (size_t)b->parity * b->n;
+  if (is_march(b->variant)) {
+    const int S = march_seg(b->variant);
+    if (cudaEventRecord(b->ev_fork, b->stream) != cudaSuccess) return HLB_ECUDA;
+    for (size_t g = 0; g < b->groups.size(); ++g) {
+      const hlb_batch::Group& G = b->groups[g];
+      if (cudaStreamWaitEvent(b->side[g], b->ev_fork, 0) != cudaSuccess) return HLB_ECUDA;
+      k_march_batch<<<G.count, G.ns, march_smem(G.ns), b->side[g]>>>(b->phys, desc, b->d_blk + G.off, b->d_active,
+                                                                    b->d_lag, S);
+      if (cudaEventRecord(b->ev_join[g], b->side[g]) != cudaSuccess ||
+          cudaStreamWaitEvent(b->stream, b->ev_join[g], 0) != cudaSuccess)
+        return HLB_ECUDA;
+    }
+  } else {
+    VARIANTS[b->variant].launch_batch(b->total_tiles, VARIANTS[b->variant].smem, b->stream, b->phys, desc, b->d_blk,
+                                      b->d_active, b->d_lag);
+  }
   if (after && cudaEventRecord(after, b->stream) != cudaSuccess) return HLB_ECUDA;
   k_reduce_batch<<<b->n, 256, 0, b->stream>>>(b->d_ra, b->d_active, b->d_lag, HIST_CAP);
   if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
@@ -555,6 +605,67 @@ hlb_status batch_build_graph(hlb_batch* b) {
 }
 
 bool batch_ok(const hlb_batch* b, int i) { return b && i >= 0 && i < b->n; }
+
+bool batch_march_ok(const hlb_batch* b) {
+  for (int i = 0; i < b->n; ++i)
+    if (b->dom[i].p.nx > MARCH_MAX_NX) return false;
+  return true;
+}
+
+// Select variant v for every domain of the batch: block table (grouped by row
+// stride for the row-marching variants), side streams, device tables.
+hlb_status set_batch_variant(hlb_batch* b, int v) {
+  if (is_march(v) && !batch_march_ok(b)) return HLB_EINVAL;
+  b->variant = v;
+  b->tile_off.assign(b->n + 1, 0);
+  for (int i = 0; i < b->n; ++i) {
+    hlb_domain* d = &b->dom[i];
+    d->variant = v;
+    d->grid = grid_of(d->p.nx, d->p.ny, v);
+    b->tile_off[i + 1] = b->tile_off[i] + (int)(d->grid.x * d->grid.y);
+  }
+  b->total_tiles = b->tile_off[b->n];
+  b->blk.clear();
+  b->groups.clear();
+  if (is_march(v)) {
+    std::vector<int> strides;
+    for (int i = 0; i < b->n; ++i) {
+      const int ns = march_row_stride(b->dom[i].p.nx);
+      bool seen = false;
+      for (int s2 : strides) seen = seen || s2 == ns;
+      if (!seen) strides.push_back(ns);
+    }
+    // widest first: their blocks are the largest and the longest
+    for (size_t a = 0; a < strides.size(); ++a)
+      for (size_t c = a + 1; c < strides.size(); ++c)
+        if (strides[c] > strides[a]) std::swap(strides[a], strides[c]);
+    for (int ns : strides) {
+      hlb_batch::Group G{ns, (int)b->blk.size(), 0};
+      for (int i = 0; i < b->n; ++i) {
+        if (march_row_stride(b->dom[i].p.nx) != ns) continue;
+        for (int t = 0; t < (int)b->dom[i].grid.x; ++t) b->blk.push_back(make_int2(i, t));
+      }
+      G.count = (int)b->blk.size() - G.off;
+      b->groups.push_back(G);
+    }
+    if (!b->ev_fork && cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+      return HLB_ECUDA;
+    while (b->side.size() < b->groups.size()) {
+      cudaStream_t s2 = nullptr;
+      cudaEvent_t e = nullptr;
+      if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) return HLB_ECUDA;
+      b->side.push_back(s2);
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return HLB_ECUDA;
+      b->ev_join.push_back(e);
+    }
+  } else {
+    for (int i = 0; i < b->n; ++i)
+      for (int t = b->tile_off[i]; t < b->tile_off[i + 1]; ++t) b->blk.push_back(make_int2(i, t - b->tile_off[i]));
+  }
+  b->smem = is_march(v) ? march_smem(MARCH_MAX_NX) : VARIANTS[v].smem;
+  batch_drop_graph(b);
+  return upload_tables(b);
+}
 
 }  // namespace
 
@@ -784,7 +895,6 @@ hlb_status hlb_batch_init(hlb_batch** out, int n, const hlb_params* p, void* d_w
     b->tile_off[i + 1] = b->tile_off[i] + (int)(b->dom[i].grid.x * b->dom[i].grid.y);
   }
   b->total_tiles = b->tile_off[n];
-  b->smem = smem_bytes();
   b->phys = physics_of(b->dom[0].base);
   for (int i = 1; i < n; ++i) {
     const StepArgs pi = physics_of(b->dom[i].base);
@@ -798,7 +908,7 @@ hlb_status hlb_batch_init(hlb_batch** out, int n, const hlb_params* p, void* d_w
   b->d_blk = (int2*)(ws + L.blk);
   b->d_active = (int*)(ws + L.active);
   b->d_lag = (float2*)(ws + L.lag);
-  const hlb_status st = upload_tables(b);
+  const hlb_status st = set_batch_variant(b, 0);
   if (st != HLB_OK) {
     delete b;
     return st;
@@ -918,21 +1028,6 @@ hlb_status hlb_batch_destroy(hlb_batch* b) {
 // ------------------------------------------------------------- autotuning
 namespace {
 
-hlb_status set_batch_variant(hlb_batch* b, int v) {
-  b->variant = v;
-  b->tile_off[0] = 0;
-  for (int i = 0; i < b->n; ++i) {
-    hlb_domain* d = &b->dom[i];
-    d->variant = v;
-    d->grid = grid_of(d->p.nx, d->p.ny, v);
-    b->tile_off[i + 1] = b->tile_off[i] + (int)(d->grid.x * d->grid.y);
-  }
-  b->total_tiles = b->tile_off[b->n];
-  b->smem = VARIANTS[v].smem;
-  batch_drop_graph(b);
-  return upload_tables(b);
-}
-
 }  // namespace
 
 hlb_status hlb_autotune(hlb_domain* d, int steps_per_variant, int* chosen, float* h_ms, int max_out) {
@@ -943,7 +1038,11 @@ hlb_status hlb_autotune(hlb_domain* d, int steps_per_variant, int* chosen, float
   float best = 1e30f;
   int best_v = 0;
   hlb_status st = HLB_OK;
-  for (int v = 0; v < NVARIANTS && st == HLB_OK; ++v) {
+  for (int v = 0; v < NV_ALL && st == HLB_OK; ++v) {
+    if (is_march(v) && d->p.nx > MARCH_MAX_NX) {
+      if (h_ms && v < max_out) h_ms[v] = 1e30f;  // not available for this width
+      continue;
+    }
     d->variant = v;
     d->grid = grid_of(d->p.nx, d->p.ny, v);
     drop_graph(d);
@@ -979,7 +1078,11 @@ hlb_status hlb_batch_autotune(hlb_batch* b, int steps_per_variant, int* chosen, 
   float best = 1e30f;
   int best_v = 0;
   hlb_status st = HLB_OK;
-  for (int v = 0; v < NVARIANTS && st == HLB_OK; ++v) {
+  for (int v = 0; v < NV_ALL && st == HLB_OK; ++v) {
+    if (is_march(v) && !batch_march_ok(b)) {
+      if (h_ms && v < max_out) h_ms[v] = 1e30f;  // not available for these widths
+      continue;
+    }
     st = set_batch_variant(b, v);
     if (st != HLB_OK) break;
     st = batch_launch(b, nullptr, nullptr);  // one untimed step per variant (first-launch costs)
@@ -1005,7 +1108,8 @@ hlb_status hlb_batch_autotune(hlb_batch* b, int steps_per_variant, int* chosen, 
 }
 
 hlb_status hlb_set_tile_variant(hlb_domain* d, int v) {
-  if (!d || v < 0 || v >= NVARIANTS) return HLB_EINVAL;
+  if (!d || v < 0 || v >= NV_ALL) return HLB_EINVAL;
+  if (is_march(v) && d->p.nx > MARCH_MAX_NX) return HLB_EINVAL;
   d->variant = v;
   d->grid = grid_of(d->p.nx, d->p.ny, v);
   drop_graph(d);
@@ -1013,17 +1117,18 @@ hlb_status hlb_set_tile_variant(hlb_domain* d, int v) {
 }
 
 hlb_status hlb_batch_set_tile_variant(hlb_batch* b, int v) {
-  if (!b || v < 0 || v >= NVARIANTS) return HLB_EINVAL;
+  if (!b || v < 0 || v >= NV_ALL) return HLB_EINVAL;
   return set_batch_variant(b, v);
 }
 
 int hlb_tile_variants(int* h_tile_w, int* h_tile_h, int* h_threads, int max_out) {
-  for (int v = 0; v < NVARIANTS && v < max_out; ++v) {
-    if (h_tile_w) h_tile_w[v] = TILE_X;
-    if (h_tile_h) h_tile_h[v] = VARIANTS[v].ty;
-    if (h_threads) h_threads[v] = VARIANTS[v].nth;
+  for (int v = 0; v < NV_ALL && v < max_out; ++v) {
+    // row-marching variants: full width (0), segment height, one thread per column (0)
+    if (h_tile_w) h_tile_w[v] = is_march(v) ? 0 : TILE_X;
+    if (h_tile_h) h_tile_h[v] = is_march(v) ? march_seg(v) : VARIANTS[v].ty;
+    if (h_threads) h_threads[v] = is_march(v) ? 0 : VARIANTS[v].nth;
   }
-  return NVARIANTS;
+  return NV_ALL;
 }
 
 const char* hlb_strerror(hlb_status s) {

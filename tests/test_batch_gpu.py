@@ -85,10 +85,21 @@ def test_stop_and_reuse_slot(coex):
     assert b.diag(1).step == 7
 
 
+def _close(fields, ref):
+    """Two kernel variants evaluate a cell's update with the same arithmetic but
+    may round differently (tiled and row-marching kernels) and sum the FP64
+    partials in another order: rho and T agree to 1e-6 of their maxima, u to
+    1e-6 in lattice units (2e-6 of the sound speed; the parity tolerance
+    against the FP64 oracle is 1e-5 of it)."""
+    for k, (x, y) in enumerate(zip(fields, ref)):
+        x, y = x.cpu().numpy().astype(np.float64), y.cpu().numpy()
+        tol = 1e-6 if k in (1, 2) else 1e-6 * max(np.abs(y).max(), 1e-30)
+        assert np.abs(x - y).max() <= tol, ("rho ux uy T".split()[k], np.abs(x - y).max())
+
+
 def test_autotune_picks_a_variant_and_keeps_results(coex):
     """The timed autotuning steps are ordinary steps: fields after autotune + k
-    steps equal an untuned run of the same length (tile shape changes only the
-    order of the FP64 partial sums)."""
+    steps match an untuned run of the same length to FP32 rounding."""
     from paper_1812_10375_gb300 import hlb
     cases = _cases()
     a = _batch(cases, coex)
@@ -101,15 +112,12 @@ def test_autotune_picks_a_variant_and_keeps_results(coex):
     b.step(5 * nv + 20)
     for i in range(len(cases)):
         assert a.diag(i).step == b.diag(i).step == 5 * nv + 20
-        for x, y in zip(a.read(i), b.read(i)):
-            x, y = x.cpu().numpy(), y.cpu().numpy()
-            assert np.abs(x - y).max() <= 1e-6 * max(np.abs(y).max(), 1e-30)
+        _close(a.read(i), b.read(i))
 
 
 def test_set_tile_variant_keeps_fields(coex):
-    """Each compiled tile variant, selected directly, advances the fields like
-    the default one (the tile shape changes only the order of the FP64 partial
-    sums of the domain-mean density)."""
+    """Each compiled variant, selected directly, advances the fields like the
+    default one, to FP32 rounding."""
     from paper_1812_10375_gb300 import hlb
     cases = _cases()
     ref = _batch(cases, coex)
@@ -123,9 +131,7 @@ def test_set_tile_variant_keeps_fields(coex):
         b.step(5)
         for i in range(len(cases)):
             assert b.diag(i).step == 9
-            for x, y in zip(b.read(i), ref.read(i)):
-                x, y = x.cpu().numpy(), y.cpu().numpy()
-                assert np.abs(x - y).max() <= 1e-6 * max(np.abs(y).max(), 1e-30)
+            _close(b.read(i), ref.read(i))
         with pytest.raises(hlb.HlbError):
             b.set_tile_variant(nv)
         b.close()
