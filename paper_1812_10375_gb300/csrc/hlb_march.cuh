@@ -47,8 +47,14 @@ enum { R3_PSI = 0, R3_RHO, R3_T1, R3_T2, R3_T3, NR3 };
 enum { R6_TN = 0, R6_UX, R6_UY, R6_LE, R6_LN, R6_IRCV, R6_AS, R6_BS, NR6 };
 
 __host__ __device__ constexpr int march_row_stride(int nx) { return (nx + 31) / 32 * 32; }
-// values per column: the rings plus one pad word so that the stride is odd
-__host__ __device__ constexpr int march_nq() { return (MARCH_DS * NR3 + MARCH_DL * NR6) | 1; }
+// Prefetch ring: the nine pulled populations and T^n of the next two rows to
+// pull, copied global -> shared by cp.async while the CTA works on earlier rows.
+constexpr int MARCH_PF = 10, MARCH_DP = 2;
+// values per column: the rings, the prefetch ring and a pad word so that the stride is odd
+__host__ __device__ constexpr int march_nq() {
+  return (MARCH_DS * NR3 + MARCH_DL * NR6 + MARCH_DP * MARCH_PF) | 1;
+}
+constexpr int MARCH_PF_OFF = MARCH_DS * NR3 + MARCH_DL * NR6;
 __host__ __device__ constexpr int march_smem_floats(int nx) { return march_nq() * march_row_stride(nx); }
 
 // Ring slot of a row: rows are >= 0 when stored, the phase PH = t mod 8 is a
@@ -84,8 +90,7 @@ struct MarchThread {
   int xm, xp;     // same, in lattice x
   bool act;       // i < nx
   float gw;       // wetting strength of the column (Eq. 10)
-  float nf[9];    // prefetched populations of the next row to pull (deviation form)
-  float nT;       // prefetched T^n of that row
+  float* pf;      // this column's prefetch ring in shared memory
   float f0[9];    // pulled populations of row t (A) ...
   float f1[9];    // ... and of row t - 1 (B collides them)
   float rho0;     // rho of row t (A) ...
@@ -101,7 +106,7 @@ struct MarchThread {
 
 // Row classes (uniform over the CTA).
 struct MarchRows {
-  int nx, ny, W, ys, ye;
+  int nx, ny, W, ys, ye, t_first;
   bool top_wall, top_open;
   __device__ __forceinline__ bool solid(int y) const { return y < W || (top_wall && y == ny - 1); }
   __device__ __forceinline__ bool dirichlet(int y) const { return y == 0 || (top_wall && y == ny - 1); }
@@ -114,33 +119,96 @@ struct MarchRows {
   __device__ __forceinline__ bool ghost(int y, int lo, int hi) const { return top_open && y == ny && in(y - 1, lo, hi); }
 };
 
-// Issue the pull of row y into th.nf / th.nT (the loads complete while the
-// CTA works on earlier phases).
-__device__ __forceinline__ void march_fetch(const StepArgs& A, const MarchRows& R, const Geo& g, MarchThread& th,
-                                            int y, float Uc) {
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// all but the most recent group complete: the row pulled now has arrived, the next one may be in flight
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Issue the pull of row y (the sources of pull(): pull-streaming, halfway
+// bounce-back next to solid rows, open-top rules) and of T^n(y) as cp.async
+// copies into prefetch slot y mod 2 of this column.  Values that are not
+// copies (the constant-density top row, Dirichlet temperatures) are stored
+// directly; the convective outlet's raw sources are copied and combined with
+// the outlet memory when the row is used (march_A).
+__device__ __forceinline__ void march_fetch(const StepArgs& A, const MarchRows& R, MarchThread& th, int y) {
   if (!th.act || y < 0 || y >= R.ny) return;
-  const int c = y * R.nx + th.i;
-  th.nT = R.dirichlet(y) ? (y == 0 ? A.T_bottom : A.T_top) : __ldg(A.T_in + c);
+  float* d = th.pf + (y & 1) * MARCH_PF;
+  const int nx = R.nx, x = th.i;
+  const int r0 = y * nx;
+  if (R.dirichlet(y))
+    d[9] = y == 0 ? A.T_bottom : A.T_top;
+  else
+    cp_async4(d + 9, A.T_in + r0 + x);
   if (R.solid(y)) return;
-  const bool sol_s = R.solid(y - 1);
+  const int P = (int)A.plane;
+  const float* __restrict__ F = A.f_in;
+  const bool bb_s = R.solid(y - 1);
   const bool sol_n = R.solid(y + 1 < R.ny ? y + 1 : R.ny - 1);
-  pull(A, g, th.i, th.xm, th.xp, y, sol_s, sol_n, Uc, th.nf);
+  const bool open_n = R.top_open && y == R.ny - 1;
+  const int rs = r0 - nx, rn = r0 + nx, xm = th.xm, xp = th.xp;
+  cp_async4(d + 0, F + r0 + x);
+  cp_async4(d + 1, F + 1 * P + r0 + xm);
+  cp_async4(d + 3, F + 3 * P + r0 + xp);
+  if (bb_s) {
+    cp_async4(d + 2, F + 4 * P + r0 + x);
+    cp_async4(d + 5, F + 7 * P + r0 + x);
+    cp_async4(d + 6, F + 8 * P + r0 + x);
+  } else {
+    cp_async4(d + 2, F + 2 * P + rs + x);
+    cp_async4(d + 5, F + 5 * P + rs + xm);
+    cp_async4(d + 6, F + 6 * P + rs + xp);
+  }
+  if (open_n) {
+    if (A.top_bc == TOP_CONST_RHO) {
+      const float dr = A.rho_v - A.rho_ref;
+      d[4] = dr * (1.f / 9.f);
+      d[7] = dr * (1.f / 36.f);
+      d[8] = dr * (1.f / 36.f);
+    } else {
+      cp_async4(d + 4, F + 4 * P + r0 + x);
+      cp_async4(d + 7, F + 7 * P + r0 + xp);
+      cp_async4(d + 8, F + 8 * P + r0 + xm);
+    }
+  } else if (sol_n) {
+    cp_async4(d + 4, F + 2 * P + r0 + x);
+    cp_async4(d + 7, F + 5 * P + r0 + x);
+    cp_async4(d + 8, F + 6 * P + r0 + x);
+  } else {
+    cp_async4(d + 4, F + 4 * P + rn + x);
+    cp_async4(d + 7, F + 7 * P + rn + xp);
+    cp_async4(d + 8, F + 8 * P + rn + xm);
+  }
 }
 
 // Phase A: row y = t.  rho, psi and T^n of the row into the rings; the pulled
 // populations stay in registers for the collision of the next iteration.
 template <int PH>
 __device__ __forceinline__ void march_A(const StepArgs& A, const MarchRows& R, const MarchCtx& C, MarchThread& th,
-                                        int y) {
+                                        int y, float Uc) {
   constexpr int s3 = Slot<PH, 0, MARCH_DS>::v, s6 = Slot<PH, 0, MARCH_DL>::v;
   const SRow psi = C.q3(R3_PSI, s3);
   const SRow rho = C.q3(R3_RHO, s3);
   const SRow tn = C.q6(R6_TN, s6);
   if (R.in(y, 5, 5)) {
-    const float T = th.nT;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) th.f0[q] = th.nf[q];
+    cp_async_wait_prev();
+    const float* d = th.pf + (y & 1) * MARCH_PF;
+    const float T = d[9];
     if (th.act) {
+      if (!R.solid(y)) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) th.f0[q] = d[q];
+        if (A.top_bc == TOP_CONVECTIVE && y == R.ny - 1) {
+          // f_i(top) = [f_i^{n-1}(top) + U f_i^n(top-1)] / (1 + U) as prev + Uc (below - prev),
+          // Uc = U / (1 + U) from FP64 (pull() evaluates the same expression)
+          const float p4 = A.ftop_in[th.i], p7 = A.ftop_in[R.nx + th.i], p8 = A.ftop_in[2 * R.nx + th.i];
+          th.f0[4] = p4 + Uc * (th.f0[4] - p4);
+          th.f0[7] = p7 + Uc * (th.f0[7] - p7);
+          th.f0[8] = p8 + Uc * (th.f0[8] - p8);
+        }
+      }
       tn[th.i] = T;
       if (R.solid(y)) {
         psi[th.i] = 0.f;
@@ -372,13 +440,14 @@ __device__ __forceinline__ void march_S(const StepArgs& A, const MarchRows& R, c
 template <int PH>
 __device__ __forceinline__ void march_iter(const StepArgs& A, const MarchRows& R, const Geo& g, const MarchCtx& C,
                                            MarchThread& th, int t, float Uc, float rho_ave) {
-  march_A<PH>(A, R, C, th, t);
+  march_A<PH>(A, R, C, th, t, Uc);
   march_S<PH, 1>(A, R, C, th, t - LAG_S1);
   march_S<PH, 4>(A, R, C, th, t - LAG_S4);
   __syncthreads();
   march_B<PH>(A, R, C, th, t - LAG_B, rho_ave);
-  // prefetch the next row to pull while the later phases run
-  if (R.in(t + 1, 5, 5)) march_fetch(A, R, g, th, t + 1, Uc);
+  // prefetch the row after next into the slot phase A has just consumed
+  if (t >= R.t_first && R.in(t + 2, 5, 5)) march_fetch(A, R, th, t + 2);
+  cp_async_commit();
   march_S<PH, 2>(A, R, C, th, t - LAG_S2);
   __syncthreads();
   march_C<PH>(A, R, C, th, t - LAG_C);
@@ -425,8 +494,8 @@ __device__ __forceinline__ void march_segment(const StepArgs& A, int ys, int ye,
   th.err = 0;
   th.rho0 = th.rho1 = 1.f;
 #pragma unroll
-  for (int q = 0; q < 9; ++q) th.nf[q] = th.f0[q] = th.f1[q] = 0.f;
-  th.nT = 0.f;
+  for (int q = 0; q < 9; ++q) th.f0[q] = th.f1[q] = 0.f;
+  th.pf = sm + (size_t)th.i * MARCH_NQ + MARCH_PF_OFF;
 #pragma unroll
   for (int q = 0; q < 5; ++q) th.ac[q] = th.tn[q] = 0.f;
   th.mh = th.ml = th.eh = th.el = 0.f;
@@ -438,7 +507,11 @@ __device__ __forceinline__ void march_segment(const StepArgs& A, int ys, int ye,
   const int t_first = ys - 5 > 0 ? ys - 5 : 0;
   const int t_last = ye - 1 + MARCH_LAG_MAX;
   const int t0 = t_first - (t_first % MARCH_DL);
-  march_fetch(A, R, g, th, t_first, Uc);
+  R.t_first = t_first;
+  if (R.in(t_first, 5, 5)) march_fetch(A, R, th, t_first);
+  cp_async_commit();
+  if (R.in(t_first + 1, 5, 5)) march_fetch(A, R, th, t_first + 1);
+  cp_async_commit();
 #pragma unroll 1
   for (int t = t0; t <= t_last; t += MARCH_DL) {
     march_iter<0>(A, R, g, C, th, t, Uc, rho_ave);
