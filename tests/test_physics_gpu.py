@@ -1,8 +1,8 @@
 """Physics checks of the GPU step that need long runs: conservation of the
 finite-volume energy update across a conjugate solid-liquid interface
 (Sections 2.3, 3.3), the film evaporation rate of Eq. (29), and statistical
-parity of the time-averaged wall heat flux of a boiling run with the FP64
-oracle (Sections 4.3-4.4)."""
+parity with the FP64 oracle of the time-averaged wall heat flux of a boiling
+run and of the bubble-departure period (Sections 4.3-4.4)."""
 import dataclasses
 
 import numpy as np
@@ -104,3 +104,35 @@ def test_boiling_time_averaged_flux_matches_oracle(coex):
     assert np.mean(co) > 0.05  # it boils
     assert dg.q_bottom_timeavg == pytest.approx(np.mean(qo), rel=0.03)
     assert dg.vapour_coverage_timeavg == pytest.approx(np.mean(co), rel=0.03, abs=0.01)
+
+
+def test_departure_period_matches_oracle(coex):
+    """Bubble departure (Section 4.3): a 64 x 140 lattice with a 10-row heater
+    at Ts + 0.11 Tc, one nucleation site (g_min = -0.3) and a vapour bubble of
+    radius 12 seeded on it.  Densities every 20 steps over 20,000 steps go
+    through the departure detector (paper_1812_10375_gb300.departure) for the
+    FP32 GPU run and the FP64 oracle run: both see the same departures, at
+    times within 3% of the departure period, and periods within 3%."""
+    from paper_1812_10375_gb300 import departure
+    rl, rv = coex["rho_l"], coex["rho_v"]
+    case = wl.pool(nx=64, ny=140, n_sites=1, heater_rows=10, superheat=0.11, seed=5)
+    case = dataclasses.replace(case, sites=[(case.sites[0][0], 10.0, -0.3)])
+    rho0, T0 = wl.initial_fields(case, rl, rv, coex["Tc"])
+    rho0 = rl + rv - wl.droplet(case.ny, case.nx, rl, rv, case.sites[0][0], case.wall_rows, 12.0)
+    every, n = 20, 1000
+    od = oracle_domain(case, coex, rho0=rho0, T0=T0)
+    gd = gpu_domain(case, coex, rho0=rho0, T0=T0)
+    so, sg, steps = [], [], []
+    for k in range(n):
+        od.step(every)
+        gd.step(every)
+        so.append(od.fields()[0].copy())
+        sg.append(gd.read()[0].cpu().numpy())
+        steps.append(every * (k + 1))
+    do = departure.detect(so, steps, case.wall_rows, rl, rv)
+    dg = departure.detect(sg, steps, case.wall_rows, rl, rv)
+    print(f"departures: oracle {list(do.times)} period {do.period():.0f}; gpu {list(dg.times)} period {dg.period():.0f}")
+    assert do.count >= 2 and dg.count == do.count
+    P = do.period()
+    assert dg.period() == pytest.approx(P, rel=0.03)
+    assert np.abs(dg.times - do.times).max() <= 0.03 * P
