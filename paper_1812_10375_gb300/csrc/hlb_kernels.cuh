@@ -246,7 +246,11 @@ __device__ __forceinline__ bool rowbit(unsigned w, int k, int m) { return (w >> 
 // Fused coupled step on tile (bx, by).  Ring r of the tile = frame cells within
 // distance r of the tile.  `part` is the tile's slot in the partial-sum array.
 // Uc, rho_ave: the lagged outlet factor U/(1+U) and mean density of the domain.
-template <int TY, int NTHREADS>
+// INT: the tile is interior (tile_interior below): every frame row is a fluid
+// row at least one row away from a solid row and from the top two rows, so the
+// row-class tests (solid, Dirichlet, bounce-back, open top, wall-flux and
+// diagnostic rows, ghost rows) are known to be false and compile away.
+template <int TY, int NTHREADS, bool INT>
 __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int part, float* sm, float Uc,
                                           float rho_ave) {
   constexpr int H = HALO, TX = TILE_W, FW = FRAME_W, FH = TY + 2 * H, FN = FW * FH;
@@ -285,7 +289,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   // (the zero-gradient ghost of an open top; unused above a top wall), so
   // every stencil reads its north and south neighbours at fixed offsets.
   const int jtop = ny - 1 - y0 + H;  // frame row of gy = ny - 1
-  const bool has_ghost = jtop < FH - 1;
+  const bool has_ghost = !INT && jtop < FH - 1;
   auto fill_ghost = [&](float* a) {
     for (int j = jtop + 1 + jp; j < FH; j += NPH) a[j * FW + i] = a[jtop * FW + i];
   };
@@ -311,18 +315,18 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   auto lt = [&](int v) -> unsigned { return (1u << min(max((v - g0 + NPH - 1) >> SH, 0), NJ)) - 1u; };
   auto ltj = [&](int v) -> unsigned { return (1u << min(max((v - jp + NPH - 1) >> SH, 0), NJ)) - 1u; };
   auto eq = [&](int v) -> unsigned { return lt(v + 1) & ~lt(v); };
-  const unsigned lat = lt(ny) & ~lt(0);
+  const unsigned lat = INT ? ALL : lt(ny) & ~lt(0);
   const unsigned ring4 = ltj(H + TY + 4) & ~ltj(H - 4) & lat;
   const unsigned ring5 = ltj(H + TY + 5) & ~ltj(H - 5) & lat;
   const unsigned ownr = own_col ? ltj(H + TY) & ~ltj(H) & lat : 0u;
-  const unsigned diag = eq(1) | eq(A.W) | eq(ny - 2) | eq(ny - 1);
+  const unsigned diag = INT ? 0u : eq(1) | eq(A.W) | eq(ny - 2) | eq(ny - 1);
   const bool tw = g.top_wall;
   const unsigned solid = lt(A.W) | (tw ? ALL & ~lt(ny - 1) : 0u);      // solid_row(min(gy, ny - 1))
   const unsigned dirich = eq(0) | (tw ? eq(ny - 1) : 0u);                // dirichlet_row(gy)
   const unsigned sol_below = lt(A.W + 1) | (tw ? eq(ny) : 0u);          // solid_row(gy - 1)
   const unsigned sol_above = lt(A.W - 1) | (tw ? ALL & ~lt(ny - 2) : 0u);  // solid_row(min(gy + 1, ny - 1))
   const unsigned rf = ring4 | ring5 << 8 | ownr << 16 | diag << 24;
-  const unsigned fl = solid | dirich << 8 | sol_below << 16 | sol_above << 24;
+  const unsigned fl = INT ? 0u : solid | dirich << 8 | sol_below << 16 | sol_above << 24;
   if (tid == 0) s_err = 0;  // read after the barriers below
   for (int t = tid; t < 3 * 2 * FW; t += NTHREADS) (&s_q[0][0][0])[t] = 0.f;
   int err = 0;
@@ -347,7 +351,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
     const float T = rowbit(fl, 1, m) ? (gy == 0 ? A.T_bottom : A.T_top) : __ldg(A.T_in + c);
     if (!rowbit(fl, 0, m)) {
       const bool sol_s = rowbit(fl, 2, m), sol_n = rowbit(fl, 3, m);
-      if (!sol_s && !sol_n && !(g.top_open && gy == ny - 1)) {
+      if (INT || (!sol_s && !sol_n && !(g.top_open && gy == ny - 1))) {
         const float* __restrict__ F = A.f_in + c;
         f[0] = __ldg(F);
         f[1] = __ldg(F + o1);
@@ -503,16 +507,16 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   for (int m = 0; m < NJ; ++m) {
     const int j = jp + NPH * m;
     const int gy = y0 - H + j;
-    if (j < H - 4 || j >= H + TY + 4 || gy < 0 || gy >= ny) continue;
+    if (j < H - 4 || j >= H + TY + 4 || (!INT && (gy < 0 || gy >= ny))) continue;
     const int idx = j * FW + i;
-    const bool solid = g.solid_row(gy);
+    const bool solid = !INT && g.solid_row(gy);
     const float lam = solid ? lam_w : sRho[idx] * cvk;
     {
       const float le = solid ? lam_w : sRho[idx + 1] * cvk;
       sLae[idx] = 2.f * lam * le / (lam + le);
     }
     if (j + 1 < H + TY + 4) {
-      const float ln = g.solid_row(gy + 1 < ny ? gy + 1 : ny - 1) ? lam_w : sRho[idx + FW] * cvk;
+      const float ln = !INT && g.solid_row(gy + 1 < ny ? gy + 1 : ny - 1) ? lam_w : sRho[idx + FW] * cvk;
       sLan[idx] = 2.f * lam * ln / (lam + ln);
     }
     if (j < H - 3 || j >= H + TY + 3) continue;
@@ -566,19 +570,19 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
       // rows outside ring r are skipped (warp-uniform); every column of a row
       // is evaluated (columns outside the ring are never read later), and only
       // the tile's own cells store or accumulate
-      if (j < H - r || j >= H + TY + r || gy < 0 || gy >= ny) continue;
+      if (j < H - r || j >= H + TY + r || (!INT && (gy < 0 || gy >= ny))) continue;
       const bool own = own_col && j >= H && j < H + TY;
       const int idx = j * FW + i;
       const int js = j - 1, jn = j + 1;
       const float Tp = Tc[idx];
       float hk = 0.f;
-      if (!g.dirichlet_row(gy)) {
+      if (INT || !g.dirichlet_row(gy)) {
         const float TE = Tc[idx + 1], TW = Tc[idx - 1], TN = Tc[jn * FW + i], TS = Tc[js * FW + i];
         // Eqs. (22)-(26): sum of face fluxes over the control volume
         float kk = sLae[idx] * (TE - Tp) + sLae[idx - 1] * (TW - Tp) + sLan[idx] * (TN - Tp) +
                    sLan[js * FW + i] * (TS - Tp);
         kk *= sIrcv[idx];
-        if (!g.solid_row(gy)) {
+        if (INT || !g.solid_row(gy)) {
           const float TNE = Tc[jn * FW + i + 1], TNW = Tc[jn * FW + i - 1];
           const float TSE = Tc[js * FW + i + 1], TSW = Tc[js * FW + i - 1];
           const float gxT = (TE - TW) * (1.f / 3.f) + ((TNE - TSW) + (TSE - TNW)) * (1.f / 12.f);
@@ -597,9 +601,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
           s_q[q][0][i] = h;
           s_q[q][1][i] = l;
         };
-        if (gy == 1) qadd(0, wk * sLan[js * FW + i] * (Tc[js * FW + i] - Tp));
-        if (g.top_wall && gy == ny - 2) qadd(1, wk * sLan[idx] * (Tp - Tc[jn * FW + i]));
-        if (gy == A.W) qadd(2, wk * sLan[js * FW + i] * (Tc[js * FW + i] - Tp));
+        if (!INT && gy == 1) qadd(0, wk * sLan[js * FW + i] * (Tc[js * FW + i] - Tp));
+        if (!INT && g.top_wall && gy == ny - 2) qadd(1, wk * sLan[idx] * (Tp - Tc[jn * FW + i]));
+        if (!INT && gy == A.W) qadd(2, wk * sLan[js * FW + i] * (Tc[js * FW + i] - Tp));
         if (k == 4) {
           const float Tnew = sT0[idx] + dt * (1.f / 6.f) * (acc[m] + hk);
           if (nonfinite(Tnew)) err |= ERR_NONFINITE;
@@ -639,11 +643,23 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   if (tid == 0 && s_err) atomicOr(&A.state->error_flags, s_err);
 }
 
+// A tile whose frame rows [y0 - HALO, y0 + TY + HALO) all lie in [W + 1, ny - 3]:
+// no row of the frame is solid, next to a solid row, the open top row or the
+// row below it, so every pull is plain streaming and no wall flux or
+// diagnostic row falls in the tile.
+__device__ __forceinline__ bool tile_interior(const StepArgs& A, int y0, int TY) {
+  return y0 - HALO >= A.W + 1 && y0 + TY + HALO - 1 <= A.ny - 3;
+}
+
 template <int TY, int NTH, int MINB>
 __global__ void __launch_bounds__(NTH, MINB) k_step(const StepArgs A) {
   extern __shared__ float sm[];
-  step_tile<TY, NTH>(A, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, sm, (float)A.state->Uc,
-                     (float)A.state->rho_ave);
+  const float Uc = (float)A.state->Uc, rho_ave = (float)A.state->rho_ave;
+  const int part = blockIdx.y * gridDim.x + blockIdx.x;
+  if (tile_interior(A, blockIdx.y * TY, TY))
+    step_tile<TY, NTH, true>(A, blockIdx.x, blockIdx.y, part, sm, Uc, rho_ave);
+  else
+    step_tile<TY, NTH, false>(A, blockIdx.x, blockIdx.y, part, sm, Uc, rho_ave);
 }
 
 // Batched step: the blocks of one launch cover the tiles of every domain of a
@@ -696,7 +712,11 @@ __global__ void __launch_bounds__(NTH, MINB) k_step_batch(const StepArgs P, cons
   A.state = sD.state;
   const int local = s_bl.y;
   const int tx = (A.nx + TILE_W - 1) / TILE_W;
-  step_tile<TY, NTH>(A, local % tx, local / tx, local, sm, s_lg.x, s_lg.y);
+  const int by = local / tx;
+  if (tile_interior(A, by * TY, TY))
+    step_tile<TY, NTH, true>(A, local % tx, by, local, sm, s_lg.x, s_lg.y);
+  else
+    step_tile<TY, NTH, false>(A, local % tx, by, local, sm, s_lg.x, s_lg.y);
 }
 
 // The lagged scalars of a domain as the batched step reads them.
