@@ -79,10 +79,9 @@ def read_traffic(tile):
                 vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_hash") != kernel_source_hash():
         return None
-    if vals.get("tile_variant") != "x".join(str(t) for t in tile):
-        return None
+    key = "dram_bytes_per_launch_full_sweep_" + "x".join(str(t) for t in tile)
     try:
-        return float(vals["dram_bytes_per_launch_full_sweep"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
 
@@ -337,16 +336,10 @@ def run_ours(args):
 
     # end to end through the public API with host buffers
     e2e = run_e2e(args, hlb, plist, fields, cases, cells, dist)
+    probe = probe_2048(hlb, wl, params_for, peak_gbs()) if rank == 0 else None
     pph = points_per_hour(hlb, plist, fields, cases) if rank == 0 else None
 
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            peaks = json.load(fh)
-    except OSError:
-        pass
-    peak = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
+    peak, peak_src = peak_gbs()
     achieved = bytes_per_step / (kern_avg_ms * 1e-3) / 1e9
     traffic = read_traffic(variants[chosen])
 
@@ -377,12 +370,56 @@ def run_ours(args):
                                     "not HBM; see profiles/k_step_batch_sweep32.md"},
             "clocks": clk,
             "points_per_hour": pph,
+            "probe_2048": probe,
             "diag_domain0": {"step": diag0.step, "q_bottom": diag0.q_bottom, "error_flags": diag0.error_flags},
         }
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def peak_gbs():
+    """The measured HBM copy bandwidth (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+        return float(peaks["hbm_gbs"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback"
+
+
+def probe_2048(hlb, wl, params_for, peak, steps=200):
+    """The large single-domain roofline probe: one 2048 x 2048 pool shaped like
+    the 400 x 400 case (25-row heater at Ts + 0.1 Tc, 5 seeded sites,
+    convective top), advanced by the single-domain step (graph-captured), timed
+    with CUDA events on the domain's stream over `steps` steps after 32 warm-up
+    steps.  State 336 MB per buffer set, larger than L2."""
+    import torch
+    case = wl.pool(nx=2048, ny=2048, n_sites=5)
+    p, Tc = params_for(case)
+    rho0, T0 = wl.initial_fields(case, p.rho_l, p.rho_v, Tc)
+    d = hlb.Domain(p)
+    d.set_fields(torch.from_numpy(rho0.astype("float32")).cuda(), torch.from_numpy(T0.astype("float32")).cuda())
+    d.set_nucleation_sites(case.sites)
+    d.step(32)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(d.stream)
+    d.step(steps)
+    e1.record(d.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    n_fluid = (case.ny - case.wall_rows) * case.nx
+    nbytes = BYTES_FLUID * n_fluid + BYTES_SOLID * case.wall_rows * case.nx
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    err = d.diag(check_flags=False).error_flags
+    d.close()
+    return {"workload": "2048 x 2048 pool, 25-row heater at Ts + 0.1 Tc, 5 sites, convective top; single-domain "
+                        "step + FP64 reduction per step (graph-captured), CUDA events over %d steps" % steps,
+            "ms_per_step": ms, "mlups": case.nx * case.ny / (ms * 1e-3) / 1e6,
+            "achieved_gbs": gbs, "frac": gbs / peak[0], "peak": peak[0], "peak_source": peak[1],
+            "bytes_per_step": nbytes, "error_flags": err}
 
 
 def run_e2e(args, hlb, plist, fields, cases, cells, dist):

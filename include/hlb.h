@@ -53,6 +53,15 @@ enum { HLB_TOP_WALL = 0, HLB_TOP_CONST_RHO = 1, HLB_TOP_CONVECTIVE = 2 };
  * or the plain populations. */
 enum { HLB_STORE_DEVIATION = 0, HLB_STORE_PLAIN = 1 };
 
+/* Diffusion term of the energy equation (Eq. 17): the finite-volume form with
+ * harmonic face conductivities (Eqs. 22-26, the paper's scheme, default), or
+ * the isotropic central form lambda lap(T) + grad(lambda) . grad(T) with the
+ * Laplacian of Eq. (20) and the gradients of Eq. (19) (Eq. 21, the scheme the
+ * paper shows to violate energy conservation across conductivity jumps,
+ * Section 3.2).  The isotropic form runs in the single-domain tiled kernel only;
+ * batches and the row-marching kernel reject it. */
+enum { HLB_DIFF_FV = 0, HLB_DIFF_ISO = 1 };
+
 /*
  * Model and geometry parameters, all in lattice units (dx = dt = 1, Section 3.1).
  * hlb_params_default fills the paper's values; fields marked "<= 0: default"
@@ -75,6 +84,10 @@ typedef struct {
   double Gw0;                          /* wall wetting strength (Eq. 10), 0.3         */
   double T_bottom, T_top;              /* Dirichlet T of row 0 / of row ny-1 (top wall) */
   double rho_l, rho_v;                 /* coexistence densities at Ts; <= 0: Maxwell  */
+  int diffusion;                       /* HLB_DIFF_FV (default) | HLB_DIFF_ISO         */
+  double lambda_top;                   /* conductivity of a top wall row; <= 0: lambda_w
+                                          (Section 3.2: each wall conducts like the phase
+                                          next to it)                                   */
 } hlb_params;
 
 /* One nucleation site: a linear drop of G_w from Gw0 to gw_min at x_center over

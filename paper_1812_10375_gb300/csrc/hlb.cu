@@ -182,6 +182,7 @@ bool params_valid(const hlb_params* p) {
   if (fluid_rows < 3) return false;
   if (p->n_sub != 1) return false;  // the fused kernel's halo is sized for N = 1
   if (p->storage != HLB_STORE_DEVIATION && p->storage != HLB_STORE_PLAIN) return false;
+  if (p->diffusion != HLB_DIFF_FV && p->diffusion != HLB_DIFF_ISO) return false;
   if (!(p->a > 0 && p->b > 0 && p->R > 0 && p->Ts_over_Tc > 0)) return false;
   if (!(p->s_e > 0 && p->s_e < 2 && p->s_zeta > 0 && p->s_zeta < 2 && p->s_j > 0 && p->s_j < 2 &&
         p->s_q > 0 && p->s_q < 2))
@@ -386,7 +387,11 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
   a.rcv_w = (float)(q.rho_w * q.cv_w);
   a.inv_rcv_w = (float)(1.0 / (q.rho_w * q.cv_w));
   a.lambda_w = (float)q.lambda_w;
+  a.lambda_top = (float)(q.lambda_top > 0 ? q.lambda_top : q.lambda_w);
   a.dt = (float)(1.0 / q.n_sub);
+  a.iso = q.diffusion == HLB_DIFF_ISO ? 1 : 0;
+  a.kd = (float)q.k;
+  a.kd_w = (float)(q.lambda_w / (q.rho_w * q.cv_w));
   a.T_bottom = (float)q.T_bottom;
   a.T_top = (float)q.T_top;
   a.Gw = d->Gw;
@@ -865,7 +870,7 @@ hlb_status hlb_destroy(hlb_domain* d) {
 size_t hlb_batch_workspace_bytes(int n, const hlb_params* p) {
   if (n < 1 || !p) return 0;
   for (int i = 0; i < n; ++i)
-    if (!params_valid(p + i)) return 0;
+    if (!params_valid(p + i) || p[i].diffusion != HLB_DIFF_FV) return 0;
   return batch_layout(n, p).total;
 }
 
@@ -874,7 +879,7 @@ hlb_status hlb_batch_init(hlb_batch** out, int n, const hlb_params* p, void* d_w
   if (!out || n < 1 || !p || !d_workspace) return HLB_EINVAL;
   *out = nullptr;
   for (int i = 0; i < n; ++i)
-    if (!params_valid(p + i)) return HLB_EINVAL;
+    if (!params_valid(p + i) || p[i].diffusion != HLB_DIFF_FV) return HLB_EINVAL;
   if (((uintptr_t)d_workspace & 255) != 0) return HLB_EINVAL;
   const BatchLayout L = batch_layout(n, p);
   if (workspace_bytes < L.total) return HLB_EINVAL;
@@ -1039,8 +1044,8 @@ hlb_status hlb_autotune(hlb_domain* d, int steps_per_variant, int* chosen, float
   int best_v = 0;
   hlb_status st = HLB_OK;
   for (int v = 0; v < NV_ALL && st == HLB_OK; ++v) {
-    if (is_march(v) && d->p.nx > MARCH_MAX_NX) {
-      if (h_ms && v < max_out) h_ms[v] = 1e30f;  // not available for this width
+    if (is_march(v) && (d->p.nx > MARCH_MAX_NX || d->p.diffusion != HLB_DIFF_FV)) {
+      if (h_ms && v < max_out) h_ms[v] = 1e30f;  // not available for this width or scheme
       continue;
     }
     d->variant = v;
@@ -1109,7 +1114,7 @@ hlb_status hlb_batch_autotune(hlb_batch* b, int steps_per_variant, int* chosen, 
 
 hlb_status hlb_set_tile_variant(hlb_domain* d, int v) {
   if (!d || v < 0 || v >= NV_ALL) return HLB_EINVAL;
-  if (is_march(v) && d->p.nx > MARCH_MAX_NX) return HLB_EINVAL;
+  if (is_march(v) && (d->p.nx > MARCH_MAX_NX || d->p.diffusion != HLB_DIFF_FV)) return HLB_EINVAL;
   d->variant = v;
   d->grid = grid_of(d->p.nx, d->p.ny, v);
   drop_graph(d);
@@ -1307,7 +1312,11 @@ extern "C" hlb_status hlb_step_static(const hlb_params* p, int n_sites, const hl
   a.rcv_w = (float)(q.rho_w * q.cv_w);
   a.inv_rcv_w = (float)(1.0 / (q.rho_w * q.cv_w));
   a.lambda_w = (float)q.lambda_w;
+  a.lambda_top = (float)(q.lambda_top > 0 ? q.lambda_top : q.lambda_w);
   a.dt = (float)(1.0 / q.n_sub);
+  a.iso = q.diffusion == HLB_DIFF_ISO ? 1 : 0;
+  a.kd = (float)q.k;
+  a.kd_w = (float)(q.lambda_w / (q.rho_w * q.cv_w));
   a.T_bottom = (float)q.T_bottom;
   a.T_top = (float)q.T_top;
   a.f_in = d_f_in;

@@ -43,6 +43,9 @@ struct StepArgs {
   float rho_mid;  // (rho_l + rho_v) / 2: vapour below, liquid above
   // energy (Eq. 17)
   float cvk, cv, rcv_w, inv_rcv_w, lambda_w, dt;
+  float lambda_top;  // conductivity of a top wall row
+  int iso;          // isotropic central diffusion (Eqs. 20-21) instead of the finite-volume faces
+  float kd, kd_w;   // lambda / (rho cv) of the fluid (k) and of the solid
   float T_bottom, T_top;
   // buffers
   const float* __restrict__ f_in;

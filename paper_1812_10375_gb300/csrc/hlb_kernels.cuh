@@ -250,7 +250,10 @@ __device__ __forceinline__ bool rowbit(unsigned w, int k, int m) { return (w >> 
 // row at least one row away from a solid row and from the top two rows, so the
 // row-class tests (solid, Dirichlet, bounce-back, open top, wall-flux and
 // diagnostic rows, ghost rows) are known to be false and compile away.
-template <int TY, int NTHREADS, bool INT>
+// ISO: the energy equation's diffusion term in the isotropic central form of
+// Eq. (21), lambda lap(T) + grad(lambda) . grad(T) with the Laplacian of
+// Eq. (20) and the gradients of Eq. (19), instead of the finite-volume faces.
+template <int TY, int NTHREADS, bool INT, bool ISO = false>
 __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int part, float* sm, float Uc,
                                           float rho_ave) {
   constexpr int H = HALO, TX = TILE_W, FW = FRAME_W, FH = TY + 2 * H, FN = FW * FH;
@@ -503,6 +506,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   // on the rows of ring 3 (every column, as in the stages); lambda = rho cv k in
   // the fluid (Section 2.2), lambda_w in solid rows
   const float lam_w = A.lambda_w, cvk = A.cvk;
+  // conductivity of a solid row: the heater's, or the top wall's (Section 3.2)
+  auto wall_lam = [&](int row) -> float { return g.top_wall && row == ny - 1 ? A.lambda_top : lam_w; };
 #pragma unroll
   for (int m = 0; m < NJ; ++m) {
     const int j = jp + NPH * m;
@@ -510,13 +515,14 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
     if (j < H - 4 || j >= H + TY + 4 || (!INT && (gy < 0 || gy >= ny))) continue;
     const int idx = j * FW + i;
     const bool solid = !INT && g.solid_row(gy);
-    const float lam = solid ? lam_w : sRho[idx] * cvk;
+    const float lam = solid ? wall_lam(gy) : sRho[idx] * cvk;
     {
-      const float le = solid ? lam_w : sRho[idx + 1] * cvk;
+      const float le = solid ? wall_lam(gy) : sRho[idx + 1] * cvk;
       sLae[idx] = 2.f * lam * le / (lam + le);
     }
     if (j + 1 < H + TY + 4) {
-      const float ln = !INT && g.solid_row(gy + 1 < ny ? gy + 1 : ny - 1) ? lam_w : sRho[idx + FW] * cvk;
+      const int gn = gy + 1 < ny ? gy + 1 : ny - 1;
+      const float ln = !INT && g.solid_row(gn) ? wall_lam(gn) : sRho[idx + FW] * cvk;
       sLan[idx] = 2.f * lam * ln / (lam + ln);
     }
     if (j < H - 3 || j >= H + TY + 3) continue;
@@ -546,6 +552,32 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
     sBs[idx] = Br * ircv * divu;
   }
   __syncthreads();
+  if (ISO) {
+    // Eq. (21): grad(lambda) . grad(T) / (rho cv) joins the advection term as
+    // u - grad(lambda) / (rho cv) (u = 0 in solid rows); lambda from rho (ring 5)
+#pragma unroll
+    for (int m = 0; m < NJ; ++m) {
+      const int j = jp + NPH * m;
+      const int gy = y0 - H + j;
+      if (j < H - 3 || j >= H + TY + 3 || gy < 0 || gy >= ny || g.dirichlet_row(gy)) continue;
+      const int idx = j * FW + i;
+      const int gs = gy - 1, gn = gy + 1 < ny ? gy + 1 : ny - 1;
+      auto lam_at = [&](int row, int jj, int di) -> float {
+        return g.solid_row(row) ? wall_lam(row) : sRho[jj * FW + i + di] * cvk;
+      };
+      const float lE = lam_at(gy, j, 1), lW = lam_at(gy, j, -1);
+      const float lN = lam_at(gn, j + 1, 0), lS = lam_at(gs, j - 1, 0);
+      const float lNE = lam_at(gn, j + 1, 1), lNW = lam_at(gn, j + 1, -1);
+      const float lSE = lam_at(gs, j - 1, 1), lSW = lam_at(gs, j - 1, -1);
+      const float glx = (lE - lW) * (1.f / 3.f) + ((lNE - lSW) + (lSE - lNW)) * (1.f / 12.f);
+      const float gly = (lN - lS) * (1.f / 3.f) + ((lNE - lSW) + (lNW - lSE)) * (1.f / 12.f);
+      const float ircv = sIrcv[idx];
+      const float ux = sUx[idx], uy = sUy[idx];
+      sUx[idx] = ux - ircv * glx;
+      sUy[idx] = uy - ircv * gly;
+    }
+    __syncthreads();
+  }
 
   // ---- RK4 stages (Eq. 18): stage k on ring 4-k (stage 4 on the output cells
   // only); h1 + 2 h2 + 2 h3 kept in registers
@@ -576,7 +608,24 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
       const int js = j - 1, jn = j + 1;
       const float Tp = Tc[idx];
       float hk = 0.f;
-      if (INT || !g.dirichlet_row(gy)) {
+      if (ISO && !g.dirichlet_row(gy)) {
+        const float TE = Tc[idx + 1], TW = Tc[idx - 1], TN = Tc[jn * FW + i], TS = Tc[js * FW + i];
+        const float TNE = Tc[jn * FW + i + 1], TNW = Tc[jn * FW + i - 1];
+        const float TSE = Tc[js * FW + i + 1], TSW = Tc[js * FW + i - 1];
+        // Eq. (20) Laplacian times lambda / (rho cv); the grad(lambda) part of
+        // Eq. (21) rides in the advection velocity (after pass C)
+        const float lap = (((TNE + TNW) + (TSE + TSW)) + 4.f * ((TE + TW) + (TN + TS)) - 20.f * Tp) * (1.f / 6.f);
+        const bool solid = g.solid_row(gy);
+        float kk = (solid ? A.kd_w : A.kd) * lap;
+        const float gxT = (TE - TW) * (1.f / 3.f) + ((TNE - TSW) + (TSE - TNW)) * (1.f / 12.f);
+        const float gyT = (TN - TS) * (1.f / 3.f) + ((TNE - TSW) + (TNW - TSE)) * (1.f / 12.f);
+        kk -= sUx[idx] * gxT + sUy[idx] * gyT;
+        if (!solid) {
+          const float sTr = sqrtf(fmaxf(Tp, 0.f) * A.invTc);
+          kk -= sAs[idx] * Tp + sBs[idx] * (1.f + A.kappa * (1.f - sTr)) * sTr;
+        }
+        hk = kk;
+      } else if (!ISO && (INT || !g.dirichlet_row(gy))) {
         const float TE = Tc[idx + 1], TW = Tc[idx - 1], TN = Tc[jn * FW + i], TS = Tc[js * FW + i];
         // Eqs. (22)-(26): sum of face fluxes over the control volume
         float kk = sLae[idx] * (TE - Tp) + sLae[idx - 1] * (TW - Tp) + sLan[idx] * (TN - Tp) +
@@ -656,7 +705,9 @@ __global__ void __launch_bounds__(NTH, MINB) k_step(const StepArgs A) {
   extern __shared__ float sm[];
   const float Uc = (float)A.state->Uc, rho_ave = (float)A.state->rho_ave;
   const int part = blockIdx.y * gridDim.x + blockIdx.x;
-  if (tile_interior(A, blockIdx.y * TY, TY))
+  if (A.iso)
+    step_tile<TY, NTH, false, true>(A, blockIdx.x, blockIdx.y, part, sm, Uc, rho_ave);
+  else if (tile_interior(A, blockIdx.y * TY, TY))
     step_tile<TY, NTH, true>(A, blockIdx.x, blockIdx.y, part, sm, Uc, rho_ave);
   else
     step_tile<TY, NTH, false>(A, blockIdx.x, blockIdx.y, part, sm, Uc, rho_ave);

@@ -316,16 +316,19 @@ __device__ __forceinline__ void march_C(const StepArgs& A, const MarchRows& R, c
   constexpr int s6 = Slot<PH, 2, MARCH_DL>::v, s6n = Slot<PH, 1, MARCH_DL>::v, s6s = Slot<PH, 3, MARCH_DL>::v;
   if (!R.in(y, 4, 3) || !th.act) return;
   const int i = th.i;
-  const float lam_w = A.lambda_w, cvk = A.cvk;
+  const float cvk = A.cvk;
+  // conductivity of a solid row: the heater's, or the top wall's (Section 3.2)
+  auto wall_lam = [&](int row) -> float { return R.top_wall && row == R.ny - 1 ? A.lambda_top : A.lambda_w; };
   const SRow RH = C.q3(R3_RHO, s3);
   const bool solid = R.solid(y);
-  const float lam = solid ? lam_w : RH[i] * cvk;
+  const float lam = solid ? wall_lam(y) : RH[i] * cvk;
   {
-    const float le = solid ? lam_w : RH[th.ie] * cvk;
+    const float le = solid ? wall_lam(y) : RH[th.ie] * cvk;
     C.q6(R6_LE, s6)[i] = 2.f * lam * le / (lam + le);
   }
   {
-    const float ln = R.solid(y + 1 < R.ny ? y + 1 : R.ny - 1) ? lam_w : C.q3(R3_RHO, s3n)[i] * cvk;
+    const int yn = y + 1 < R.ny ? y + 1 : R.ny - 1;
+    const float ln = R.solid(yn) ? wall_lam(yn) : C.q3(R3_RHO, s3n)[i] * cvk;
     C.q6(R6_LN, s6)[i] = 2.f * lam * ln / (lam + ln);
   }
   if (y < R.ys - 3) return;  // the fourth halo row only needs its north face

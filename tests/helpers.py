@@ -14,7 +14,8 @@ def coexistence():
     return dict(Tc=pr.Tc, Ts=Ts, rho_l=rl, rho_v=rv)
 
 
-def oracle_domain(case: wl.Case, coex, rho0=None, T0=None) -> ODomain:
+def oracle_domain(case: wl.Case, coex, rho0=None, T0=None, **extra) -> ODomain:
+    """The FP64 reference domain of a case; `extra` overrides Params fields."""
     Tc = coex["Tc"]
     if rho0 is None:
         rho0, T0 = wl.initial_fields(case, coex["rho_l"], coex["rho_v"], Tc)
@@ -24,15 +25,18 @@ def oracle_domain(case: wl.Case, coex, rho0=None, T0=None) -> ODomain:
         kw["lambda_w"] = coex["rho_v"] * 6.0 * 0.1
     p = OParams(nx=case.nx, ny=case.ny, wall_rows=case.wall_rows, top_bc=case.top_bc,
                 T_bottom=case.T_bottom(Tc), T_top=case.T_top(Tc), eos_T_fixed=case.eos_T_fixed,
-                g_y=case.g_y, Gw=Gw, rho_l=coex["rho_l"], rho_v=coex["rho_v"], **kw)
+                g_y=case.g_y, Gw=Gw, rho_l=coex["rho_l"], rho_v=coex["rho_v"], **{**kw, **extra})
     return ODomain(p, rho0, T0)
 
 
-def gpu_domain(case: wl.Case, coex, storage=0, rho0=None, T0=None):
+def gpu_domain(case: wl.Case, coex, storage=0, rho0=None, T0=None, **extra):
+    """The library domain of a case; `extra` overrides hlb_params fields."""
     import torch
     from paper_1812_10375_gb300 import hlb
     from paper_1812_10375_gb300.config import params_for
     p, Tc = params_for(case, storage=storage, rho_l=coex["rho_l"], rho_v=coex["rho_v"])
+    for k, v in extra.items():
+        setattr(p, k, v)
     d = hlb.Domain(p)
     if rho0 is None:
         rho0, T0 = wl.initial_fields(case, coex["rho_l"], coex["rho_v"], Tc)

@@ -232,15 +232,17 @@ def test_energy_rhs_converges_to_eq17(coex):
     assert 3.0 < e1 / e2 < 5.0
 
 
-def _steady_wall_flux_difference(coex, scheme):
+def _steady_wall_flux_difference(coex, scheme, rho0=None):
     """Exact discrete steady state of conduction (u = 0, frozen rho) through a
     flat liquid-vapour interface between walls at T = 1 and T = 0 (Section 3.2,
     transposed to y), solved as the linear system K(T) = 0; returns the paper's
-    relative wall-flux difference 2 |q_h - q_l| / (q_h + q_l)."""
+    relative wall-flux difference 2 |q_h - q_l| / (q_h + q_l).  rho0: the
+    density field (4 x 120; default a tanh interface at mid height)."""
     nx, ny = 4, 120
     # liquid in the lower half, vapour in the upper half; each Dirichlet row
     # conducts like the phase next to it (the paper's boundaries are fluid nodes)
-    rho0 = wl.tanh_film(ny, nx, coex["rho_l"], coex["rho_v"], ny / 2.0)
+    if rho0 is None:
+        rho0 = wl.tanh_film(ny, nx, coex["rho_l"], coex["rho_v"], ny / 2.0)
     p = Params(nx=nx, ny=ny, wall_rows=1, top_bc="wall", T_bottom=1.0, T_top=0.0, eos_T_fixed=True,
                rho_l=coex["rho_l"], rho_v=coex["rho_v"], lambda_w=coex["rho_l"] * 6.0 * 0.1,
                lambda_top=coex["rho_v"] * 6.0 * 0.1, diffusion=scheme)
