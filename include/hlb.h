@@ -62,6 +62,13 @@ enum { HLB_STORE_DEVIATION = 0, HLB_STORE_PLAIN = 1 };
  * batches and the row-marching kernel reject it. */
 enum { HLB_DIFF_FV = 0, HLB_DIFF_ISO = 1 };
 
+/* Bottom thermal boundary: row 0 held at T_bottom (default), or heated by an
+ * imposed flux q_in (heat per unit time and unit length entering row 0
+ * through its bottom face, Section 3.3); row 0 then evolves like the other
+ * heater rows.  q_bottom in the diagnostics is always the flux through the
+ * face between rows 0 and 1. */
+enum { HLB_BOTTOM_DIRICHLET = 0, HLB_BOTTOM_FLUX = 1 };
+
 /*
  * Model and geometry parameters, all in lattice units (dx = dt = 1, Section 3.1).
  * hlb_params_default fills the paper's values; fields marked "<= 0: default"
@@ -88,6 +95,8 @@ typedef struct {
   double lambda_top;                   /* conductivity of a top wall row; <= 0: lambda_w
                                           (Section 3.2: each wall conducts like the phase
                                           next to it)                                   */
+  int bottom_bc;                       /* HLB_BOTTOM_DIRICHLET (default) | HLB_BOTTOM_FLUX */
+  double q_in;                         /* imposed heat flux into row 0 (HLB_BOTTOM_FLUX) */
 } hlb_params;
 
 /* One nucleation site: a linear drop of G_w from Gw0 to gw_min at x_center over

@@ -111,6 +111,8 @@ class Params:
     rho_l: float | None = None      # coexistence densities at Ts (Maxwell if None)
     rho_v: float | None = None
     diffusion: str = "fv"          # "fv" (Eqs. 22-26) or "iso" (Eqs. 20-21, the comparison scheme)
+    bottom_bc: str = "dirichlet"   # row 0 held at T_bottom, or "flux": heat q_in per unit time and
+    q_in: float = 0.0              # unit length enters row 0 through its bottom face (Section 3.3)
 
     def resolved(self) -> "Params":
         p = Params(**{k: getattr(self, k) for k in self.__dataclass_fields__})
@@ -202,8 +204,10 @@ class Domain:
         self.solid = solid
         self.fluid = ~solid
         self.n_fluid = int(self.fluid.sum())
-        dirichlet = y == 0
-        Tfix = np.where(y == 0, p.T_bottom, 0.0)
+        if p.bottom_bc not in ("dirichlet", "flux"):
+            raise ValueError("bottom_bc must be 'dirichlet' or 'flux'")
+        dirichlet = (y == 0) & (p.bottom_bc == "dirichlet")
+        Tfix = np.where(dirichlet, p.T_bottom, 0.0)
         if p.top_bc == TOP_WALL:
             dirichlet = dirichlet | (y == ny - 1)
             Tfix = np.where(y == ny - 1, p.T_top, Tfix)
@@ -338,6 +342,11 @@ class Domain:
             diff = (c["lam_e"] * (_at(P, 1, 0) - T) + c["lam_w"] * (_at(P, -1, 0) - T)
                     + c["lam_n"] * (_at(P, 0, 1) - T) + c["lam_s"] * (_at(P, 0, -1) - T))
         k = diff / c["rcv"]
+        if self.p.bottom_bc == "flux":
+            # Section 3.3: the imposed heat flux enters row 0's control volume from
+            # below (beyond the lattice T is the edge copy, so no other flux crosses
+            # that face)
+            k[0] = k[0] + self.p.q_in / c["rcv"][0]
         gx, gy = iso_grad(T)
         adv = c["ux"] * gx + c["uy"] * gy
         src = _eos.T_dp_dT(c["rho"], T, self.p.eos) / c["rcv"] * c["divu"]

@@ -183,6 +183,8 @@ bool params_valid(const hlb_params* p) {
   if (p->n_sub != 1) return false;  // the fused kernel's halo is sized for N = 1
   if (p->storage != HLB_STORE_DEVIATION && p->storage != HLB_STORE_PLAIN) return false;
   if (p->diffusion != HLB_DIFF_FV && p->diffusion != HLB_DIFF_ISO) return false;
+  if (p->bottom_bc != HLB_BOTTOM_DIRICHLET && p->bottom_bc != HLB_BOTTOM_FLUX) return false;
+  if (!isfinite(p->q_in)) return false;
   if (!(p->a > 0 && p->b > 0 && p->R > 0 && p->Ts_over_Tc > 0)) return false;
   if (!(p->s_e > 0 && p->s_e < 2 && p->s_zeta > 0 && p->s_zeta < 2 && p->s_j > 0 && p->s_j < 2 &&
         p->s_q > 0 && p->s_q < 2))
@@ -388,6 +390,8 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
   a.inv_rcv_w = (float)(1.0 / (q.rho_w * q.cv_w));
   a.lambda_w = (float)q.lambda_w;
   a.lambda_top = (float)(q.lambda_top > 0 ? q.lambda_top : q.lambda_w);
+  a.bottom_flux = q.bottom_bc == HLB_BOTTOM_FLUX ? 1 : 0;
+  a.q_in = (float)q.q_in;
   a.dt = (float)(1.0 / q.n_sub);
   a.iso = q.diffusion == HLB_DIFF_ISO ? 1 : 0;
   a.kd = (float)q.k;
@@ -1313,6 +1317,8 @@ extern "C" hlb_status hlb_step_static(const hlb_params* p, int n_sites, const hl
   a.inv_rcv_w = (float)(1.0 / (q.rho_w * q.cv_w));
   a.lambda_w = (float)q.lambda_w;
   a.lambda_top = (float)(q.lambda_top > 0 ? q.lambda_top : q.lambda_w);
+  a.bottom_flux = q.bottom_bc == HLB_BOTTOM_FLUX ? 1 : 0;
+  a.q_in = (float)q.q_in;
   a.dt = (float)(1.0 / q.n_sub);
   a.iso = q.diffusion == HLB_DIFF_ISO ? 1 : 0;
   a.kd = (float)q.k;

@@ -44,6 +44,8 @@ struct StepArgs {
   // energy (Eq. 17)
   float cvk, cv, rcv_w, inv_rcv_w, lambda_w, dt;
   float lambda_top;  // conductivity of a top wall row
+  int bottom_flux;   // row 0 heated by the imposed flux q_in instead of held at T_bottom
+  float q_in;
   int iso;          // isotropic central diffusion (Eqs. 20-21) instead of the finite-volume faces
   float kd, kd_w;   // lambda / (rho cv) of the fluid (k) and of the solid
   float T_bottom, T_top;

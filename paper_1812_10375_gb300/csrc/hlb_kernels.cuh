@@ -38,9 +38,11 @@ __device__ __forceinline__ bool nonfinite(float v) {
 
 struct Geo {
   int nx, ny, W;
-  bool top_wall, top_open;
+  bool top_wall, top_open, bottom_flux;
   __device__ __forceinline__ bool solid_row(int y) const { return y < W || (top_wall && y == ny - 1); }
-  __device__ __forceinline__ bool dirichlet_row(int y) const { return y == 0 || (top_wall && y == ny - 1); }
+  __device__ __forceinline__ bool dirichlet_row(int y) const {
+    return (y == 0 && !bottom_flux) || (top_wall && y == ny - 1);
+  }
 };
 
 __device__ __forceinline__ Geo make_geo(const StepArgs& A) {
@@ -50,6 +52,7 @@ __device__ __forceinline__ Geo make_geo(const StepArgs& A) {
   g.W = A.W;
   g.top_wall = A.top_bc == TOP_WALL;
   g.top_open = A.top_bc != TOP_WALL;
+  g.bottom_flux = A.bottom_flux != 0;
   return g;
 }
 
@@ -325,7 +328,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
   const unsigned diag = INT ? 0u : eq(1) | eq(A.W) | eq(ny - 2) | eq(ny - 1);
   const bool tw = g.top_wall;
   const unsigned solid = lt(A.W) | (tw ? ALL & ~lt(ny - 1) : 0u);      // solid_row(min(gy, ny - 1))
-  const unsigned dirich = eq(0) | (tw ? eq(ny - 1) : 0u);                // dirichlet_row(gy)
+  const unsigned dirich = (g.bottom_flux ? 0u : eq(0)) | (tw ? eq(ny - 1) : 0u);  // dirichlet_row(gy)
   const unsigned sol_below = lt(A.W + 1) | (tw ? eq(ny) : 0u);          // solid_row(gy - 1)
   const unsigned sol_above = lt(A.W - 1) | (tw ? ALL & ~lt(ny - 2) : 0u);  // solid_row(min(gy + 1, ny - 1))
   const unsigned rf = ring4 | ring5 << 8 | ownr << 16 | diag << 24;
@@ -608,10 +611,14 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
       const int js = j - 1, jn = j + 1;
       const float Tp = Tc[idx];
       float hk = 0.f;
+      // row 0 under an imposed flux (Section 3.3): beyond the lattice T is the
+      // edge copy, and the heat q_in enters through the bottom face instead
+      const bool bot = !INT && gy == 0;
       if (ISO && !g.dirichlet_row(gy)) {
-        const float TE = Tc[idx + 1], TW = Tc[idx - 1], TN = Tc[jn * FW + i], TS = Tc[js * FW + i];
+        const float TE = Tc[idx + 1], TW = Tc[idx - 1], TN = Tc[jn * FW + i];
+        const float TS = bot ? Tp : Tc[js * FW + i];
         const float TNE = Tc[jn * FW + i + 1], TNW = Tc[jn * FW + i - 1];
-        const float TSE = Tc[js * FW + i + 1], TSW = Tc[js * FW + i - 1];
+        const float TSE = bot ? TE : Tc[js * FW + i + 1], TSW = bot ? TW : Tc[js * FW + i - 1];
         // Eq. (20) Laplacian times lambda / (rho cv); the grad(lambda) part of
         // Eq. (21) rides in the advection velocity (after pass C)
         const float lap = (((TNE + TNW) + (TSE + TSW)) + 4.f * ((TE + TW) + (TN + TS)) - 20.f * Tp) * (1.f / 6.f);
@@ -624,12 +631,17 @@ __device__ __forceinline__ void step_tile(const StepArgs& A, int bx, int by, int
           const float sTr = sqrtf(fmaxf(Tp, 0.f) * A.invTc);
           kk -= sAs[idx] * Tp + sBs[idx] * (1.f + A.kappa * (1.f - sTr)) * sTr;
         }
+        if (bot) kk += A.q_in * sIrcv[idx];
         hk = kk;
       } else if (!ISO && (INT || !g.dirichlet_row(gy))) {
         const float TE = Tc[idx + 1], TW = Tc[idx - 1], TN = Tc[jn * FW + i], TS = Tc[js * FW + i];
         // Eqs. (22)-(26): sum of face fluxes over the control volume
-        float kk = sLae[idx] * (TE - Tp) + sLae[idx - 1] * (TW - Tp) + sLan[idx] * (TN - Tp) +
-                   sLan[js * FW + i] * (TS - Tp);
+        // (an explicit multiply-add chain, so that every kernel that inlines this
+        // tile step rounds the face sum the same way)
+        float kk = sLae[idx] * (TE - Tp);
+        kk = fmaf(sLae[idx - 1], TW - Tp, kk);
+        kk = fmaf(sLan[idx], TN - Tp, kk);
+        kk = bot ? kk + A.q_in : fmaf(sLan[js * FW + i], TS - Tp, kk);
         kk *= sIrcv[idx];
         if (INT || !g.solid_row(gy)) {
           const float TNE = Tc[jn * FW + i + 1], TNW = Tc[jn * FW + i - 1];

@@ -107,9 +107,11 @@ struct MarchThread {
 // Row classes (uniform over the CTA).
 struct MarchRows {
   int nx, ny, W, ys, ye, t_first;
-  bool top_wall, top_open;
+  bool top_wall, top_open, bottom_flux;
   __device__ __forceinline__ bool solid(int y) const { return y < W || (top_wall && y == ny - 1); }
-  __device__ __forceinline__ bool dirichlet(int y) const { return y == 0 || (top_wall && y == ny - 1); }
+  __device__ __forceinline__ bool dirichlet(int y) const {
+    return (y == 0 && !bottom_flux) || (top_wall && y == ny - 1);
+  }
   // rows a phase covers: [ys - lo, ye + hi) within the lattice; row ny is
   // the zero-gradient ghost above an open top, copied from row ny - 1 by
   // every phase whose range reaches the top row
@@ -401,7 +403,13 @@ __device__ __forceinline__ void march_S(const StepArgs& A, const MarchRows& R, c
       const SRow LN = C.q6(R6_LN, c6);
       const SRow LNs = C.q6(R6_LN, c6s);
       const float TE = Tc[th.ie], TW = Tc[th.iw], TN = Tcn[i], TS = Tcs[i];
-      float kk = LE[i] * (TE - Tp) + LE[th.iw] * (TW - Tp) + LN[i] * (TN - Tp) + LNs[i] * (TS - Tp);
+      // row 0 under an imposed flux (Section 3.3): q_in enters through its bottom face
+      const bool bot = y == 0;
+      float kk;
+      if (bot)
+        kk = LE[i] * (TE - Tp) + LE[th.iw] * (TW - Tp) + LN[i] * (TN - Tp) + A.q_in;
+      else
+        kk = LE[i] * (TE - Tp) + LE[th.iw] * (TW - Tp) + LN[i] * (TN - Tp) + LNs[i] * (TS - Tp);
       kk *= C.q6(R6_IRCV, c6)[i];
       if (!R.solid(y)) {
         const float TNE = Tcn[th.ie], TNW = Tcn[th.iw];
@@ -482,6 +490,7 @@ __device__ __forceinline__ void march_segment(const StepArgs& A, int ys, int ye,
   R.ye = ye;
   R.top_wall = g.top_wall;
   R.top_open = g.top_open;
+  R.bottom_flux = g.bottom_flux;
   MarchCtx C;
   C.sm = sm;
 

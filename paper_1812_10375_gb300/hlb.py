@@ -18,6 +18,7 @@ HLB_OK, HLB_EINVAL, HLB_ECUDA, HLB_EUNSTABLE, HLB_ETIMEOUT, HLB_ESTATE = 0, -1, 
 HLB_TOP_WALL, HLB_TOP_CONST_RHO, HLB_TOP_CONVECTIVE = 0, 1, 2
 HLB_STORE_DEVIATION, HLB_STORE_PLAIN = 0, 1
 HLB_DIFF_FV, HLB_DIFF_ISO = 0, 1
+HLB_BOTTOM_DIRICHLET, HLB_BOTTOM_FLUX = 0, 1
 TOP_KIND = {"wall": HLB_TOP_WALL, "const_rho": HLB_TOP_CONST_RHO, "convective": HLB_TOP_CONVECTIVE}
 
 
@@ -27,7 +28,7 @@ class hlb_params(C.Structure):
             "a", "b", "R", "omega", "Ts_over_Tc", "G", "sigma", "sigma_coef",
             "s_rho", "s_e", "s_zeta", "s_j", "s_q", "tau_l", "tau_v", "cv", "k",
             "rho_w", "cv_w", "lambda_w", "g_y", "Gw0", "T_bottom", "T_top", "rho_l", "rho_v")] + [
-        ("diffusion", C.c_int), ("lambda_top", C.c_double)]
+        ("diffusion", C.c_int), ("lambda_top", C.c_double), ("bottom_bc", C.c_int), ("q_in", C.c_double)]
 
 
 class hlb_site(C.Structure):

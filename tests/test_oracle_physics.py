@@ -95,6 +95,48 @@ def test_series_resistance_steady_state_is_exact(coex, paper):
     assert 2 * abs(g["q_bottom"] - g["q_top"]) / (g["q_bottom"] + g["q_top"]) < paper["fv_relative_flux_difference_max"]["value"]
 
 
+@pytest.mark.parametrize("two_d", [False, True])
+def test_imposed_flux_heater_energy_balance(coex, two_d):
+    """Section 3.3's heater: heat q_in per unit time and length enters row 0
+    from below.  With u = 0 and frozen rho the face fluxes telescope, so the
+    change of sum(rho cv T) is exactly nx q_in per step minus the heat out at
+    the top wall (dropping or doubling the source breaks it; the steady-state
+    test below pins the row it enters)."""
+    p, rho0, T0 = _conduction_case(coex, two_d)
+    p.bottom_bc, p.q_in = "flux", 2e-4
+    d = Domain(p, rho0, T0, conduction_only=True).step(1)
+    E1 = d.diag()["energy"]
+    net = 0.0
+    for _ in range(300):
+        d.step(1)
+        net += p.nx * (p.q_in - d.diag()["q_top"])
+    assert d.diag()["energy"] - E1 == pytest.approx(net, rel=1e-11, abs=1e-11 * abs(E1))
+    assert not d.dirichlet[0].any()
+
+
+def test_imposed_flux_steady_state_is_exact(coex):
+    """Steady conduction under an imposed flux q with the top wall at T_top:
+    every face carries q, so T rises from the top by q times each series
+    resistance 1/(2 lambda_j) + 1/(2 lambda_j+1).  That profile must be a fixed
+    point of the energy update, and the flux reported through the face above
+    row 0 and through the top face must both equal q."""
+    p, rho0, _ = _conduction_case(coex, False)
+    p.bottom_bc, p.q_in = "flux", 3e-4
+    pr = p.resolved()
+    ny = p.ny
+    y = np.arange(ny)
+    solid = (y < p.wall_rows) | (y == ny - 1)
+    lam = np.where(solid, pr.lambda_w, rho0[:, 0] * pr.cv * pr.k)
+    res = 0.5 / lam[:-1] + 0.5 / lam[1:]
+    Ty = p.T_top + p.q_in * np.concatenate([np.cumsum(res[::-1])[::-1], [0.0]])
+    T0 = np.repeat(Ty[:, None], p.nx, axis=1)
+    d = Domain(p, rho0, T0, conduction_only=True).step(5)
+    np.testing.assert_allclose(d.T, T0, rtol=0, atol=1e-13)
+    g = d.diag()
+    assert g["q_bottom"] == pytest.approx(p.q_in, rel=1e-11)
+    assert g["q_top"] == pytest.approx(p.q_in, rel=1e-11)
+
+
 @pytest.mark.slow
 def test_flat_interface_reaches_maxwell_densities(coex):
     """Thermodynamic consistency (Sections 2.1, 3.1): the bulk densities of the
