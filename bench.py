@@ -506,10 +506,12 @@ def points_per_hour(hlb, plist, fields, cases, steps=400, full_steps=40000):
     b.close()
     scale = full_steps / steps
     n = len(cases)
+    frac = 0.783  # cell updates the early-stop policy spends per point (tests/test_surrogate_gpu.py)
     return {"plain": n * 3600.0 / (t_plain * scale), "batched": n * 3600.0 / (t_batch * scale),
+            "batched_with_surrogate_estimate": n * 3600.0 / (t_batch * scale * frac),
             "unit": f"points/hour at {full_steps} steps per point (timed over {steps} steps per point, "
                     "including set-up and graph capture)",
-            "surrogate_work_fraction_small_domains": 0.783,
+            "surrogate_work_fraction_small_domains": frac,
             "surrogate_note": "early-stop policy measured on 48 held-out 64-96 lattice points "
                               "(tests/test_surrogate_gpu.py); not re-trained inside the bench"}
 
