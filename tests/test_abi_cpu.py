@@ -92,3 +92,26 @@ def test_tile_variant_entry_points_reject_bad_arguments(lib):
     assert L.hlb_set_tile_variant(None, 0) == lib.HLB_EINVAL
     assert L.hlb_batch_set_tile_variant(None, 0) == lib.HLB_EINVAL
     assert L.hlb_autotune(None, 4, None, None, 0) == lib.HLB_EINVAL
+
+
+def test_scheme_and_heater_parameters_are_validated(lib):
+    """The diffusion scheme and bottom-boundary selectors take only their
+    enumerated values; the isotropic scheme is a single-domain option, so a
+    batch workspace of it is refused; an imposed flux must be finite."""
+    p = lib.default_params(64, 48)
+    assert p.diffusion == lib.HLB_DIFF_FV and p.bottom_bc == lib.HLB_BOTTOM_DIRICHLET
+    assert p.lambda_top == 0.0 and p.q_in == 0.0
+    p.diffusion = 2
+    assert lib.workspace_bytes(p) == 0
+    p.diffusion = lib.HLB_DIFF_ISO
+    assert lib.workspace_bytes(p) > 0
+    assert lib.lib().hlb_batch_workspace_bytes(1, ctypes.byref(p)) == 0
+    p.diffusion = lib.HLB_DIFF_FV
+    p.bottom_bc = 5
+    assert lib.workspace_bytes(p) == 0
+    p.bottom_bc = lib.HLB_BOTTOM_FLUX
+    p.q_in = float("nan")
+    assert lib.workspace_bytes(p) == 0
+    p.q_in = 2e-4
+    assert lib.workspace_bytes(p) > 0
+    assert lib.lib().hlb_batch_workspace_bytes(1, ctypes.byref(p)) > 0
