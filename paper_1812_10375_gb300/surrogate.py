@@ -6,7 +6,7 @@ the first steps of its wall-heat-flux history q(t) and predicts the run's
 quasi-steady mean wall heat flux and boiling regime.  Every forward, backward
 and Adam step runs in libhlb.so; this module only marshals arguments and keeps
 the feature scaling.  A plain full run stays the fallback: the policy only
-stops a point early when the network is confident, and the full runs judge the
+stops a point early when the network is confident, and the full runs measure the
 error of the points it stops.
 """
 from __future__ import annotations

@@ -1,6 +1,6 @@
 """Surrogate kernels against the FP64 reference (forward, gradients, Adam) and
 the sweep policy: a network trained by the project's kernels on runs of the
-method itself stops sweep points early, and full runs judge its error."""
+method itself stops sweep points early, and full runs measure its error."""
 import numpy as np
 import pytest
 
@@ -82,7 +82,7 @@ def test_adam_matches_reference():
 def test_trained_surrogate_gain_on_sweep():
     """Generate points with the batched step, train an ensemble with the CUDA
     kernels, calibrate the acceptance on separate points, and let it stop
-    held-out points early; their full runs judge the error (3% bar)."""
+    held-out points early; their full runs measure the error (3% bar)."""
     from paper_1812_10375_gb300 import surrogate as sur, sweep
     pts = sweep.make_points(256, seed=77, sides=(64, 96), sites_range=(1, 4), heater_rows=10, aspect=1.25)
     full, hist_steps = 4000, 1500
