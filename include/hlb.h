@@ -233,24 +233,29 @@ hlb_status hlb_batch_stop(hlb_batch* b, int i);
 hlb_status hlb_batch_destroy(hlb_batch* b);
 
 /* ------------------------------------------------------------- autotuning
- * The fused step kernel is compiled for several tile shapes (52 columns by a
- * few heights, with 256 or 512 threads per CTA).  hlb_tile_variants lists them
- * (returns their count; arrays may be NULL).  hlb_autotune / hlb_batch_autotune
- * run one untimed and then steps_per_variant timed steps of every variant on
- * the handle's own state, keep
- * the fastest for later steps and report its index in *chosen (and the measured
- * ms per step in h_ms[0..max_out) if h_ms is not NULL).  The timed steps are
- * ordinary steps of the simulation: a cell's update does not depend on the tile
- * shape, so the fields advance exactly as with any variant (only the order of
- * the FP64 partial sums differs).  Synchronises the stream. */
+ * The fused step is compiled in two forms: tiled kernels (52 columns by a few
+ * heights, with 256 or 512 threads per CTA; the default) and row-marching
+ * kernels (one CTA per full-width segment of 32, 48 or 64 rows, one thread per
+ * column, for lattices up to 512 columns and the finite-volume scheme only;
+ * a batch launches one kernel per row stride).  hlb_tile_variants lists them
+ * (returns their count; arrays may be NULL): a tiled variant reports its tile
+ * width, height and threads, a row-marching one reports width 0, its segment
+ * height and 0 threads.  hlb_autotune / hlb_batch_autotune run one untimed and
+ * then steps_per_variant timed steps of every variant available to the
+ * handle on its own state (others report 1e30 ms), keep the fastest for later
+ * steps and report its index in *chosen (and the measured ms per step in
+ * h_ms[0..max_out) if h_ms is not NULL).  The timed steps are ordinary steps of
+ * the simulation: every variant evaluates a cell's update with the same
+ * arithmetic (the tiled shapes bit for bit, the two forms to FP32 rounding).
+ * Synchronises the stream. */
 int hlb_tile_variants(int* h_tile_w, int* h_tile_h, int* h_threads, int max_out);
 hlb_status hlb_autotune(hlb_domain* d, int steps_per_variant, int* chosen, float* h_ms, int max_out);
 hlb_status hlb_batch_autotune(hlb_batch* b, int steps_per_variant, int* chosen, float* h_ms, int max_out);
 
-/* Select tile variant v (0 <= v < hlb_tile_variants(...)) for later steps
- * without timing anything, e.g. to reproduce a launch configuration under a
- * profiler.  HLB_EINVAL for a NULL handle or v out of range.  Fields advance
- * identically under every variant. */
+/* Select variant v (0 <= v < hlb_tile_variants(...)) for later steps without
+ * timing anything, e.g. to reproduce a launch configuration under a profiler.
+ * HLB_EINVAL for a NULL handle, v out of range, or a row-marching variant the
+ * handle cannot use (a lattice wider than 512 columns, the isotropic scheme). */
 hlb_status hlb_set_tile_variant(hlb_domain* d, int v);
 hlb_status hlb_batch_set_tile_variant(hlb_batch* b, int v);
 
