@@ -246,8 +246,9 @@ hlb_status hlb_batch_destroy(hlb_batch* b);
  * steps and report its index in *chosen (and the measured ms per step in
  * h_ms[0..max_out) if h_ms is not NULL).  The timed steps are ordinary steps of
  * the simulation: every variant evaluates a cell's update with the same
- * arithmetic (the tiled shapes bit for bit, the two forms to FP32 rounding).
- * Synchronises the stream. */
+ * arithmetic (tiled shapes differ only in the order of the FP64 partial sums,
+ * hence in the last bits of the mean density of Eq. 9; the two forms agree to
+ * FP32 rounding).  Synchronises the stream. */
 int hlb_tile_variants(int* h_tile_w, int* h_tile_h, int* h_threads, int max_out);
 hlb_status hlb_autotune(hlb_domain* d, int steps_per_variant, int* chosen, float* h_ms, int max_out);
 hlb_status hlb_batch_autotune(hlb_batch* b, int steps_per_variant, int* chosen, float* h_ms, int max_out);
