@@ -160,15 +160,47 @@ def choose_threshold(ens, results, L0, tol=0.03, floor=0.5):
     return best
 
 
-def evaluate_policy(ens, results, L0, threshold, hist_steps, full_steps, cells):
+def policy_score(prob, kind):
+    """Acceptance score from the ensemble-mean regime probabilities: 'not_film'
+    is the probability that the point does not end in film boiling (the vapour
+    film forms late, after the history window); 'no_boiling' the probability
+    that it does not boil at all, where the quasi-steady flux is a fixed
+    fraction of the early flux (transient conduction)."""
+    return 1.0 - prob[:, -1] if kind == "not_film" else prob[:, 0]
+
+
+def choose_policy(ens, results, L0, tol=0.03, floor=0.5, kind="not_film"):
+    """Acceptance by score and ensemble agreement: among the pairs (score
+    threshold, spread limit) taken from the calibration points, the one that
+    accepts the most calibration points while every accepted one stays within
+    `tol` of its full run.  Returns (score threshold, spread limit); (1.01, 0)
+    accepts nothing."""
+    hist, scal, q, _ = features(results, L0)
+    qp, spread, prob = ens.predict(hist, scal)
+    score = policy_score(prob, kind)
+    err = np.abs(qp - q) / np.maximum(np.abs(q), 1e-12)
+    best, best_n = (1.01, 0.0), 0
+    for thr in np.unique(score[score >= floor]):
+        for smax in np.unique(spread):
+            acc = (score >= thr) & (spread <= smax)
+            n = int(acc.sum())
+            if n > best_n and err[acc].max() <= tol:
+                best, best_n = (float(thr), float(smax)), n
+    return best
+
+
+def evaluate_policy(ens, results, L0, threshold, hist_steps, full_steps, cells, spread_max=None, kind="not_film"):
     """Stop a point after `hist_steps` when its acceptance score reaches the
     threshold (the ensemble-mean prediction is then the point's result), else
     run it in full.  Returns the accepted mask, the relative errors of the
     accepted points against their full runs, and the cell updates spent
     relative to running every point in full."""
     hist, scal, q, _ = features(results, L0)
-    qp, score = acceptance_score(ens, hist, scal)
+    qp, spread, prob = ens.predict(hist, scal)
+    score = policy_score(prob, kind)
     acc = score >= threshold
+    if spread_max is not None:
+        acc &= spread <= spread_max
     err = np.abs(qp - q) / np.maximum(np.abs(q), 1e-12)
     cells = np.asarray(cells, dtype=np.float64)
     spent = np.where(acc, hist_steps, full_steps) * cells
@@ -234,6 +266,68 @@ def paper_curve(ja_values, steps, cp=None):
     return rows, seconds
 
 
+# ------------------------------------------------------------------ surrogate at the sweep's scale
+def _save_results(path, res):
+    np.savez_compressed(path, history=np.stack([r.history for r in res]), q=[r.q_qs for r in res],
+                        coverage=[r.coverage for r in res], regime=[r.regime for r in res])
+
+
+def _load_results(path, pts):
+    z = np.load(path)
+    return [PointResult(c, c.T_bottom_over_Tc - wl.TS_OVER_TC, len(c.sites), z["history"][i], float(z["q"][i]),
+                        float(z["coverage"][i]), int(z["regime"][i])) for i, c in enumerate(pts)]
+
+
+def surrogate_study(n=256, full=40000, hist_steps=5000, seed=wl.BASE_SEED, n_fit=160, n_cal=48, members=4,
+                    epochs=600, cache=None):
+    """The learned early-stop policy on sweep points of the spec's scale: n
+    square domains of sides 256-512 (3-9 sites, 25-row heater, superheats
+    0.02-0.30 Tc), each run `full` steps in one batch, the first `hist_steps`
+    steps of their wall-flux histories as the network input.  An ensemble is
+    trained by the CUDA kernels on n_fit points, the acceptance threshold is
+    calibrated on the next n_cal, and the policy is evaluated on the rest
+    against their full runs.  Returns the numbers of the study (errors,
+    accepted points, work fraction, batched seconds)."""
+    import os
+    from .surrogate import Ensemble
+    pts = make_points(n, seed=seed)
+    if cache and os.path.exists(cache):
+        res, secs = _load_results(cache, pts), float("nan")
+    else:
+        res, secs = run_batched(pts, full, hist_steps)
+        if cache:
+            _save_results(cache, res)
+    fit, cal, test = res[:n_fit], res[n_fit:n_fit + n_cal], res[n_fit + n_cal:]
+    ens = Ensemble(members=members, seed=3, max_batch=max(n_fit, 64))
+    L0 = ens.members[0].net.cfg.L0
+    hist, scal, q, lab = features(fit, L0)
+    losses = ens.fit(hist, scal, q, lab, epochs=epochs, batch=64, lr=1e-3)
+    cells = [r.case.nx * r.case.ny for r in test]
+    hist_t, scal_t, q_t, _ = features(test, L0)
+    qp_t, spread_t, _ = ens.predict(hist_t, scal_t)
+    err_all = np.abs(qp_t - q_t) / np.maximum(np.abs(q_t), 1e-12)
+    policies = {}
+    thr = choose_threshold(ens, cal, L0, tol=0.03)
+    acc, err, cost = evaluate_policy(ens, test, L0, thr, hist_steps, full, cells)
+    policies["score"] = dict(threshold=thr, accepted=int(acc.sum()), max_error=float(err.max()) if len(err) else 0.0,
+                             work_fraction=cost)
+    for kind in ("not_film", "no_boiling"):
+        for tol in (0.03, 0.02):
+            thr2, smax = choose_policy(ens, cal, L0, tol=tol, kind=kind)
+            acc, err, cost = evaluate_policy(ens, test, L0, thr2, hist_steps, full, cells, spread_max=smax,
+                                             kind=kind)
+            policies[f"{kind}_spread_tol{tol}"] = dict(threshold=thr2, spread_max=smax, accepted=int(acc.sum()),
+                                                       max_error=float(err.max()) if len(err) else 0.0,
+                                                       work_fraction=cost)
+    regimes = [r.regime for r in res]
+    return dict(points=n, full_steps=full, hist_steps=hist_steps, batched_seconds=secs,
+                cell_updates=float(sum(r.case.nx * r.case.ny for r in res)) * full,
+                loss_first=[float(l[0].sum()) for l in losses], loss_last=[float(l[-1].sum()) for l in losses],
+                held_out=len(test), held_out_median_error=float(np.median(err_all)),
+                held_out_error_quartiles=[float(x) for x in np.percentile(err_all, [25, 75, 90])],
+                policies=policies, regime_counts=[int(regimes.count(k)) for k in range(5)])
+
+
 if __name__ == "__main__":
     import argparse
     import json
@@ -241,7 +335,13 @@ if __name__ == "__main__":
     ap.add_argument("--steps", type=int, default=60000)
     ap.add_argument("--ja", type=str, default="0.05,0.07,0.093,0.11,0.13,0.15,0.166,0.176,0.186,0.197,0.21,0.22,0.25,0.3")
     ap.add_argument("--cp-eos", action="store_true", help="c_p of Ja: the saturated liquid's (default c_v)")
+    ap.add_argument("--surrogate-study", action="store_true",
+                    help="instead: the early-stop policy on 256 sweep points of sides 256-512 (40,000 steps)")
+    ap.add_argument("--cache", type=str, default=None, help="npz of the study's runs (written once, then reused)")
     a = ap.parse_args()
+    if a.surrogate_study:
+        print(json.dumps(surrogate_study(cache=a.cache)))
+        raise SystemExit(0)
     cp = liquid_cp(hlb.default_params(8, 8)) if a.cp_eos else None
     rows, sec = paper_curve([float(x) for x in a.ja.split(",")], a.steps, cp=cp)
     for r in rows:
