@@ -10,10 +10,12 @@ The model is Hu & Liu, arXiv 1812.10375, Section 2:
 * energy: Eq. (17) advanced by classical RK4 (Eq. 18) with N sub-steps (Eq. 27),
   the isotropic central gradient of Eq. (19) for u.grad T and div u, and the
   finite-volume diffusion term with harmonic face conductivities of
-  Eqs. (22)-(26);
-* walls: halfway bounce-back, conjugate heater in the energy equation, constant
-  density or convective open top (Sections 3.3 and 4.2), wettability-based
-  nucleation sites (Section 4.2, Fig. 6b).
+  Eqs. (22)-(26), or, as the paper's comparison scheme, the isotropic central
+  form of Eqs. (20)-(21);
+* walls: halfway bounce-back, conjugate heater in the energy equation held at
+  T_bottom or heated by an imposed flux (Section 3.3), constant density or
+  convective open top (Sections 3.3 and 4.2), wettability-based nucleation
+  sites (Section 4.2, Fig. 6b).
 
 Every stage works on full-field arrays indexed [y, x]; x is periodic.  One step
 n takes the stored post-collision populations f*^{n-1} and T^n to f*^n and
