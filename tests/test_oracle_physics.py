@@ -317,3 +317,54 @@ def test_paper_contrast_fv_conserves_iso_does_not(coex, paper):
     print(f"relative wall-flux difference: FV {fv:.2e}, isotropic {iso:.3f}")
     assert fv < paper["fv_relative_flux_difference_max"]["value"]
     assert 0.02 < iso < 0.6
+
+
+def test_rk4_step_is_the_fourth_order_taylor_polynomial(coex):
+    """Eq. (18) on a linear problem: with u = 0 and rho frozen, Eq. (17) is the
+    affine system dT/dt = A T + b of the finite-volume faces (Eqs. 22-26), and
+    one classical RK4 step of length h maps T0 to
+    T* + P4(hA)(T0 - T*), P4(z) = 1 + z + z^2/2 + z^3/6 + z^4/24, with T* the
+    steady state.  A and b are assembled here from the harmonic face
+    conductivities on a 3 x 9 lattice (two heater rows, liquid and vapour,
+    Dirichlet bottom and top rows); a wrong stage coefficient or weight in the
+    oracle's RK4 changes P4 and fails the comparison."""
+    nx, ny, W_ = 3, 9, 2
+    rho0 = wl.tanh_slab(ny, nx, coex["rho_l"], coex["rho_v"], 3.0, 6.5)
+    rho0 = rho0 * (1.0 + 0.2 * np.sin(2 * np.pi * np.arange(nx) / nx))[None, :]
+    rng = np.random.default_rng(4)
+    T0 = 0.3 + 0.4 * rng.random((ny, nx))
+    p = Params(nx=nx, ny=ny, wall_rows=W_, top_bc="wall", T_bottom=1.0, T_top=0.1,
+               rho_l=coex["rho_l"], rho_v=coex["rho_v"], lambda_top=0.37)
+    d = Domain(p, rho0, T0, conduction_only=True)
+    pr = p.resolved()
+    solid = np.zeros((ny, nx), bool)
+    solid[:W_] = True
+    solid[ny - 1] = True
+    lam = np.where(solid, pr.lambda_w, rho0 * pr.cv * pr.k)
+    lam[ny - 1] = pr.lambda_top
+    rcv = np.where(solid, pr.rho_w * pr.cv_w, rho0 * pr.cv)
+    Tfix = np.zeros((ny, nx))
+    Tfix[0], Tfix[ny - 1] = p.T_bottom, p.T_top
+    free = [(y, x) for y in range(1, ny - 1) for x in range(nx)]
+    index = {c: k for k, c in enumerate(free)}
+    A = np.zeros((len(free), len(free)))
+    b = np.zeros(len(free))
+    for (y, x), k in index.items():
+        for yy, xx in ((y, (x + 1) % nx), (y, (x - 1) % nx), (y + 1, x), (y - 1, x)):
+            lf = 2.0 * lam[y, x] * lam[yy, xx] / (lam[y, x] + lam[yy, xx])
+            A[k, k] -= lf / rcv[y, x]
+            if (yy, xx) in index:
+                A[k, index[(yy, xx)]] += lf / rcv[y, x]
+            else:
+                b[k] += lf * Tfix[yy, xx] / rcv[y, x]
+    Ts = np.linalg.solve(A, -b)
+    z = A  # h = 1 (N = 1)
+    I = np.eye(len(free))
+    P4 = I + z + z @ z / 2 + z @ z @ z / 6 + z @ z @ z @ z / 24
+    t0 = np.array([d.T[y, x] for y, x in free])
+    expect = Ts + P4 @ (t0 - Ts)
+    d.step(1)
+    got = np.array([d.T[y, x] for y, x in free])
+    np.testing.assert_allclose(got, expect, rtol=0, atol=1e-12)
+    # and the step moved the field (the test is not vacuous)
+    assert np.abs(got - t0).max() > 1e-4
