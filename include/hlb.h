@@ -183,6 +183,40 @@ hlb_status hlb_reset_timeavg(hlb_domain* d);
 /* Release the handle (the workspace stays the caller's). */
 hlb_status hlb_destroy(hlb_domain* d);
 
+/* ------------------------------------------------------ checkpoint / resume
+ * The paper has no counterpart; long boiling runs (Section 4.3 averages the wall
+ * flux over tens of thousands of steps) need to survive a lost process.  A
+ * checkpoint is a byte image, in host memory, of everything one domain carries
+ * from a step to the next, taken at a step boundary:
+ *   a 512-byte header (magic "HLBCKPT1", format version, lattice size, wall
+ *   rows, top and bottom boundary kinds, storage form and its reference
+ *   density, T_bottom, the step counter and the device diagnostics record with
+ *   the lagged rho_ave and outlet velocity of Eq. 9 and the running sums),
+ *   then FP32 arrays: the nine population planes (nx*ny each, the storage form
+ *   of the domain), T^{n+1}, T^n, the convective-outlet memory (3*nx), the
+ *   wetting table (nx), then, 8-byte aligned, the hist_len FP64 entries of the
+ *   per-step wall-flux history.
+ * Stepping a domain restored from a checkpoint gives bit-for-bit the states the
+ * saved domain would have reached (same library build and variant).
+ *
+ * hlb_checkpoint_bytes: the largest checkpoint of a domain with parameters p
+ * (full flux history); 0 on invalid parameters.
+ * hlb_checkpoint_save: writes the checkpoint of the state after the last step
+ * into h_buf[0..cap) and its length into *h_len (synchronises the stream).
+ * HLB_ESTATE before hlb_set_fields; HLB_EINVAL if cap is too small.
+ * hlb_checkpoint_load: replaces the domain's state by the checkpoint in
+ * h_buf[0..len) (synchronises).  The lattice size, wall rows, boundary kinds and
+ * storage form (with its reference density) must equal the domain's, else
+ * HLB_EINVAL and the domain is unchanged; the other model parameters are the
+ * domain's own.  T_bottom and the wetting table are restored from the
+ * checkpoint.  A checkpoint whose error word is set restores that word too
+ * (later steps then return HLB_ESTATE).
+ * hlb_batch_checkpoint_save / _load: the same for domain i of a batch; loading
+ * makes domain i active again. */
+size_t hlb_checkpoint_bytes(const hlb_params* p);
+hlb_status hlb_checkpoint_save(hlb_domain* d, void* h_buf, size_t cap, size_t* h_len);
+hlb_status hlb_checkpoint_load(hlb_domain* d, const void* h_buf, size_t len);
+
 /* ------------------------------------------------------------------ batch
  * A boiling-curve sweep: n independent domains (each with its own size,
  * superheat and sites) advanced together.  One step is a single launch of the
@@ -229,6 +263,10 @@ hlb_status hlb_batch_flux_history(hlb_batch* b, int i, double* h_out, int max_le
 /* Stop domain i: later batch steps skip it and its state stays readable
  * (early stop of a sweep point). */
 hlb_status hlb_batch_stop(hlb_batch* b, int i);
+
+/* Checkpoint of domain i (see hlb_checkpoint_save / hlb_checkpoint_load). */
+hlb_status hlb_batch_checkpoint_save(hlb_batch* b, int i, void* h_buf, size_t cap, size_t* h_len);
+hlb_status hlb_batch_checkpoint_load(hlb_batch* b, int i, const void* h_buf, size_t len);
 
 hlb_status hlb_batch_destroy(hlb_batch* b);
 

@@ -676,6 +676,133 @@ hlb_status set_batch_variant(hlb_batch* b, int v) {
   return upload_tables(b);
 }
 
+// ------------------------------------------------------------ checkpoints
+// Byte image of a domain's carried state (layout in include/hlb.h).
+constexpr unsigned long long CKPT_MAGIC = 0x3154504b43424c48ull;  // "HLBCKPT1" read little-endian
+constexpr int CKPT_VERSION = 1;
+constexpr size_t CKPT_HEADER = 512;
+
+struct CkptHeader {
+  unsigned long long magic;
+  int version, header_bytes, state_bytes;
+  int nx, ny, wall_rows, top_bc, bottom_bc, storage, hist_len;
+  double rho_ref, T_bottom;
+  long long step;
+  DevState state;
+};
+static_assert(sizeof(CkptHeader) <= CKPT_HEADER, "checkpoint header does not fit its slot");
+
+// float offsets of the arrays after the header
+struct CkptLayout {
+  size_t f, T, T_prev, ftop, Gw, hist;  // hist is a byte offset, 8-byte aligned
+};
+
+CkptLayout ckpt_layout(int nx, int ny) {
+  const size_t N = (size_t)nx * ny;
+  CkptLayout L;
+  L.f = 0;
+  L.T = L.f + 9 * N;
+  L.T_prev = L.T + N;
+  L.ftop = L.T_prev + N;
+  L.Gw = L.ftop + 3 * (size_t)nx;
+  L.hist = (CKPT_HEADER + (L.Gw + nx) * sizeof(float) + 7) & ~(size_t)7;
+  return L;
+}
+
+hlb_status ckpt_save(hlb_domain* d, void* h_buf, size_t cap, size_t* h_len) {
+  if (!d || !h_buf || !h_len) return HLB_EINVAL;
+  if (!d->fields_set) return HLB_ESTATE;
+  CkptHeader h;
+  memset(&h, 0, sizeof(h));
+  if (cudaMemcpyAsync(&h.state, d->state, sizeof(DevState), cudaMemcpyDeviceToHost, d->stream) != cudaSuccess ||
+      cudaStreamSynchronize(d->stream) != cudaSuccess)
+    return HLB_ECUDA;
+  const int nx = d->p.nx, ny = d->p.ny;
+  const CkptLayout L = ckpt_layout(nx, ny);
+  const int hist_len = h.state.hist_len < 0 ? 0 : (h.state.hist_len > HIST_CAP ? HIST_CAP : h.state.hist_len);
+  const size_t need = L.hist + (size_t)hist_len * sizeof(double);
+  if (cap < need) return HLB_EINVAL;
+  h.magic = CKPT_MAGIC;
+  h.version = CKPT_VERSION;
+  h.header_bytes = (int)CKPT_HEADER;
+  h.state_bytes = (int)sizeof(DevState);
+  h.nx = nx;
+  h.ny = ny;
+  h.wall_rows = d->p.wall_rows;
+  h.top_bc = d->p.top_bc;
+  h.bottom_bc = d->p.bottom_bc;
+  h.storage = d->p.storage;
+  h.hist_len = hist_len;
+  h.rho_ref = d->rho_ref;
+  h.T_bottom = d->p.T_bottom;
+  h.step = h.state.step;
+  char* out = (char*)h_buf;
+  memset(out, 0, CKPT_HEADER);
+  memcpy(out, &h, sizeof(h));
+  float* a = (float*)(out + CKPT_HEADER);
+  const size_t N = (size_t)nx * ny;
+  const int cur = d->parity;
+  cudaStream_t s = d->stream;
+  if (cudaMemcpy2DAsync(a + L.f, N * sizeof(float), d->f[cur], (size_t)d->base.plane * sizeof(float),
+                        N * sizeof(float), 9, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(a + L.T, d->T[cur], N * sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(a + L.T_prev, d->T[cur ^ 1], N * sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(a + L.ftop, d->ftop[cur], 3 * (size_t)nx * sizeof(float), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(a + L.Gw, d->Gw, (size_t)nx * sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      (hist_len > 0 && cudaMemcpyAsync(out + L.hist, d->hist, (size_t)hist_len * sizeof(double),
+                                       cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return HLB_ECUDA;
+  *h_len = need;
+  return HLB_OK;
+}
+
+// Restore into buffer set `par` (the populations and the outlet memory go to
+// both sets, so that every buffer a later step may read holds saved values).
+hlb_status ckpt_load(hlb_domain* d, const void* h_buf, size_t len, int par) {
+  if (!d || !h_buf || len < CKPT_HEADER) return HLB_EINVAL;
+  CkptHeader h;
+  memcpy(&h, h_buf, sizeof(h));
+  const hlb_params& p = d->p;
+  if (h.magic != CKPT_MAGIC || h.version != CKPT_VERSION || h.header_bytes != (int)CKPT_HEADER ||
+      h.state_bytes != (int)sizeof(DevState))
+    return HLB_EINVAL;
+  if (h.nx != p.nx || h.ny != p.ny || h.wall_rows != p.wall_rows || h.top_bc != p.top_bc ||
+      h.bottom_bc != p.bottom_bc || h.storage != p.storage || memcmp(&h.rho_ref, &d->rho_ref, sizeof(double)) != 0)
+    return HLB_EINVAL;
+  if (h.hist_len < 0 || h.hist_len > HIST_CAP || h.state.hist_len != h.hist_len || h.step < 0 ||
+      h.state.step != h.step || !isfinite(h.T_bottom))
+    return HLB_EINVAL;
+  const CkptLayout L = ckpt_layout(p.nx, p.ny);
+  if (len < L.hist + (size_t)h.hist_len * sizeof(double)) return HLB_EINVAL;
+  const char* in = (const char*)h_buf;
+  const float* a = (const float*)(in + CKPT_HEADER);
+  const size_t N = (size_t)p.nx * p.ny;
+  cudaStream_t s = d->stream;
+  bool ok = cudaStreamSynchronize(s) == cudaSuccess;
+  for (int k = 0; k < 2 && ok; ++k) {
+    ok = cudaMemcpy2DAsync(d->f[k], (size_t)d->base.plane * sizeof(float), a + L.f, N * sizeof(float),
+                           N * sizeof(float), 9, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+         cudaMemcpyAsync(d->ftop[k], a + L.ftop, 3 * (size_t)p.nx * sizeof(float), cudaMemcpyHostToDevice, s) ==
+             cudaSuccess;
+  }
+  ok = ok &&
+       cudaMemcpyAsync(d->T[par], a + L.T, N * sizeof(float), cudaMemcpyHostToDevice, s) == cudaSuccess &&
+       cudaMemcpyAsync(d->T[par ^ 1], a + L.T_prev, N * sizeof(float), cudaMemcpyHostToDevice, s) == cudaSuccess &&
+       cudaMemcpyAsync(d->Gw, a + L.Gw, (size_t)p.nx * sizeof(float), cudaMemcpyHostToDevice, s) == cudaSuccess &&
+       (h.hist_len == 0 || cudaMemcpyAsync(d->hist, in + L.hist, (size_t)h.hist_len * sizeof(double),
+                                           cudaMemcpyHostToDevice, s) == cudaSuccess) &&
+       cudaMemcpyAsync(d->state, &h.state, sizeof(DevState), cudaMemcpyHostToDevice, s) == cudaSuccess &&
+       cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) return HLB_ECUDA;
+  d->parity = par;
+  d->steps = h.step;
+  d->fields_set = true;
+  d->host_flags = h.state.error_flags;
+  return hlb_set_wall(d, h.T_bottom);
+}
+
 }  // namespace
 
 extern "C" {
@@ -870,6 +997,20 @@ hlb_status hlb_destroy(hlb_domain* d) {
   return HLB_OK;
 }
 
+size_t hlb_checkpoint_bytes(const hlb_params* p) {
+  if (!params_valid(p)) return 0;
+  return ckpt_layout(p->nx, p->ny).hist + (size_t)HIST_CAP * sizeof(double);
+}
+
+hlb_status hlb_checkpoint_save(hlb_domain* d, void* h_buf, size_t cap, size_t* h_len) {
+  return ckpt_save(d, h_buf, cap, h_len);
+}
+
+hlb_status hlb_checkpoint_load(hlb_domain* d, const void* h_buf, size_t len) {
+  // a single domain resumes at buffer parity 0, where its step graph starts
+  return ckpt_load(d, h_buf, len, 0);
+}
+
 // ------------------------------------------------------------- batch API
 size_t hlb_batch_workspace_bytes(int n, const hlb_params* p) {
   if (n < 1 || !p) return 0;
@@ -1024,6 +1165,23 @@ hlb_status hlb_batch_stop(hlb_batch* b, int i) {
       cudaStreamSynchronize(b->stream) != cudaSuccess)
     return HLB_ECUDA;
   return HLB_OK;
+}
+
+hlb_status hlb_batch_checkpoint_save(hlb_batch* b, int i, void* h_buf, size_t cap, size_t* h_len) {
+  if (!batch_ok(b, i)) return HLB_EINVAL;
+  return ckpt_save(&b->dom[i], h_buf, cap, h_len);
+}
+
+hlb_status hlb_batch_checkpoint_load(hlb_batch* b, int i, const void* h_buf, size_t len) {
+  if (!batch_ok(b, i)) return HLB_EINVAL;
+  // the domain rejoins the batch at the batch's current buffer parity
+  hlb_status st = ckpt_load(&b->dom[i], h_buf, len, b->parity);
+  if (st != HLB_OK) return st;
+  k_lag_from_state<<<1, 32, 0, b->stream>>>(b->dom[i].state, b->d_lag + i);
+  if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
+  b->active[i] = 1;
+  batch_drop_graph(b);
+  return upload_tables(b);  // T_bottom in the descriptors, the active flag
 }
 
 hlb_status hlb_batch_destroy(hlb_batch* b) {

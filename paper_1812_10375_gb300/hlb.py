@@ -90,6 +90,11 @@ def lib() -> C.CDLL:
             "hlb_batch_autotune": (st, [vp, C.c_int, P(C.c_int), P(C.c_float), C.c_int]),
             "hlb_set_tile_variant": (st, [vp, C.c_int]),
             "hlb_batch_set_tile_variant": (st, [vp, C.c_int]),
+            "hlb_checkpoint_bytes": (sz, [P(hlb_params)]),
+            "hlb_checkpoint_save": (st, [vp, vp, sz, P(sz)]),
+            "hlb_checkpoint_load": (st, [vp, vp, sz]),
+            "hlb_batch_checkpoint_save": (st, [vp, C.c_int, vp, sz, P(sz)]),
+            "hlb_batch_checkpoint_load": (st, [vp, C.c_int, vp, sz]),
             "hlb_step_static": (st, [P(hlb_params), C.c_int, P(hlb_site), vp, vp, vp, vp, vp, vp,
                                      C.c_double, C.c_double, P(hlb_diag_record), vp]),
         }
@@ -122,6 +127,36 @@ def eos_coexistence(p: hlb_params):
 
 def workspace_bytes(p: hlb_params) -> int:
     return int(lib().hlb_workspace_bytes(C.byref(p)))
+
+
+def checkpoint_bytes(p: hlb_params) -> int:
+    """Largest checkpoint of a domain with parameters p (full flux history)."""
+    return int(lib().hlb_checkpoint_bytes(C.byref(p)))
+
+
+def _save_checkpoint(fn, name, params, *args) -> bytes:
+    cap = checkpoint_bytes(params)
+    buf = C.create_string_buffer(cap)
+    n = C.c_size_t()
+    check(name, fn(*args, buf, cap, C.byref(n)))
+    return buf.raw[:n.value]
+
+
+def write_checkpoint(path: str, blob: bytes, **meta):
+    """Store a checkpoint (and optional scalar metadata) as an .npz file,
+    replacing `path` atomically."""
+    import numpy as np
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, hlb_checkpoint=np.frombuffer(blob, dtype=np.uint8), **meta)
+    os.replace(tmp, path)
+
+
+def read_checkpoint(path: str):
+    """(blob, metadata dict) of an .npz written by write_checkpoint."""
+    import numpy as np
+    with np.load(path) as z:
+        meta = {k: z[k][()] for k in z.files if k != "hlb_checkpoint"}
+        return z["hlb_checkpoint"].tobytes(), meta
 
 
 def _ptr(t) -> C.c_void_p:
@@ -235,6 +270,16 @@ class Domain:
 
     def reset_timeavg(self):
         check("hlb_reset_timeavg", lib().hlb_reset_timeavg(self._h))
+
+    def checkpoint(self) -> bytes:
+        """Byte image of the state after the last step (see hlb_checkpoint_save)."""
+        self._enter()
+        return _save_checkpoint(lib().hlb_checkpoint_save, "hlb_checkpoint_save", self.params, self._h)
+
+    def restore(self, blob: bytes):
+        """Replace the state by a checkpoint taken with checkpoint()."""
+        self._enter()
+        check("hlb_checkpoint_load", lib().hlb_checkpoint_load(self._h, blob, len(blob)))
 
     def autotune(self, steps_per_variant=8):
         """Time every compiled tile variant on this domain and keep the fastest."""
@@ -355,6 +400,17 @@ class Batch:
 
     def stop(self, i):
         check("hlb_batch_stop", lib().hlb_batch_stop(self._h, i))
+
+    def checkpoint(self, i) -> bytes:
+        """Byte image of domain i's state after its last step."""
+        self._enter()
+        return _save_checkpoint(lib().hlb_batch_checkpoint_save, "hlb_batch_checkpoint_save", self.params[i],
+                                self._h, int(i))
+
+    def restore(self, i, blob: bytes):
+        """Replace domain i's state by a checkpoint and make it active again."""
+        self._enter()
+        check("hlb_batch_checkpoint_load", lib().hlb_batch_checkpoint_load(self._h, int(i), blob, len(blob)))
 
     def autotune(self, steps_per_variant=8):
         """Time every compiled tile variant on this batch and keep the fastest."""

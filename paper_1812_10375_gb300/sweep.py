@@ -88,21 +88,138 @@ def run_batched(cases, steps, hist_steps, stop_after=None):
                     b.stop(i)
     torch.cuda.synchronize()
     seconds = time.perf_counter() - t0
-    res = []
-    for i, c in enumerate(cases):
-        h = b.flux_history(i)
-        dg = b.diag(i, check_flags=False)
-        n = len(h)
-        if n == dg.step:
-            q_qs = float(h[n // 2:].mean()) if n >= 2 else float("nan")
-        else:  # the stored history is shorter than the run: use the running sums
-            n = dg.step
-            q_qs = (dg.q_bottom_timeavg * n - q_half[i]) / max(n - half, 1) if n > half else float("nan")
-        cov = (dg.vapour_coverage_timeavg * n - cov_half[i]) / max(n - half, 1) if n > half else float("nan")
-        res.append(PointResult(c, c.T_bottom_over_Tc - wl.TS_OVER_TC, len(c.sites), h[:hist_steps], q_qs, cov,
-                               regime_of(cov) if np.isfinite(cov) else -1))
+    res = [_point_result(c, b.flux_history(i), b.diag(i, check_flags=False), half, q_half[i], cov_half[i],
+                         hist_steps) for i, c in enumerate(cases)]
     b.close()
     return res, seconds
+
+
+def _point_result(case, h, dg, half, q_half, cov_half, hist_steps):
+    """A point's result from its flux history and diagnostics: means over the
+    second half of the run (steps half+1 .. dg.step); q_half and cov_half are
+    the running sums of q_bottom and of the wall vapour fraction at step half."""
+    n = len(h)
+    if n == dg.step:
+        q_qs = float(h[n // 2:].mean()) if n >= 2 else float("nan")
+    else:  # the stored history is shorter than the run: use the running sums
+        n = dg.step
+        q_qs = (dg.q_bottom_timeavg * n - q_half) / max(n - half, 1) if n > half else float("nan")
+    cov = (dg.vapour_coverage_timeavg * n - cov_half) / max(n - half, 1) if n > half else float("nan")
+    return PointResult(case, case.T_bottom_over_Tc - wl.TS_OVER_TC, len(case.sites), h[:hist_steps], q_qs, cov,
+                       regime_of(cov) if np.isfinite(cov) else -1)
+
+
+def run_resumable(cases, steps, hist_steps, ckpt_dir, every=2048):
+    """run_batched with a checkpoint of every point on disk each `every` steps
+    (and at the half-way step), so that a sweep cut short resumes per point.
+
+    Per point k, `ckpt_dir` holds pt<k>.ckpt.npz (the library checkpoint of
+    its last good step with the half-way running sums) and, once the point is
+    finished, pt<k>.done.npz (its result).  Calling this again with the same
+    cases and directory skips finished points and restores the others from
+    their checkpoints; points at different steps advance one group at a time
+    until they share a step.  A point whose device error word is set at a
+    checkpoint boundary (an instability of the method: the step is
+    deterministic, so running it again would fail the same way) is stopped
+    and recorded with NaN means, regime -1 and `failed_at` (the step of the
+    detection); its last good checkpoint stays on disk.
+
+    Returns (results, failed_at) with failed_at[k] = -1 for points that ran
+    to the end."""
+    import os
+    every = max(16, (int(every) + 15) // 16 * 16)  # whole graph chunks
+    half = steps // 2
+    os.makedirs(ckpt_dir, exist_ok=True)
+    ck = lambda k: os.path.join(ckpt_dir, f"pt{k:05d}.ckpt.npz")
+    dn = lambda k: os.path.join(ckpt_dir, f"pt{k:05d}.done.npz")
+    results, failed_at = [None] * len(cases), [-1] * len(cases)
+    for k, c in enumerate(cases):
+        if os.path.exists(dn(k)):
+            results[k], failed_at[k] = _load_done(dn(k), c, steps)
+    todo = [k for k in range(len(cases)) if results[k] is None]
+    if todo:
+        plist, tcs = zip(*[params_for(cases[k]) for k in todo])
+        b = hlb.Batch(list(plist))
+        pos, blobs, q_half, cov_half = [], [], [], []
+        for j, k in enumerate(todo):
+            if os.path.exists(ck(k)):
+                blob, meta = hlb.read_checkpoint(ck(k))
+                if str(meta["name"]) != cases[k].name or int(meta["steps"]) != steps:
+                    raise ValueError(f"{ck(k)} belongs to another sweep")
+                b.restore(j, blob)
+                pos.append(int(meta["step"]))
+                q_half.append(float(meta["q_half"]))
+                cov_half.append(float(meta["cov_half"]))
+            else:
+                _setup(b, j, cases[k], plist[j], tcs[j])
+                blob = None
+                pos.append(0)
+                q_half.append(0.0)
+                cov_half.append(0.0)
+            blobs.append(blob)
+        active = [True] * len(todo)
+        failed = [False] * len(todo)
+        while True:
+            left = [j for j in range(len(todo)) if pos[j] < steps and not failed[j]]
+            if not left:
+                break
+            m = min(pos[j] for j in left)
+            run = {j for j in left if pos[j] == m}
+            for j in range(len(todo)):
+                if active[j] and j not in run:
+                    b.stop(j)
+                    active[j] = False
+                elif j in run and not active[j]:
+                    b.restore(j, blobs[j])  # its own state: picks up where it stopped
+                    active[j] = True
+            nxt = min((m // every + 1) * every, steps, half if m < half else steps)
+            b.step(nxt - m)
+            for j in sorted(run):
+                k = todo[j]
+                pos[j] = nxt
+                dg = b.diag(j, check_flags=False)
+                if dg.error_flags:
+                    failed[j] = True
+                    failed_at[k] = nxt
+                    b.stop(j)
+                    active[j] = False
+                    results[k] = PointResult(cases[k], cases[k].T_bottom_over_Tc - wl.TS_OVER_TC,
+                                             len(cases[k].sites), np.zeros(0), float("nan"), float("nan"), -1)
+                    _save_done(dn(k), results[k], steps, nxt)
+                    continue
+                if nxt == half:
+                    q_half[j] = dg.q_bottom_timeavg * half
+                    cov_half[j] = dg.vapour_coverage_timeavg * half
+                blobs[j] = b.checkpoint(j)
+                hlb.write_checkpoint(ck(k), blobs[j], name=cases[k].name, steps=steps, step=nxt,
+                                     q_half=q_half[j], cov_half=cov_half[j])
+                if nxt == steps:
+                    results[k] = _point_result(cases[k], b.flux_history(j), dg, half, q_half[j], cov_half[j],
+                                               hist_steps)
+                    _save_done(dn(k), results[k], steps, -1)
+        for j, k in enumerate(todo):  # restored at the last step, finished before its result was written
+            if results[k] is None:
+                results[k] = _point_result(cases[k], b.flux_history(j), b.diag(j, check_flags=False), half,
+                                           q_half[j], cov_half[j], hist_steps)
+                _save_done(dn(k), results[k], steps, -1)
+        b.close()
+    return results, failed_at
+
+
+def _save_done(path, r, steps, failed_at):
+    import os
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, name=r.case.name, steps=steps, history=r.history, q=r.q_qs, coverage=r.coverage,
+             regime=r.regime, failed_at=failed_at)
+    os.replace(tmp, path)
+
+
+def _load_done(path, case, steps):
+    with np.load(path) as z:
+        if str(z["name"]) != case.name or int(z["steps"]) != steps:
+            raise ValueError(f"{path} belongs to another sweep")
+        return (PointResult(case, case.T_bottom_over_Tc - wl.TS_OVER_TC, len(case.sites), z["history"].copy(),
+                            float(z["q"]), float(z["coverage"]), int(z["regime"])), int(z["failed_at"]))
 
 
 def run_plain(cases, steps):

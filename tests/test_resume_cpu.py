@@ -1,0 +1,201 @@
+"""Host logic of the resumable sweep: a process lost mid-sweep resumes each
+point from its own checkpoint and ends with the results of an uninterrupted
+sweep; an unstable point is stopped, recorded and not run again.  The batch is
+a host-side fake with deterministic per-point dynamics, and the faults are
+injected on the host (an exception in place of a lost process, a set error
+word in place of a non-finite step); no GPU is used."""
+import pickle
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+
+from paper_1812_10375_gb300 import hlb, sweep
+
+
+class Lost(RuntimeError):
+    pass
+
+
+class FakeBatch:
+    """Stands in for hlb.Batch: per slot a step counter, running sums and a
+    flux history of q(step) = 1 + 0.01 * seed + 0.1 sin(0.37 step + seed)."""
+    crash_after = None  # total steps (over all instances) before a Lost is raised
+    fail = {}           # seed -> step at which the error word becomes set
+    steps_run = 0
+
+    def __init__(self, plist, stream=None):
+        self.seeds = [p.seed for p in plist]
+        self.slot = [None] * len(plist)
+        self.active = [True] * len(plist)
+
+    def _fresh(self, j):
+        return dict(step=0, qsum=0.0, csum=0.0, hist=[], err=0, seed=self.seeds[j])
+
+    def step(self, n):
+        for _ in range(n):
+            if FakeBatch.crash_after is not None and FakeBatch.steps_run >= FakeBatch.crash_after:
+                raise Lost("process lost")
+            FakeBatch.steps_run += 1
+            for j, s in enumerate(self.slot):
+                if not self.active[j]:
+                    continue
+                s["step"] += 1
+                q = 1.0 + 0.01 * s["seed"] + 0.1 * np.sin(0.37 * s["step"] + s["seed"])
+                s["qsum"] += q
+                s["csum"] += 0.5 + 0.5 * np.cos(0.11 * s["step"] * (1 + s["seed"]))
+                s["hist"].append(q)
+                if FakeBatch.fail.get(s["seed"]) == s["step"]:
+                    s["err"] = 1
+
+    def diag(self, j, check_flags=True):
+        s = self.slot[j]
+        n = max(s["step"], 1)
+        return SimpleNamespace(step=s["step"], error_flags=s["err"], q_bottom_timeavg=s["qsum"] / n,
+                               vapour_coverage_timeavg=s["csum"] / n)
+
+    def checkpoint(self, j):
+        return b"FAKE" + pickle.dumps(self.slot[j])
+
+    def restore(self, j, blob):
+        assert blob[:4] == b"FAKE"
+        self.slot[j] = pickle.loads(blob[4:])
+        self.active[j] = True
+
+    def stop(self, j):
+        self.active[j] = False
+
+    def flux_history(self, j):
+        return np.asarray(self.slot[j]["hist"])
+
+    def close(self):
+        pass
+
+
+@pytest.fixture
+def fake(monkeypatch):
+    FakeBatch.crash_after, FakeBatch.fail, FakeBatch.steps_run = None, {}, 0
+    monkeypatch.setattr(hlb, "Batch", FakeBatch)
+    monkeypatch.setattr(sweep, "params_for", lambda c: (SimpleNamespace(seed=int(c.name[2:5])), 1.0))
+    monkeypatch.setattr(sweep, "_setup", lambda b, j, c, p, Tc: b.slot.__setitem__(j, b._fresh(j)))
+    return FakeBatch
+
+
+def _cases(n=5):
+    return sweep.make_points(n, seed=11, sides=(64,), sites_range=(1, 2), heater_rows=10)
+
+
+def _same(a, b):
+    assert len(a) == len(b)
+    for x, y in zip(a, b):
+        assert x.case.name == y.case.name
+        np.testing.assert_array_equal(x.history, y.history)
+        assert (x.q_qs == y.q_qs or (np.isnan(x.q_qs) and np.isnan(y.q_qs)))
+        assert (x.coverage == y.coverage or (np.isnan(x.coverage) and np.isnan(y.coverage)))
+        assert x.regime == y.regime
+
+
+def test_lost_process_resumes_each_point_from_its_checkpoint(fake, tmp_path):
+    cases, steps = _cases(), 200
+    ref, fa_ref = sweep.run_resumable(cases, steps, 50, str(tmp_path / "ref"), every=32)
+    assert fa_ref == [-1] * len(cases)
+    full = fake.steps_run
+    assert full == steps
+    # lose the process part-way, twice, then finish
+    d = str(tmp_path / "cut")
+    for cut in (70, 100):
+        fake.steps_run, fake.crash_after = 0, cut
+        with pytest.raises(Lost):
+            sweep.run_resumable(cases, steps, 50, d, every=32)
+    fake.crash_after, fake.steps_run = None, 0
+    res, fa = sweep.run_resumable(cases, steps, 50, d, every=32)
+    _same(res, ref)
+    assert fa == fa_ref
+    # the first run was lost after its checkpoint at 64, the second (from 64,
+    # through the half-way step 100) after its checkpoint at 160: the last run
+    # steps from 160 only
+    assert fake.steps_run == steps - 160
+    # everything finished: a further call steps nothing
+    fake.steps_run = 0
+    again, _ = sweep.run_resumable(cases, steps, 50, d, every=32)
+    _same(again, ref)
+    assert fake.steps_run == 0
+
+
+def test_points_at_different_steps_realign(fake, tmp_path):
+    """A checkpoint directory where points stopped at different steps (the
+    process was lost while it wrote one boundary's checkpoints)."""
+    cases, steps = _cases(4), 160
+    ref, _ = sweep.run_resumable(cases, steps, 40, str(tmp_path / "ref"), every=32)
+    d = tmp_path / "mixed"
+    fake.crash_after, fake.steps_run = 96, 0
+    with pytest.raises(Lost):
+        sweep.run_resumable(cases, steps, 40, str(d), every=32)
+    # roll point 2 back to a fresh start and point 1 to an older checkpoint
+    (d / "pt00002.ckpt.npz").unlink()
+    blob, meta = hlb.read_checkpoint(str(d / "pt00001.ckpt.npz"))
+    assert int(meta["step"]) == 96
+    old_dir = tmp_path / "old"
+    fake.crash_after, fake.steps_run = 64, 0
+    with pytest.raises(Lost):
+        sweep.run_resumable(cases, steps, 40, str(old_dir), every=32)
+    (d / "pt00001.ckpt.npz").write_bytes((old_dir / "pt00001.ckpt.npz").read_bytes())
+    fake.crash_after, fake.steps_run = None, 0
+    res, _ = sweep.run_resumable(cases, steps, 40, str(d), every=32)
+    _same(res, ref)
+    # point 2 ran from 0 alone to 64, then with point 1 to 96, then with all
+    assert fake.steps_run == steps
+
+
+def test_unstable_point_is_recorded_and_not_rerun(fake, tmp_path):
+    cases, steps = _cases(), 200
+    bad = int(cases[3].name[2:5])
+    fake.fail = {bad: 77}
+    d = str(tmp_path / "f")
+    res, fa = sweep.run_resumable(cases, steps, 50, d, every=32)
+    assert fa[3] == 96  # detected at the first boundary after step 77
+    assert res[3].regime == -1 and np.isnan(res[3].q_qs) and np.isnan(res[3].coverage)
+    assert all(fa[k] == -1 and res[k].regime >= 0 for k in range(len(cases)) if k != 3)
+    # its last good checkpoint stays
+    _, meta = hlb.read_checkpoint(str(tmp_path / "f" / "pt00003.ckpt.npz"))
+    assert int(meta["step"]) == 64
+    # the other points match a sweep without the unstable point
+    fake.fail = {}
+    ref, _ = sweep.run_resumable([c for k, c in enumerate(cases) if k != 3], steps, 50, str(tmp_path / "r"),
+                                 every=32)
+    _same([r for k, r in enumerate(res) if k != 3], ref)
+    fake.steps_run = 0
+    res2, fa2 = sweep.run_resumable(cases, steps, 50, d, every=32)
+    assert fake.steps_run == 0 and fa2 == fa
+
+
+def test_checkpoints_of_another_sweep_are_refused(fake, tmp_path):
+    cases = _cases(3)
+    d = str(tmp_path / "x")
+    fake.crash_after = 40
+    with pytest.raises(Lost):
+        sweep.run_resumable(cases, 100, 20, d, every=32)
+    fake.crash_after, fake.steps_run = None, 0
+    with pytest.raises(ValueError):
+        sweep.run_resumable(cases, 120, 20, d, every=32)  # other length
+    with pytest.raises(ValueError):
+        sweep.run_resumable(_cases(3)[::-1], 100, 20, d, every=32)  # other points
+
+
+def test_checkpoint_file_round_trip(tmp_path):
+    blob = bytes(range(256)) * 3
+    p = str(tmp_path / "c.npz")
+    hlb.write_checkpoint(p, blob, step=48, name="pt001_64")
+    b2, meta = hlb.read_checkpoint(p)
+    assert b2 == blob and int(meta["step"]) == 48 and str(meta["name"]) == "pt001_64"
+
+
+def test_checkpoint_bytes_covers_header_fields_and_history():
+    from paper_1812_10375_gb300 import build
+    build.build()
+    p = hlb.default_params(64, 96)
+    N = 64 * 96
+    fields = 4 * (9 * N + 2 * N + 3 * 64 + 64)
+    assert hlb.checkpoint_bytes(p) == 512 + (fields + 7) // 8 * 8 + 8 * 65536
+    p.ny = 3
+    assert hlb.checkpoint_bytes(p) == 0
