@@ -22,7 +22,9 @@
  *    launched asynchronously on the handle's stream; hlb_diag and
  *    hlb_batch_flux_history synchronise that stream.
  *  - Device-side problems set a sticky error word (bit 0: non-finite value,
- *    bit 1: psi^2 < 0 outside the EOS range, bit 2: batch barrier timeout).
+ *    bit 1: psi^2 < 0 outside the EOS range, bit 2: a bounded device wait gave
+ *    up; no kernel of this library waits on another block, so bit 2 is
+ *    reserved and never set).
  *    hlb_diag reports it; once it is set, hlb_step returns HLB_ESTATE.
  *  - A handle is not thread-safe: use it from one host thread at a time.
  *  - `stream` arguments are cudaStream_t values passed as void* (NULL = the
@@ -42,7 +44,7 @@ typedef enum {
   HLB_EINVAL = -1,     /* bad argument or parameter set                  */
   HLB_ECUDA = -2,      /* a CUDA runtime call failed                      */
   HLB_EUNSTABLE = -3,  /* the device error word reports non-finite / psi  */
-  HLB_ETIMEOUT = -4,   /* a bounded device wait gave up                   */
+  HLB_ETIMEOUT = -4,   /* a bounded device wait gave up (reserved)        */
   HLB_ESTATE = -5      /* call not valid in the handle's current state    */
 } hlb_status;
 
