@@ -5,7 +5,7 @@
  *
  * One step of a domain is: D2Q9 MRT pseudo-potential collide-and-stream
  * (Section 2.1, Eqs. 1-10), Peng-Robinson EOS (Section 3.1, Eq. 28), the energy
- * equation (Eq. 17) advanced by RK4 (Eq. 18) with N sub-steps (Eq. 27) and
+ * equation (Eq. 17) advanced by one RK4 step (Eq. 18; N = 1 in Eq. 27) and
  * finite-volume diffusion with harmonic face conductivities (Eqs. 22-26),
  * halfway bounce-back walls, a conjugate heater and open tops (Sections 3.3,
  * 4.2), and the wettability nucleation sites of Section 4.2 (Fig. 6b).
@@ -81,7 +81,8 @@ typedef struct {
   int wall_rows;       /* rows y < wall_rows are solid (>= 1); row 0 has Dirichlet T */
   int top_bc;          /* HLB_TOP_*; HLB_TOP_WALL makes row ny-1 a solid Dirichlet row */
   int eos_T_fixed;     /* 1: the EOS uses Ts everywhere (Section 3.2)               */
-  int n_sub;           /* N of Eq. (27), >= 1                                        */
+  int n_sub;           /* N of Eq. (27); must be 1 (one RK4 step per LB step: the
+                          fused kernel's halo is sized for it)                       */
   int storage;         /* HLB_STORE_DEVIATION | HLB_STORE_PLAIN                      */
   double a, b, R, omega, Ts_over_Tc;   /* Eq. (28): 3/49, 2/21, 1, 0.344, 0.86        */
   double G, sigma, sigma_coef;         /* Eqs. (6)-(8): -1, 0.107, 12                 */
