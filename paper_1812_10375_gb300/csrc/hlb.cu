@@ -12,6 +12,7 @@
 #include "hlb.h"
 #include "hlb_kernels.cuh"
 #include "hlb_march.cuh"
+#include "hlb_substep.cuh"
 
 using namespace hlb;
 
@@ -67,6 +68,7 @@ dim3 grid_of(int nx, int ny, int v) {
 constexpr int GRAPH_STEPS = 16;     // steps per captured graph (even: buffers return to parity 0)
 constexpr int HIST_CAP = 1 << 16;   // wall-flux history entries kept per domain
 constexpr int INIT_BLOCKS = 304;
+constexpr int MAX_SUB = 64;  // largest N of Eq. (27)
 
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -180,7 +182,10 @@ bool params_valid(const hlb_params* p) {
   if (p->top_bc < HLB_TOP_WALL || p->top_bc > HLB_TOP_CONVECTIVE) return false;
   const int fluid_rows = p->ny - p->wall_rows - (p->top_bc == HLB_TOP_WALL ? 1 : 0);
   if (fluid_rows < 3) return false;
-  if (p->n_sub != 1) return false;  // the fused kernel's halo is sized for N = 1
+  // N of Eq. (27): the fused kernel takes the first sub-step, k_energy_substep
+  // the others (finite-volume scheme only)
+  if (p->n_sub < 1 || p->n_sub > MAX_SUB) return false;
+  if (p->n_sub > 1 && p->diffusion != HLB_DIFF_FV) return false;
   if (p->storage != HLB_STORE_DEVIATION && p->storage != HLB_STORE_PLAIN) return false;
   if (p->diffusion != HLB_DIFF_FV && p->diffusion != HLB_DIFF_ISO) return false;
   if (p->bottom_bc != HLB_BOTTOM_DIRICHLET && p->bottom_bc != HLB_BOTTOM_FLUX) return false;
@@ -210,6 +215,12 @@ struct hlb_domain {
   double* partials = nullptr;
   DevState* state = nullptr;
   double* hist = nullptr;
+  // N > 1 (Eq. 27): rho^n, u_x^n, u_y^n of the step, a T buffer and the
+  // sub-steps' per-block partials
+  float* mom = nullptr;
+  float* Tscr = nullptr;
+  double* subpart = nullptr;
+  dim3 sub_grid;
   int parity = 0;
   long long steps = 0;
   bool fields_set = false;
@@ -225,8 +236,10 @@ struct hlb_domain {
 namespace {
 
 struct Layout {
-  size_t f, T, Gw, ftop, partials, state, hist, total;
+  size_t f, T, Gw, ftop, partials, state, hist, sub, total;
 };
+
+dim3 sub_grid_of(int nx, int ny) { return dim3((nx + SUB_TX - 1) / SUB_TX, (ny + SUB_TY - 1) / SUB_TY); }
 
 Layout layout_of(const hlb_params* p) {
   Layout L;
@@ -241,6 +254,12 @@ Layout layout_of(const hlb_params* p) {
   L.partials = o; o += align_up((nblk > INIT_BLOCKS ? nblk : INIT_BLOCKS) * NPART * sizeof(double));
   L.state = o;    o += align_up(sizeof(DevState));
   L.hist = o;     o += align_up(HIST_CAP * sizeof(double));
+  L.sub = o;
+  if (p->n_sub > 1) {
+    const dim3 sg = sub_grid_of(p->nx, p->ny);
+    o += align_up(4 * N * sizeof(float));  // rho, u_x, u_y, T
+    o += align_up((size_t)sg.x * sg.y * NSUBPART * sizeof(double));
+  }
   L.total = o;
   return L;
 }
@@ -268,6 +287,31 @@ hlb_status launch_step(hlb_domain* d) {
     VARIANTS[d->variant].launch_single(d->grid, VARIANTS[d->variant].smem, d->stream, a);
   k_reduce<<<1, 256, 0, d->stream>>>(d->partials, (int)(d->grid.x * d->grid.y), d->state, 1.0 / (double)d->n_fluid,
                                      1.0 / (double)d->p.nx, d->hist, HIST_CAP);
+  if (d->p.n_sub > 1) {
+    // Eq. (27): sub-steps 2..N on the step's rho^n and u^n (recovered from the
+    // post-collision populations and T^n, with the mean density the step used)
+    const size_t N = (size_t)d->p.nx * d->p.ny;
+    float* rho = d->mom;
+    float* ux = d->mom + N;
+    float* uy = d->mom + 2 * N;
+    k_read<<<INIT_BLOCKS, 256, 0, d->stream>>>(a, d->T[d->parity], 0, rho, ux, uy);
+    float* Tcur = d->T[d->parity ^ 1];
+    float* Tother = d->Tscr;
+    const int nsub = d->p.n_sub;
+    for (int s = 2; s <= nsub; ++s) {
+      k_energy_substep<<<d->sub_grid, SUB_NT, sub_smem_bytes(), d->stream>>>(a, rho, ux, uy, Tcur, Tother,
+                                                                             d->subpart, s == 2, s == nsub);
+      float* t = Tcur;
+      Tcur = Tother;
+      Tother = t;
+    }
+    if (Tcur != d->T[d->parity ^ 1] &&
+        cudaMemcpyAsync(d->T[d->parity ^ 1], Tcur, N * sizeof(float), cudaMemcpyDeviceToDevice, d->stream) !=
+            cudaSuccess)
+      return HLB_ECUDA;
+    k_substep_fix<<<1, 256, 0, d->stream>>>(d->subpart, (int)(d->sub_grid.x * d->sub_grid.y), d->state,
+                                            1.0 / (double)d->p.nx, d->hist);
+  }
   if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
   d->parity ^= 1;
   d->steps += 1;
@@ -349,6 +393,12 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
   d->partials = (double*)(ws + L.partials);
   d->state = (DevState*)(ws + L.state);
   d->hist = (double*)(ws + L.hist);
+  if (q.n_sub > 1) {
+    d->mom = (float*)(ws + L.sub);
+    d->Tscr = d->mom + 3 * N;
+    d->subpart = (double*)(ws + L.sub + align_up(4 * N * sizeof(float)));
+    d->sub_grid = sub_grid_of(q.nx, q.ny);
+  }
   const int fluid_rows = q.ny - q.wall_rows - (q.top_bc == HLB_TOP_WALL ? 1 : 0);
   d->n_fluid = (long long)fluid_rows * q.nx;
   d->variant = 0;
@@ -409,6 +459,9 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
                              (int)VARIANTS[v].smem) != cudaSuccess)
       return HLB_ECUDA;
   }
+  if (q.n_sub > 1 && cudaFuncSetAttribute(k_energy_substep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sub_smem_bytes()) != cudaSuccess)
+    return HLB_ECUDA;
   if (cudaFuncSetAttribute(k_march, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem(MARCH_MAX_NX)) !=
           cudaSuccess ||
       cudaFuncSetAttribute(k_march_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1015,7 +1068,7 @@ hlb_status hlb_checkpoint_load(hlb_domain* d, const void* h_buf, size_t len) {
 size_t hlb_batch_workspace_bytes(int n, const hlb_params* p) {
   if (n < 1 || !p) return 0;
   for (int i = 0; i < n; ++i)
-    if (!params_valid(p + i) || p[i].diffusion != HLB_DIFF_FV) return 0;
+    if (!params_valid(p + i) || p[i].diffusion != HLB_DIFF_FV || p[i].n_sub != 1) return 0;
   return batch_layout(n, p).total;
 }
 
@@ -1024,7 +1077,7 @@ hlb_status hlb_batch_init(hlb_batch** out, int n, const hlb_params* p, void* d_w
   if (!out || n < 1 || !p || !d_workspace) return HLB_EINVAL;
   *out = nullptr;
   for (int i = 0; i < n; ++i)
-    if (!params_valid(p + i) || p[i].diffusion != HLB_DIFF_FV) return HLB_EINVAL;
+    if (!params_valid(p + i) || p[i].diffusion != HLB_DIFF_FV || p[i].n_sub != 1) return HLB_EINVAL;
   if (((uintptr_t)d_workspace & 255) != 0) return HLB_EINVAL;
   const BatchLayout L = batch_layout(n, p);
   if (workspace_bytes < L.total) return HLB_EINVAL;
@@ -1413,6 +1466,7 @@ extern "C" hlb_status hlb_step_static(const hlb_params* p, int n_sites, const hl
   if (!p || !d_f_in || !d_f_out || !d_T_in || !d_T_out || !h_out) return HLB_EINVAL;
   if (n_sites < 0 || n_sites > HLB_STATIC_MAX_SITES || (n_sites > 0 && !h_sites)) return HLB_EINVAL;
   if (hlb_workspace_bytes(p) == 0) return HLB_EINVAL;  // the same parameter checks as hlb_init
+  if (p->n_sub != 1) return HLB_EINVAL;                 // sub-steps need workspace scratch
   if (p->top_bc == HLB_TOP_CONVECTIVE && (!d_ftop_in || !d_ftop_out)) return HLB_EINVAL;
   if (p->nx > HLB_STATIC_MAX_NX) return HLB_EINVAL;
   const long long nblk = (long long)((p->nx + TILE_X - 1) / TILE_X) * ((p->ny + TILE_Y - 1) / TILE_Y);

@@ -65,8 +65,22 @@ def test_workspace_size_and_rejections(lib):
     assert n >= 2 * 10 * 64 * 48 * 4
     bad = lib.default_params(2, 48)
     assert lib.workspace_bytes(bad) == 0
+    # N of Eq. (27): 1..64; N > 1 adds the sub-steps' scratch (rho, u, T and
+    # the per-block partials), is a single-domain, finite-volume option, and
+    # is refused by batches
+    for bad_n in (0, -1, 65):
+        p.n_sub = bad_n
+        assert lib.workspace_bytes(p) == 0
     p.n_sub = 2
+    extra = 4 * 64 * 48 * 4 + 2 * 2 * 4 * 8  # four planes + (2 x 2 tiles of 56 x 24) x 4 FP64 partials
+    assert lib.workspace_bytes(p) >= n + extra
+    assert lib.lib().hlb_batch_workspace_bytes(1, ctypes.byref(p)) == 0
+    p.diffusion = lib.HLB_DIFF_ISO
     assert lib.workspace_bytes(p) == 0
+    p.diffusion = lib.HLB_DIFF_FV
+    w2 = lib.workspace_bytes(p)
+    p.n_sub = 64  # the scratch does not grow with N (the sub-steps reuse it)
+    assert lib.workspace_bytes(p) == w2
     # nine population planes must stay below 2^31 floats (32-bit offsets in the kernels)
     assert lib.workspace_bytes(lib.default_params(15000, 15000)) > 0
     assert lib.workspace_bytes(lib.default_params(16384, 16384)) == 0
@@ -79,7 +93,7 @@ def test_init_rejects_invalid_parameters_without_a_gpu(lib):
     st = lib.lib().hlb_init(C.byref(h), C.byref(p), C.c_void_p(256), 1 << 20, None)
     assert st == lib.HLB_EINVAL and not h.value
     q = lib.default_params(64, 64)
-    q.n_sub = 3
+    q.n_sub = 65
     assert lib.lib().hlb_init(C.byref(h), C.byref(q), C.c_void_p(256), 1 << 30, None) == lib.HLB_EINVAL
     assert lib.lib().hlb_strerror(lib.HLB_EUNSTABLE).decode().startswith("device error word")
 
