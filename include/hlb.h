@@ -5,7 +5,7 @@
  *
  * One step of a domain is: D2Q9 MRT pseudo-potential collide-and-stream
  * (Section 2.1, Eqs. 1-10), Peng-Robinson EOS (Section 3.1, Eq. 28), the energy
- * equation (Eq. 17) advanced by one RK4 step (Eq. 18; N = 1 in Eq. 27) and
+ * equation (Eq. 17) advanced by N RK4 sub-steps of dt/N (Eqs. 18, 27) and
  * finite-volume diffusion with harmonic face conductivities (Eqs. 22-26),
  * halfway bounce-back walls, a conjugate heater and open tops (Sections 3.3,
  * 4.2), and the wettability nucleation sites of Section 4.2 (Fig. 6b).
@@ -19,8 +19,8 @@
  *    hlb_init / hlb_batch_init, which must stay valid until hlb_destroy.
  *  - Host pointers are read or written only during the call.
  *  - Every call returns an hlb_status and never throws or aborts.  Kernels are
- *    launched asynchronously on the handle's stream; hlb_diag and
- *    hlb_batch_flux_history synchronise that stream.
+ *    launched asynchronously on the handle's stream; hlb_diag and the flux
+ *    history and checkpoint calls synchronise that stream.
  *  - Device-side problems set a sticky error word (bit 0: non-finite value,
  *    bit 1: psi^2 < 0 outside the EOS range, bit 2: a bounded device wait gave
  *    up; no kernel of this library waits on another block, so bit 2 is
@@ -81,8 +81,10 @@ typedef struct {
   int wall_rows;       /* rows y < wall_rows are solid (>= 1); row 0 has Dirichlet T */
   int top_bc;          /* HLB_TOP_*; HLB_TOP_WALL makes row ny-1 a solid Dirichlet row */
   int eos_T_fixed;     /* 1: the EOS uses Ts everywhere (Section 3.2)               */
-  int n_sub;           /* N of Eq. (27); must be 1 (one RK4 step per LB step: the
-                          fused kernel's halo is sized for it)                       */
+  int n_sub;           /* N of Eq. (27), 1..64 (1: the paper's parameters are stable).
+                          N > 1 holds rho^n and u^n over the sub-steps and runs for
+                          single domains with HLB_DIFF_FV; batches, the isotropic
+                          scheme and hlb_step_static take N = 1 only              */
   int storage;         /* HLB_STORE_DEVIATION | HLB_STORE_PLAIN                      */
   double a, b, R, omega, Ts_over_Tc;   /* Eq. (28): 3/49, 2/21, 1, 0.344, 0.86        */
   double G, sigma, sigma_coef;         /* Eqs. (6)-(8): -1, 0.107, 12                 */
@@ -139,7 +141,8 @@ hlb_status hlb_eos_coexistence(const hlb_params* p, double* Tc, double* rho_l, d
                                double* h_fg);
 
 /* Device bytes one domain needs (fields double-buffered, per-block FP64 partials,
- * site table, flux history).  0 on invalid parameters, which include lattices
+ * site table, flux history; for N > 1 also rho, u and T planes and the
+ * sub-steps' partials).  0 on invalid parameters, which include lattices
  * whose nine population planes would exceed 2^31 floats (about 238 million
  * cells, e.g. 15,000 x 15,000 fits, 16,384 x 16,384 does not). */
 size_t hlb_workspace_bytes(const hlb_params* p);
@@ -179,6 +182,11 @@ hlb_status hlb_read(hlb_domain* d, float* d_rho, float* d_ux, float* d_uy, float
  * stream).  Returns HLB_EUNSTABLE if the device error word is set (the record is
  * still written). */
 hlb_status hlb_diag(hlb_domain* d, hlb_diag_record* h_out);
+
+/* Copy the per-step wall heat flux q_bottom (FP64, one entry per step since
+ * hlb_set_fields, at most 65536 entries) into h_out[0..max_len); *h_len
+ * receives the number written.  Synchronises the stream. */
+hlb_status hlb_flux_history(hlb_domain* d, double* h_out, int max_len, int* h_len);
 
 /* Restart the running time averages (q_bottom, vapour coverage) at the next step. */
 hlb_status hlb_reset_timeavg(hlb_domain* d);

@@ -1193,20 +1193,24 @@ hlb_status hlb_batch_diag(hlb_batch* b, int i, hlb_diag_record* h_out) {
   return hlb_diag(&b->dom[i], h_out);
 }
 
-hlb_status hlb_batch_flux_history(hlb_batch* b, int i, double* h_out, int max_len, int* h_len) {
-  if (!batch_ok(b, i) || !h_out || max_len < 0 || !h_len) return HLB_EINVAL;
-  hlb_domain* d = &b->dom[i];
+hlb_status hlb_flux_history(hlb_domain* d, double* h_out, int max_len, int* h_len) {
+  if (!d || !h_out || max_len < 0 || !h_len) return HLB_EINVAL;
   DevState s;
-  if (cudaMemcpyAsync(&s, d->state, sizeof(s), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
-      cudaStreamSynchronize(b->stream) != cudaSuccess)
+  if (cudaMemcpyAsync(&s, d->state, sizeof(s), cudaMemcpyDeviceToHost, d->stream) != cudaSuccess ||
+      cudaStreamSynchronize(d->stream) != cudaSuccess)
     return HLB_ECUDA;
   const int len = s.hist_len < max_len ? s.hist_len : max_len;
-  if (len > 0 && (cudaMemcpyAsync(h_out, d->hist, sizeof(double) * len, cudaMemcpyDeviceToHost, b->stream) !=
+  if (len > 0 && (cudaMemcpyAsync(h_out, d->hist, sizeof(double) * len, cudaMemcpyDeviceToHost, d->stream) !=
                       cudaSuccess ||
-                  cudaStreamSynchronize(b->stream) != cudaSuccess))
+                  cudaStreamSynchronize(d->stream) != cudaSuccess))
     return HLB_ECUDA;
   *h_len = len;
   return HLB_OK;
+}
+
+hlb_status hlb_batch_flux_history(hlb_batch* b, int i, double* h_out, int max_len, int* h_len) {
+  if (!batch_ok(b, i)) return HLB_EINVAL;
+  return hlb_flux_history(&b->dom[i], h_out, max_len, h_len);
 }
 
 hlb_status hlb_batch_stop(hlb_batch* b, int i) {

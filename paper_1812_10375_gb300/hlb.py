@@ -71,6 +71,7 @@ def lib() -> C.CDLL:
             "hlb_read": (st, [vp, vp, vp, vp, vp]),
             "hlb_diag": (st, [vp, P(hlb_diag_record)]),
             "hlb_reset_timeavg": (st, [vp]),
+            "hlb_flux_history": (st, [vp, P(C.c_double), C.c_int, P(C.c_int)]),
             "hlb_destroy": (st, [vp]),
             "hlb_strerror": (C.c_char_p, [st]),
             "hlb_batch_workspace_bytes": (sz, [C.c_int, P(hlb_params)]),
@@ -270,6 +271,15 @@ class Domain:
 
     def reset_timeavg(self):
         check("hlb_reset_timeavg", lib().hlb_reset_timeavg(self._h))
+
+    def flux_history(self, max_len=65536):
+        """The per-step wall heat flux q_bottom since set_fields (FP64)."""
+        import numpy as np
+        buf = np.zeros(max_len, dtype=np.float64)
+        n = C.c_int()
+        check("hlb_flux_history", lib().hlb_flux_history(
+            self._h, buf.ctypes.data_as(C.POINTER(C.c_double)), max_len, C.byref(n)))
+        return buf[:n.value].copy()
 
     def checkpoint(self) -> bytes:
         """Byte image of the state after the last step (see hlb_checkpoint_save)."""

@@ -24,6 +24,7 @@ class PointResult:
     q_qs: float             # mean q_bottom over the second half of the run
     coverage: float         # mean wall vapour fraction over the second half
     regime: int
+    n_sub: int = 1          # N of Eq. (27) the point ran with
 
 
 def make_points(n, seed=wl.BASE_SEED, sides=(256, 320, 384, 448, 512), superheat_range=(0.02, 0.30),
@@ -94,7 +95,7 @@ def run_batched(cases, steps, hist_steps, stop_after=None):
     return res, seconds
 
 
-def _point_result(case, h, dg, half, q_half, cov_half, hist_steps):
+def _point_result(case, h, dg, half, q_half, cov_half, hist_steps, n_sub=1):
     """A point's result from its flux history and diagnostics: means over the
     second half of the run (steps half+1 .. dg.step); q_half and cov_half are
     the running sums of q_bottom and of the wall vapour fraction at step half."""
@@ -106,26 +107,31 @@ def _point_result(case, h, dg, half, q_half, cov_half, hist_steps):
         q_qs = (dg.q_bottom_timeavg * n - q_half) / max(n - half, 1) if n > half else float("nan")
     cov = (dg.vapour_coverage_timeavg * n - cov_half) / max(n - half, 1) if n > half else float("nan")
     return PointResult(case, case.T_bottom_over_Tc - wl.TS_OVER_TC, len(case.sites), h[:hist_steps], q_qs, cov,
-                       regime_of(cov) if np.isfinite(cov) else -1)
+                       regime_of(cov) if np.isfinite(cov) else -1, n_sub)
 
 
-def run_resumable(cases, steps, hist_steps, ckpt_dir, every=2048):
+def run_resumable(cases, steps, hist_steps, ckpt_dir, every=2048, retry=True):
     """run_batched with a checkpoint of every point on disk each `every` steps
     (and at the half-way step), so that a sweep cut short resumes per point.
 
     Per point k, `ckpt_dir` holds pt<k>.ckpt.npz (the library checkpoint of
-    its last good step with the half-way running sums) and, once the point is
-    finished, pt<k>.done.npz (its result).  Calling this again with the same
-    cases and directory skips finished points and restores the others from
-    their checkpoints; points at different steps advance one group at a time
-    until they share a step.  A point whose device error word is set at a
-    checkpoint boundary (an instability of the method: the step is
-    deterministic, so running it again would fail the same way) is stopped
-    and recorded with NaN means, regime -1 and `failed_at` (the step of the
+    its last good step with the half-way running sums and its N of Eq. 27)
+    and, once the point is finished, pt<k>.done.npz (its result).  Calling this
+    again with the same cases and directory skips finished points and restores
+    the others from their checkpoints; points at different steps advance one
+    group at a time until they share a step.
+
+    A point whose device error word is set at a checkpoint boundary is stopped.
+    With `retry`, it runs once more, alone, from its last good checkpoint (or
+    its initial fields) with N of Eq. (27) doubled: the explicit energy update
+    is the part of the step whose stability N controls (Section 2.2), and the
+    step being deterministic, running it again unchanged would fail the same
+    way.  A point that fails again, or any failed point without `retry`, is
+    recorded with NaN means, regime -1 and `failed_at` (the step of the
     detection); its last good checkpoint stays on disk.
 
     Returns (results, failed_at) with failed_at[k] = -1 for points that ran
-    to the end."""
+    to the end; results[k].n_sub is the N the point finished (or failed) with."""
     import os
     every = max(16, (int(every) + 15) // 16 * 16)  # whole graph chunks
     half = steps // 2
@@ -136,20 +142,28 @@ def run_resumable(cases, steps, hist_steps, ckpt_dir, every=2048):
     for k, c in enumerate(cases):
         if os.path.exists(dn(k)):
             results[k], failed_at[k] = _load_done(dn(k), c, steps)
-    todo = [k for k in range(len(cases)) if results[k] is None]
+    meta = {}
+    for k in range(len(cases)):
+        if results[k] is None and os.path.exists(ck(k)):
+            blob, m = hlb.read_checkpoint(ck(k))
+            if str(m["name"]) != cases[k].name or int(m["steps"]) != steps:
+                raise ValueError(f"{ck(k)} belongs to another sweep")
+            meta[k] = (blob, m)
+    base_n = {k: params_for(cases[k])[0].n_sub for k in range(len(cases)) if results[k] is None}
+    # points resumed inside their retry continue alone at their checkpoint's N
+    single = {k: int(meta[k][1].get("n_sub", base_n[k])) for k in meta if int(meta[k][1].get("n_sub", 1)) > base_n[k]}
+    todo = [k for k in range(len(cases)) if results[k] is None and k not in single]
     if todo:
         plist, tcs = zip(*[params_for(cases[k]) for k in todo])
         b = hlb.Batch(list(plist))
         pos, blobs, q_half, cov_half = [], [], [], []
         for j, k in enumerate(todo):
-            if os.path.exists(ck(k)):
-                blob, meta = hlb.read_checkpoint(ck(k))
-                if str(meta["name"]) != cases[k].name or int(meta["steps"]) != steps:
-                    raise ValueError(f"{ck(k)} belongs to another sweep")
+            if k in meta:
+                blob, m = meta[k]
                 b.restore(j, blob)
-                pos.append(int(meta["step"]))
-                q_half.append(float(meta["q_half"]))
-                cov_half.append(float(meta["cov_half"]))
+                pos.append(int(m["step"]))
+                q_half.append(float(m["q_half"]))
+                cov_half.append(float(m["cov_half"]))
             else:
                 _setup(b, j, cases[k], plist[j], tcs[j])
                 blob = None
@@ -180,37 +194,93 @@ def run_resumable(cases, steps, hist_steps, ckpt_dir, every=2048):
                 dg = b.diag(j, check_flags=False)
                 if dg.error_flags:
                     failed[j] = True
-                    failed_at[k] = nxt
                     b.stop(j)
                     active[j] = False
-                    results[k] = PointResult(cases[k], cases[k].T_bottom_over_Tc - wl.TS_OVER_TC,
-                                             len(cases[k].sites), np.zeros(0), float("nan"), float("nan"), -1)
-                    _save_done(dn(k), results[k], steps, nxt)
+                    if retry and 2 * plist[j].n_sub <= MAX_SUB:
+                        single[k] = 2 * plist[j].n_sub
+                    else:
+                        _record_failure(results, failed_at, k, cases[k], steps, nxt, plist[j].n_sub, dn(k))
                     continue
                 if nxt == half:
                     q_half[j] = dg.q_bottom_timeavg * half
                     cov_half[j] = dg.vapour_coverage_timeavg * half
                 blobs[j] = b.checkpoint(j)
                 hlb.write_checkpoint(ck(k), blobs[j], name=cases[k].name, steps=steps, step=nxt,
-                                     q_half=q_half[j], cov_half=cov_half[j])
+                                     q_half=q_half[j], cov_half=cov_half[j], n_sub=plist[j].n_sub)
                 if nxt == steps:
                     results[k] = _point_result(cases[k], b.flux_history(j), dg, half, q_half[j], cov_half[j],
-                                               hist_steps)
+                                               hist_steps, plist[j].n_sub)
                     _save_done(dn(k), results[k], steps, -1)
         for j, k in enumerate(todo):  # restored at the last step, finished before its result was written
-            if results[k] is None:
+            if results[k] is None and not failed[j]:
                 results[k] = _point_result(cases[k], b.flux_history(j), b.diag(j, check_flags=False), half,
-                                           q_half[j], cov_half[j], hist_steps)
+                                           q_half[j], cov_half[j], hist_steps, plist[j].n_sub)
                 _save_done(dn(k), results[k], steps, -1)
         b.close()
+    for k in sorted(single):
+        _run_single(results, failed_at, k, cases[k], single[k], steps, hist_steps, every, ck(k), dn(k))
     return results, failed_at
+
+
+MAX_SUB = 64  # the library's largest N of Eq. (27)
+
+
+def _setup_domain(d, case, p, Tc):
+    import torch
+    rho0, T0 = wl.initial_fields(case, p.rho_l, p.rho_v, Tc)
+    d.set_fields(torch.tensor(rho0, dtype=torch.float32, device="cuda"),
+                 torch.tensor(T0, dtype=torch.float32, device="cuda"))
+    d.set_nucleation_sites(case.sites)
+
+
+def _record_failure(results, failed_at, k, case, steps, at, n_sub, done_path):
+    results[k] = PointResult(case, case.T_bottom_over_Tc - wl.TS_OVER_TC, len(case.sites), np.zeros(0),
+                             float("nan"), float("nan"), -1, n_sub)
+    failed_at[k] = at
+    _save_done(done_path, results[k], steps, at)
+
+
+def _run_single(results, failed_at, k, case, n_sub, steps, hist_steps, every, ck_path, done_path):
+    """One sweep point alone in a domain with N = n_sub, from its checkpoint
+    (taken at any N: the checkpoint holds state, not the model) or from its
+    initial fields, with checkpoints as in the batch; no further retry."""
+    import os
+    half = steps // 2
+    p, Tc = params_for(case)
+    p.n_sub = n_sub
+    d = hlb.Domain(p)
+    if os.path.exists(ck_path):
+        blob, m = hlb.read_checkpoint(ck_path)
+        d.restore(blob)
+        pos, q_half, cov_half = int(m["step"]), float(m["q_half"]), float(m["cov_half"])
+    else:
+        _setup_domain(d, case, p, Tc)
+        pos, q_half, cov_half = 0, 0.0, 0.0
+    dg = d.diag(check_flags=False)
+    while pos < steps:
+        nxt = min((pos // every + 1) * every, steps, half if pos < half else steps)
+        d.step(nxt - pos)
+        pos = nxt
+        dg = d.diag(check_flags=False)
+        if dg.error_flags:
+            _record_failure(results, failed_at, k, case, steps, nxt, n_sub, done_path)
+            d.close()
+            return
+        if nxt == half:
+            q_half = dg.q_bottom_timeavg * half
+            cov_half = dg.vapour_coverage_timeavg * half
+        hlb.write_checkpoint(ck_path, d.checkpoint(), name=case.name, steps=steps, step=nxt, q_half=q_half,
+                             cov_half=cov_half, n_sub=n_sub)
+    results[k] = _point_result(case, d.flux_history(), dg, half, q_half, cov_half, hist_steps, n_sub)
+    _save_done(done_path, results[k], steps, -1)
+    d.close()
 
 
 def _save_done(path, r, steps, failed_at):
     import os
     tmp = path + ".tmp.npz"
     np.savez(tmp, name=r.case.name, steps=steps, history=r.history, q=r.q_qs, coverage=r.coverage,
-             regime=r.regime, failed_at=failed_at)
+             regime=r.regime, failed_at=failed_at, n_sub=r.n_sub)
     os.replace(tmp, path)
 
 
@@ -219,7 +289,8 @@ def _load_done(path, case, steps):
         if str(z["name"]) != case.name or int(z["steps"]) != steps:
             raise ValueError(f"{path} belongs to another sweep")
         return (PointResult(case, case.T_bottom_over_Tc - wl.TS_OVER_TC, len(case.sites), z["history"].copy(),
-                            float(z["q"]), float(z["coverage"]), int(z["regime"])), int(z["failed_at"]))
+                            float(z["q"]), float(z["coverage"]), int(z["regime"]), int(z["n_sub"])),
+                int(z["failed_at"]))
 
 
 def run_plain(cases, steps):

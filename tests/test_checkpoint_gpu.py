@@ -222,3 +222,34 @@ def test_resumable_sweep_after_a_lost_process_matches_uninterrupted(coex, tmp_pa
     for r, p in zip(res, ref):
         np.testing.assert_array_equal(r.history, p.history)
         assert r.q_qs == p.q_qs and r.coverage == p.coverage and r.regime == p.regime
+
+
+def test_sweep_retries_an_unstable_point_with_doubled_n(coex, tmp_path, monkeypatch):
+    """A heater of diffusivity 0.65 is beyond RK4's bound at N = 1 (the error
+    word is set within a dozen steps) and within it at N = 2: the sweep stops
+    both points in the batch, runs each again alone with N = 2 from its
+    initial fields (no good checkpoint exists yet), and ends with the results
+    of a plain N = 2 run."""
+    from paper_1812_10375_gb300 import hlb, sweep
+    pts = sweep.make_points(2, seed=9, sides=(64,), sites_range=(1, 2), heater_rows=10)
+    real = sweep.params_for
+
+    def conductive(c):
+        p, Tc = real(c)
+        p.lambda_w = 0.65 * 3.0 * p.rho_l * p.cv
+        return p, Tc
+
+    monkeypatch.setattr(sweep, "params_for", conductive)
+    steps = 128
+    res, fa = sweep.run_resumable(pts, steps, 100, str(tmp_path / "s"), every=64)
+    assert fa == [-1, -1] and [r.n_sub for r in res] == [2, 2]
+    for r, c in zip(res, pts):
+        p, Tc = conductive(c)
+        p.n_sub = 2
+        d = hlb.Domain(p)
+        sweep._setup_domain(d, c, p, Tc)
+        d.step(steps)
+        h = d.flux_history()
+        assert len(h) == steps and d.diag().error_flags == 0
+        np.testing.assert_array_equal(r.history, h[:100])
+        assert r.q_qs == float(h[steps // 2:].mean())

@@ -1,9 +1,11 @@
 """Host logic of the resumable sweep: a process lost mid-sweep resumes each
 point from its own checkpoint and ends with the results of an uninterrupted
-sweep; an unstable point is stopped, recorded and not run again.  The batch is
-a host-side fake with deterministic per-point dynamics, and the faults are
-injected on the host (an exception in place of a lost process, a set error
-word in place of a non-finite step); no GPU is used."""
+sweep; an unstable point runs once more alone from its last good checkpoint
+with N of Eq. (27) doubled, and is recorded as failed if that fails too.  The
+batch and the single domain are host-side fakes with deterministic per-point
+dynamics, and the faults are injected on the host (an exception in place of a
+lost process, a set error word in place of a non-finite step); no GPU is
+used."""
 import pickle
 from types import SimpleNamespace
 
@@ -21,11 +23,13 @@ class FakeBatch:
     """Stands in for hlb.Batch: per slot a step counter, running sums and a
     flux history of q(step) = 1 + 0.01 * seed + 0.1 sin(0.37 step + seed)."""
     crash_after = None  # total steps (over all instances) before a Lost is raised
-    fail = {}           # seed -> step at which the error word becomes set
+    fail = {}           # seed -> step at which the error word becomes set at N = 1
+    fail_always = set()  # seeds whose failure N = 2 does not cure
     steps_run = 0
 
     def __init__(self, plist, stream=None):
         self.seeds = [p.seed for p in plist]
+        self.nsub = [p.n_sub for p in plist]
         self.slot = [None] * len(plist)
         self.active = [True] * len(plist)
 
@@ -45,7 +49,8 @@ class FakeBatch:
                 s["qsum"] += q
                 s["csum"] += 0.5 + 0.5 * np.cos(0.11 * s["step"] * (1 + s["seed"]))
                 s["hist"].append(q)
-                if FakeBatch.fail.get(s["seed"]) == s["step"]:
+                if FakeBatch.fail.get(s["seed"]) == s["step"] and (
+                        self.nsub[j] == 1 or s["seed"] in FakeBatch.fail_always):
                     s["err"] = 1
 
     def diag(self, j, check_flags=True):
@@ -72,12 +77,42 @@ class FakeBatch:
         pass
 
 
+class FakeDomain:
+    """Stands in for hlb.Domain: one FakeBatch slot."""
+    made = []  # N of every domain created
+
+    def __init__(self, p, stream=None):
+        self.b = FakeBatch([p])
+        FakeDomain.made.append(p.n_sub)
+
+    def step(self, n=1):
+        self.b.step(n)
+
+    def diag(self, check_flags=True):
+        return self.b.diag(0)
+
+    def checkpoint(self):
+        return self.b.checkpoint(0)
+
+    def restore(self, blob):
+        self.b.restore(0, blob)
+
+    def flux_history(self):
+        return self.b.flux_history(0)
+
+    def close(self):
+        pass
+
+
 @pytest.fixture
 def fake(monkeypatch):
-    FakeBatch.crash_after, FakeBatch.fail, FakeBatch.steps_run = None, {}, 0
+    FakeBatch.crash_after, FakeBatch.fail, FakeBatch.fail_always, FakeBatch.steps_run = None, {}, set(), 0
+    FakeDomain.made = []
     monkeypatch.setattr(hlb, "Batch", FakeBatch)
-    monkeypatch.setattr(sweep, "params_for", lambda c: (SimpleNamespace(seed=int(c.name[2:5])), 1.0))
+    monkeypatch.setattr(hlb, "Domain", FakeDomain)
+    monkeypatch.setattr(sweep, "params_for", lambda c: (SimpleNamespace(seed=int(c.name[2:5]), n_sub=1), 1.0))
     monkeypatch.setattr(sweep, "_setup", lambda b, j, c, p, Tc: b.slot.__setitem__(j, b._fresh(j)))
+    monkeypatch.setattr(sweep, "_setup_domain", lambda d, c, p, Tc: d.b.slot.__setitem__(0, d.b._fresh(0)))
     return FakeBatch
 
 
@@ -147,26 +182,73 @@ def test_points_at_different_steps_realign(fake, tmp_path):
     assert fake.steps_run == steps
 
 
-def test_unstable_point_is_recorded_and_not_rerun(fake, tmp_path):
+def test_unstable_point_is_retried_alone_with_doubled_n(fake, tmp_path):
     cases, steps = _cases(), 200
     bad = int(cases[3].name[2:5])
-    fake.fail = {bad: 77}
+    fake.fail = {bad: 77}  # unstable at N = 1 only
     d = str(tmp_path / "f")
     res, fa = sweep.run_resumable(cases, steps, 50, d, every=32)
-    assert fa[3] == 96  # detected at the first boundary after step 77
-    assert res[3].regime == -1 and np.isnan(res[3].q_qs) and np.isnan(res[3].coverage)
+    assert fa == [-1] * len(cases)
+    assert res[3].n_sub == 2 and all(res[k].n_sub == 1 for k in range(len(cases)) if k != 3)
+    assert FakeDomain.made == [2]
+    # the batch ran 96 steps with the point (detection at the boundary after 77),
+    # then 200 - 96 without it; the retry restarted from the checkpoint at 64
+    assert fake.steps_run == steps + (steps - 64)
+    # the fake's dynamics do not depend on N: every result equals a sweep
+    # without the instability
+    fake.fail, fake.steps_run = {}, 0
+    ref, _ = sweep.run_resumable(cases, steps, 50, str(tmp_path / "r"), every=32)
+    _same(res, ref)
+    _, meta = hlb.read_checkpoint(str(tmp_path / "f" / "pt00003.ckpt.npz"))
+    assert int(meta["step"]) == steps and int(meta["n_sub"]) == 2
+
+
+def test_point_failing_at_doubled_n_is_recorded_and_not_rerun(fake, tmp_path):
+    cases, steps = _cases(), 200
+    bad = int(cases[3].name[2:5])
+    fake.fail, fake.fail_always = {bad: 77}, {bad}
+    d = str(tmp_path / "f")
+    res, fa = sweep.run_resumable(cases, steps, 50, d, every=32)
+    assert fa[3] == 96  # the retry from 64 fails again at its first boundary
+    assert res[3].regime == -1 and res[3].n_sub == 2 and np.isnan(res[3].q_qs) and np.isnan(res[3].coverage)
     assert all(fa[k] == -1 and res[k].regime >= 0 for k in range(len(cases)) if k != 3)
     # its last good checkpoint stays
     _, meta = hlb.read_checkpoint(str(tmp_path / "f" / "pt00003.ckpt.npz"))
-    assert int(meta["step"]) == 64
+    assert int(meta["step"]) == 64 and int(meta["n_sub"]) == 1
+    fake.steps_run = 0
+    res2, fa2 = sweep.run_resumable(cases, steps, 50, d, every=32)
+    assert fake.steps_run == 0 and fa2 == fa
+    # without retries the failure is recorded at N = 1
+    fake.steps_run = 0
+    res3, fa3 = sweep.run_resumable(cases, steps, 50, str(tmp_path / "nr"), every=32, retry=False)
+    assert fa3[3] == 96 and res3[3].n_sub == 1 and FakeDomain.made == [2]
     # the other points match a sweep without the unstable point
     fake.fail = {}
     ref, _ = sweep.run_resumable([c for k, c in enumerate(cases) if k != 3], steps, 50, str(tmp_path / "r"),
                                  every=32)
     _same([r for k, r in enumerate(res) if k != 3], ref)
-    fake.steps_run = 0
-    res2, fa2 = sweep.run_resumable(cases, steps, 50, d, every=32)
-    assert fake.steps_run == 0 and fa2 == fa
+
+
+def test_process_lost_during_a_retry_resumes_the_retry(fake, tmp_path):
+    cases, steps = _cases(3), 192
+    bad = int(cases[1].name[2:5])
+    fake.fail = {bad: 40}
+    d = str(tmp_path / "f")
+    # the batch finishes (192 steps, detection at 64), then the retry from 32
+    # is lost after 100 more steps (its checkpoint at 128 is on disk)
+    fake.crash_after = steps + 100
+    with pytest.raises(Lost):
+        sweep.run_resumable(cases, steps, 40, d, every=32)
+    _, meta = hlb.read_checkpoint(str(tmp_path / "f" / "pt00001.ckpt.npz"))
+    assert int(meta["step"]) == 128 and int(meta["n_sub"]) == 2
+    fake.crash_after, fake.steps_run = None, 0
+    res, fa = sweep.run_resumable(cases, steps, 40, d, every=32)
+    assert fa == [-1, -1, -1] and res[1].n_sub == 2
+    assert fake.steps_run == steps - 128  # only the retry's remainder, alone
+    assert FakeDomain.made == [2, 2]
+    fake.fail, fake.steps_run = {}, 0
+    ref, _ = sweep.run_resumable(cases, steps, 40, str(tmp_path / "r"), every=32)
+    _same(res, ref)
 
 
 def test_checkpoints_of_another_sweep_are_refused(fake, tmp_path):
