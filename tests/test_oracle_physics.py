@@ -56,11 +56,15 @@ def _conduction_case(coex, two_d: bool):
     return p, rho0, T0
 
 
+@pytest.mark.parametrize("N", [1, 3])
 @pytest.mark.parametrize("two_d", [False, True])
-def test_energy_balance_conduction_only(coex, two_d):
+def test_energy_balance_conduction_only(coex, two_d, N):
     """With u = 0 and frozen rho the FV face fluxes telescope: the change of
-    sum(rho cv T) equals the heat in through the bottom minus the heat out at the top."""
+    sum(rho cv T) equals the heat in through the bottom minus the heat out at
+    the top, also when a step is N sub-steps (Eq. 27) whose RK-weighted face
+    fluxes add up to the step's."""
     p, rho0, T0 = _conduction_case(coex, two_d)
+    p.n_sub = N
     d = Domain(p, rho0, T0, conduction_only=True).step(1)
     E1 = d.diag()["energy"]
     net = 0.0
@@ -319,22 +323,25 @@ def test_paper_contrast_fv_conserves_iso_does_not(coex, paper):
     assert 0.02 < iso < 0.6
 
 
-def test_rk4_step_is_the_fourth_order_taylor_polynomial(coex):
+@pytest.mark.parametrize("N", [1, 2, 3])
+def test_rk4_step_is_the_fourth_order_taylor_polynomial(coex, N):
     """Eq. (18) on a linear problem: with u = 0 and rho frozen, Eq. (17) is the
     affine system dT/dt = A T + b of the finite-volume faces (Eqs. 22-26), and
     one classical RK4 step of length h maps T0 to
     T* + P4(hA)(T0 - T*), P4(z) = 1 + z + z^2/2 + z^3/6 + z^4/24, with T* the
-    steady state.  A and b are assembled here from the harmonic face
-    conductivities on a 3 x 9 lattice (two heater rows, liquid and vapour,
-    Dirichlet bottom and top rows); a wrong stage coefficient or weight in the
-    oracle's RK4 changes P4 and fails the comparison."""
+    steady state; N sub-steps of h = 1/N (Eq. 27) apply P4(A/N) N times.  A and
+    b are assembled here from the harmonic face conductivities on a 3 x 9
+    lattice (two heater rows, liquid and vapour, Dirichlet bottom and top rows);
+    a wrong stage coefficient or weight in the oracle's RK4, or a wrong
+    sub-step length or count, changes the polynomial and fails the
+    comparison."""
     nx, ny, W_ = 3, 9, 2
     rho0 = wl.tanh_slab(ny, nx, coex["rho_l"], coex["rho_v"], 3.0, 6.5)
     rho0 = rho0 * (1.0 + 0.2 * np.sin(2 * np.pi * np.arange(nx) / nx))[None, :]
     rng = np.random.default_rng(4)
     T0 = 0.3 + 0.4 * rng.random((ny, nx))
     p = Params(nx=nx, ny=ny, wall_rows=W_, top_bc="wall", T_bottom=1.0, T_top=0.1,
-               rho_l=coex["rho_l"], rho_v=coex["rho_v"], lambda_top=0.37)
+               rho_l=coex["rho_l"], rho_v=coex["rho_v"], lambda_top=0.37, n_sub=N)
     d = Domain(p, rho0, T0, conduction_only=True)
     pr = p.resolved()
     solid = np.zeros((ny, nx), bool)
@@ -358,11 +365,11 @@ def test_rk4_step_is_the_fourth_order_taylor_polynomial(coex):
             else:
                 b[k] += lf * Tfix[yy, xx] / rcv[y, x]
     Ts = np.linalg.solve(A, -b)
-    z = A  # h = 1 (N = 1)
+    z = A / N  # h = 1/N
     I = np.eye(len(free))
     P4 = I + z + z @ z / 2 + z @ z @ z / 6 + z @ z @ z @ z / 24
     t0 = np.array([d.T[y, x] for y, x in free])
-    expect = Ts + P4 @ (t0 - Ts)
+    expect = Ts + np.linalg.matrix_power(P4, N) @ (t0 - Ts)
     d.step(1)
     got = np.array([d.T[y, x] for y, x in free])
     np.testing.assert_allclose(got, expect, rtol=0, atol=1e-12)
