@@ -81,10 +81,11 @@ typedef struct {
   int wall_rows;       /* rows y < wall_rows are solid (>= 1); row 0 has Dirichlet T */
   int top_bc;          /* HLB_TOP_*; HLB_TOP_WALL makes row ny-1 a solid Dirichlet row */
   int eos_T_fixed;     /* 1: the EOS uses Ts everywhere (Section 3.2)               */
-  int n_sub;           /* N of Eq. (27), 1..64 (1: the paper's parameters are stable).
-                          N > 1 holds rho^n and u^n over the sub-steps and runs for
-                          single domains with HLB_DIFF_FV; batches, the isotropic
-                          scheme and hlb_step_static take N = 1 only              */
+  int n_sub;           /* N of Eq. (27), 1..64, or 0: hlb_stable_substeps (1 for the
+                          paper's parameters).  N > 1 holds rho^n and u^n over the
+                          sub-steps and runs for single domains with HLB_DIFF_FV;
+                          batches, the isotropic scheme and hlb_step_static take
+                          N = 1 only                                              */
   int storage;         /* HLB_STORE_DEVIATION | HLB_STORE_PLAIN                      */
   double a, b, R, omega, Ts_over_Tc;   /* Eq. (28): 3/49, 2/21, 1, 0.344, 0.86        */
   double G, sigma, sigma_coef;         /* Eqs. (6)-(8): -1, 0.107, 12                 */
@@ -132,6 +133,17 @@ typedef struct hlb_batch hlb_batch;
 
 /* Fill the paper's parameter values (Section 3.1) for an nx x ny lattice. */
 void hlb_params_default(hlb_params* p, int nx, int ny);
+
+/* Host-only: the N of Eq. (27) that n_sub = 0 selects, the smallest N for which
+ * one RK4 sub-step of dt/N is stable for the finite-volume conduction operator
+ * (Section 2.2 leaves N to stability).  The operator's eigenvalues are real
+ * and within [-16 D, 0], D the largest of k (the fluid) and
+ * lambda_w / (rho_w cv_w) (the heater), by Gershgorin's theorem with harmonic
+ * face conductivities at most twice a cell's own.  RK4 is stable on the
+ * negative real axis down to -2.785, so N = ceil(16 D / 2.785).  Advection and
+ * the latent-heat term are not part of the bound.  Returns 0 on invalid
+ * parameters. */
+int hlb_stable_substeps(const hlb_params* p);
 
 /* Host-only: Tc (from a, b, R), and the Maxwell equal-area coexistence
  * densities at T = Ts_over_Tc * Tc (Section 3.1), plus the latent heat of

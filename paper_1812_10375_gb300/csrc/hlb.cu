@@ -172,6 +172,37 @@ PRHost pr_of(const hlb_params* p) {
   return e;
 }
 
+// Smallest N of Eq. (27) for which one RK4 sub-step of dt/N is stable for the
+// finite-volume conduction operator.  The operator is C^-1 K (C the diagonal
+// heat capacities, K symmetric), so its eigenvalues are real and <= 0; by
+// Gershgorin they lie in [-2 S, 0] with S the largest sum over a cell's four
+// faces of lambda_f / (rho c)_P, and a harmonic face conductivity is at most
+// twice the cell's own, so |eigenvalue| <= 16 D_max with D = lambda / (rho c)
+// of a material (k in the fluid, lambda_w / (rho_w c_w) in the heater).  RK4's
+// stability interval on the negative real axis reaches 2.785.  The advection
+// and latent-heat terms are not in the bound: at the method's velocities they
+// are small beside it.  0 when the coexistence densities needed for the
+// heater's defaults do not exist.
+int stable_substeps(const hlb_params* p) {
+  double rho_l = p->rho_l;
+  if (!(rho_l > 0)) {
+    const PRHost e = pr_of(p);
+    double rv;
+    if (!coexistence(e, p->Ts_over_Tc * e.Tc, &rho_l, &rv, nullptr)) return 0;
+  }
+  const double rho_w = p->rho_w > 0 ? p->rho_w : 3.0 * rho_l;
+  const double cv_w = p->cv_w > 0 ? p->cv_w : p->cv;
+  const double lam_w = p->lambda_w > 0 ? p->lambda_w : 3.0 * rho_l * p->cv * p->k;
+  const double D = fmax(p->k, lam_w / (rho_w * cv_w));
+  const double RK4_REAL_AXIS = 2.785;
+  const double n = ceil(16.0 * D / RK4_REAL_AXIS);
+  if (!(n < 1e6)) return 0;
+  return n < 1.0 ? 1 : (int)n;
+}
+
+// N of Eq. (27) a parameter set runs with: n_sub, or the bound above when it is 0.
+int resolved_nsub(const hlb_params* p) { return p->n_sub != 0 ? p->n_sub : stable_substeps(p); }
+
 // Stride of the population planes in floats: nx ny rounded up to whole
 // 128-byte lines, so that every plane starts on a line.
 size_t plane_stride(size_t N) { return (N + 31) / 32 * 32; }
@@ -182,10 +213,7 @@ bool params_valid(const hlb_params* p) {
   if (p->top_bc < HLB_TOP_WALL || p->top_bc > HLB_TOP_CONVECTIVE) return false;
   const int fluid_rows = p->ny - p->wall_rows - (p->top_bc == HLB_TOP_WALL ? 1 : 0);
   if (fluid_rows < 3) return false;
-  // N of Eq. (27): the fused kernel takes the first sub-step, k_energy_substep
-  // the others (finite-volume scheme only)
-  if (p->n_sub < 1 || p->n_sub > MAX_SUB) return false;
-  if (p->n_sub > 1 && p->diffusion != HLB_DIFF_FV) return false;
+  if (p->n_sub < 0 || p->n_sub > MAX_SUB) return false;
   if (p->storage != HLB_STORE_DEVIATION && p->storage != HLB_STORE_PLAIN) return false;
   if (p->diffusion != HLB_DIFF_FV && p->diffusion != HLB_DIFF_ISO) return false;
   if (p->bottom_bc != HLB_BOTTOM_DIRICHLET && p->bottom_bc != HLB_BOTTOM_FLUX) return false;
@@ -198,6 +226,11 @@ bool params_valid(const hlb_params* p) {
   // the kernels address a cell's nine populations with 32-bit offsets (q plane + cell)
   if (p->nx > (1 << 20) || p->ny > (1 << 20)) return false;
   if (9 * (long long)plane_stride((size_t)p->nx * p->ny) >= (1LL << 31)) return false;
+  // N of Eq. (27): the fused kernel takes the first sub-step, k_energy_substep
+  // the others (finite-volume scheme only)
+  const int nsub = resolved_nsub(p);
+  if (nsub < 1 || nsub > MAX_SUB) return false;
+  if (nsub > 1 && p->diffusion != HLB_DIFF_FV) return false;
   return true;
 }
 
@@ -255,7 +288,7 @@ Layout layout_of(const hlb_params* p) {
   L.state = o;    o += align_up(sizeof(DevState));
   L.hist = o;     o += align_up(HIST_CAP * sizeof(double));
   L.sub = o;
-  if (p->n_sub > 1) {
+  if (resolved_nsub(p) > 1) {
     const dim3 sg = sub_grid_of(p->nx, p->ny);
     o += align_up(4 * N * sizeof(float));  // rho, u_x, u_y, T
     o += align_up((size_t)sg.x * sg.y * NSUBPART * sizeof(double));
@@ -376,6 +409,7 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
     d->p.rho_v = rv;
   }
   hlb_params& q = d->p;
+  q.n_sub = resolved_nsub(p);
   if (!(q.rho_w > 0)) q.rho_w = 3.0 * q.rho_l;
   if (!(q.cv_w > 0)) q.cv_w = q.cv;
   if (!(q.lambda_w > 0)) q.lambda_w = 3.0 * q.rho_l * q.cv * q.k;
@@ -1050,6 +1084,11 @@ hlb_status hlb_destroy(hlb_domain* d) {
   return HLB_OK;
 }
 
+int hlb_stable_substeps(const hlb_params* p) {
+  if (!p || !(p->k > 0 && p->cv > 0 && p->a > 0 && p->b > 0 && p->R > 0 && p->Ts_over_Tc > 0)) return 0;
+  return stable_substeps(p);
+}
+
 size_t hlb_checkpoint_bytes(const hlb_params* p) {
   if (!params_valid(p)) return 0;
   return ckpt_layout(p->nx, p->ny).hist + (size_t)HIST_CAP * sizeof(double);
@@ -1068,7 +1107,7 @@ hlb_status hlb_checkpoint_load(hlb_domain* d, const void* h_buf, size_t len) {
 size_t hlb_batch_workspace_bytes(int n, const hlb_params* p) {
   if (n < 1 || !p) return 0;
   for (int i = 0; i < n; ++i)
-    if (!params_valid(p + i) || p[i].diffusion != HLB_DIFF_FV || p[i].n_sub != 1) return 0;
+    if (!params_valid(p + i) || p[i].diffusion != HLB_DIFF_FV || resolved_nsub(p + i) != 1) return 0;
   return batch_layout(n, p).total;
 }
 
@@ -1077,7 +1116,7 @@ hlb_status hlb_batch_init(hlb_batch** out, int n, const hlb_params* p, void* d_w
   if (!out || n < 1 || !p || !d_workspace) return HLB_EINVAL;
   *out = nullptr;
   for (int i = 0; i < n; ++i)
-    if (!params_valid(p + i) || p[i].diffusion != HLB_DIFF_FV || p[i].n_sub != 1) return HLB_EINVAL;
+    if (!params_valid(p + i) || p[i].diffusion != HLB_DIFF_FV || resolved_nsub(p + i) != 1) return HLB_EINVAL;
   if (((uintptr_t)d_workspace & 255) != 0) return HLB_EINVAL;
   const BatchLayout L = batch_layout(n, p);
   if (workspace_bytes < L.total) return HLB_EINVAL;
@@ -1470,7 +1509,7 @@ extern "C" hlb_status hlb_step_static(const hlb_params* p, int n_sites, const hl
   if (!p || !d_f_in || !d_f_out || !d_T_in || !d_T_out || !h_out) return HLB_EINVAL;
   if (n_sites < 0 || n_sites > HLB_STATIC_MAX_SITES || (n_sites > 0 && !h_sites)) return HLB_EINVAL;
   if (hlb_workspace_bytes(p) == 0) return HLB_EINVAL;  // the same parameter checks as hlb_init
-  if (p->n_sub != 1) return HLB_EINVAL;                 // sub-steps need workspace scratch
+  if (resolved_nsub(p) != 1) return HLB_EINVAL;         // sub-steps need workspace scratch
   if (p->top_bc == HLB_TOP_CONVECTIVE && (!d_ftop_in || !d_ftop_out)) return HLB_EINVAL;
   if (p->nx > HLB_STATIC_MAX_NX) return HLB_EINVAL;
   const long long nblk = (long long)((p->nx + TILE_X - 1) / TILE_X) * ((p->ny + TILE_Y - 1) / TILE_Y);

@@ -92,6 +92,7 @@ def lib() -> C.CDLL:
             "hlb_set_tile_variant": (st, [vp, C.c_int]),
             "hlb_batch_set_tile_variant": (st, [vp, C.c_int]),
             "hlb_checkpoint_bytes": (sz, [P(hlb_params)]),
+            "hlb_stable_substeps": (C.c_int, [P(hlb_params)]),
             "hlb_checkpoint_save": (st, [vp, vp, sz, P(sz)]),
             "hlb_checkpoint_load": (st, [vp, vp, sz]),
             "hlb_batch_checkpoint_save": (st, [vp, C.c_int, vp, sz, P(sz)]),
@@ -128,6 +129,11 @@ def eos_coexistence(p: hlb_params):
 
 def workspace_bytes(p: hlb_params) -> int:
     return int(lib().hlb_workspace_bytes(C.byref(p)))
+
+
+def stable_substeps(p: hlb_params) -> int:
+    """N of Eq. (27) that n_sub = 0 selects (RK4 stability of the conduction operator)."""
+    return int(lib().hlb_stable_substeps(C.byref(p)))
 
 
 def checkpoint_bytes(p: hlb_params) -> int:

@@ -129,3 +129,54 @@ def test_scheme_and_heater_parameters_are_validated(lib):
     p.q_in = 2e-4
     assert lib.workspace_bytes(p) > 0
     assert lib.lib().hlb_batch_workspace_bytes(1, ctypes.byref(p)) > 0
+
+
+def test_stable_substeps_bound(lib):
+    """n_sub = 0 picks N of Eq. (27) from the RK4 stability of the conduction
+    operator: N = ceil(16 D_max / 2.785).  The bound is checked here on the
+    finite-volume operator assembled from harmonic face conductivities (a
+    heater under a liquid-vapour column, periodic x, Dirichlet bottom and top
+    rows): its eigenvalues are real, within [-16 D_max, 0], and every RK4
+    sub-step amplification |P4(h z)|, h = 1/N, is at most 1 at the chosen N,
+    while N = 1 is unstable for the conductive heater."""
+    import numpy as np
+    p = lib.default_params(64, 48)
+    assert lib.stable_substeps(p) == 1
+    Tc, rl, rv, _ = lib.eos_coexistence(p)
+    q = lib.default_params(64, 48)
+    q.n_sub = 0
+    assert lib.workspace_bytes(q) == lib.workspace_bytes(p)  # resolves to N = 1
+    nx, ny, W = 4, 12, 3
+    rho = np.where(np.arange(ny)[:, None] < 7, rl, rv) * np.ones((ny, nx))
+    for D_w in (0.1, 0.3, 0.65, 1.3):
+        q = lib.default_params(64, 48)
+        q.lambda_w = D_w * 3.0 * rl * q.cv
+        N = lib.stable_substeps(q)
+        assert N == int(np.ceil(16.0 * max(q.k, D_w) / 2.785))
+        q.n_sub = 0
+        assert lib.workspace_bytes(q) > 0
+        q.n_sub = N
+        w_n = lib.workspace_bytes(q)
+        q.n_sub = 0
+        assert lib.workspace_bytes(q) == w_n
+        assert lib.lib().hlb_batch_workspace_bytes(1, ctypes.byref(q)) == (0 if N > 1 else
+                                                                          lib.lib().hlb_batch_workspace_bytes(1, ctypes.byref(p)))
+        solid = np.arange(ny)[:, None] < W
+        lam = np.where(solid, q.lambda_w, rho * q.cv * q.k)
+        rcv = np.where(solid, 3.0 * rl * q.cv, rho * q.cv)
+        free = [(y, x) for y in range(1, ny - 1) for x in range(nx)]
+        index = {c: k for k, c in enumerate(free)}
+        A = np.zeros((len(free), len(free)))
+        for (y, x), k in index.items():
+            for yy, xx in ((y, (x + 1) % nx), (y, (x - 1) % nx), (y + 1, x), (y - 1, x)):
+                lf = 2.0 * lam[y, x] * lam[yy, xx] / (lam[y, x] + lam[yy, xx])
+                A[k, k] -= lf / rcv[y, x]
+                if (yy, xx) in index:
+                    A[k, index[(yy, xx)]] += lf / rcv[y, x]
+        z = np.linalg.eigvals(A)
+        assert np.abs(z.imag).max() < 1e-9 and z.real.max() < 1e-12
+        assert -z.real.min() <= 16.0 * max(q.k, D_w) + 1e-12
+        P4 = lambda w: 1 + w + w ** 2 / 2 + w ** 3 / 6 + w ** 4 / 24
+        assert np.abs(P4(z.real / N)).max() <= 1.0 + 1e-12
+        if D_w >= 0.65:
+            assert np.abs(P4(z.real)).max() > 1.0  # N = 1 would diverge

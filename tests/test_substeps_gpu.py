@@ -112,3 +112,20 @@ def test_graph_replay_matches_single_launches_with_substeps(coex):
     for x, y in zip(a.read(), b.read()):
         assert (x == y).all()
     assert a.diag().energy == b.diag().energy
+
+
+def test_n_sub_zero_picks_a_stable_n(coex):
+    """n_sub = 0 takes N from the stability bound: 4 for a heater of
+    diffusivity 0.65, and the run matches the oracle at that N."""
+    from paper_1812_10375_gb300 import hlb
+    from paper_1812_10375_gb300.config import params_for
+    case = ragged_case(3)
+    lam_w = 0.65 * 3.0 * coex["rho_l"] * 6.0
+    p, _ = params_for(case, rho_l=coex["rho_l"], rho_v=coex["rho_v"])
+    p.lambda_w = lam_w
+    assert hlb.stable_substeps(p) == 4
+    err, gd, od = _run(case, coex, 300, oracle_kw=dict(lambda_w=lam_w, n_sub=4),
+                       gpu_kw=dict(lambda_w=lam_w, n_sub=0))
+    print("n_sub=0 -> 4", err)
+    assert max(err.values()) < TOL, err
+    assert gd.diag().error_flags == 0
