@@ -68,7 +68,7 @@ def test_workspace_size_and_rejections(lib):
     # N of Eq. (27): 1..64; N > 1 adds the sub-steps' scratch (rho, u, T and
     # the per-block partials), is a single-domain, finite-volume option, and
     # is refused by batches
-    for bad_n in (0, -1, 65):
+    for bad_n in (-1, 65):  # 0 selects N from the stability bound
         p.n_sub = bad_n
         assert lib.workspace_bytes(p) == 0
     p.n_sub = 2
