@@ -1527,6 +1527,7 @@ extern "C" hlb_status hlb_step_static(const hlb_params* p, int n_sites, const hl
 
   // parameters, resolved as hlb_init resolves them (no allocation: host stack only)
   hlb_params q = *p;
+  q.n_sub = 1;  // checked above: n_sub is 1, or 0 resolving to 1
   double Tc = 0.0;
   if (!(q.rho_l > 0 && q.rho_v > 0)) {
     if (hlb_eos_coexistence(p, &Tc, &q.rho_l, &q.rho_v, nullptr) != HLB_OK) return HLB_EINVAL;
