@@ -439,18 +439,26 @@ def paper_cases(ja_values, nx=400, ny=600, heater_rows=25, seed=wl.BASE_SEED, cp
     return out, h_fg, Tc
 
 
-def paper_curve(ja_values, steps, cp=None):
+def paper_curve(ja_values, steps, cp=None, ckpt_dir=None, every=4096):
     """Run the Fig. 11 cases together (one batched launch per step) and return,
     per Jakob number, the quasi-steady wall heat flux (mean over the second
     half of the run), the heat transfer coefficient q / (T_w - Ts), the wall
-    vapour coverage and its regime label."""
+    vapour coverage and its regime label.  With `ckpt_dir` the run goes
+    through run_resumable: checkpoints every `every` steps, resumable per
+    point, an unstable point retried once with N of Eq. (27) doubled."""
     cases, h_fg, Tc = paper_cases(ja_values, cp=cp)
-    res, seconds = run_batched(cases, steps, hist_steps=0)
+    failed = [-1] * len(cases)
+    if ckpt_dir is None:
+        res, seconds = run_batched(cases, steps, hist_steps=0)
+    else:
+        t0 = time.perf_counter()
+        res, failed = run_resumable(cases, steps, 0, ckpt_dir, every=every)
+        seconds = time.perf_counter() - t0
     rows = []
-    for ja, r in zip(ja_values, res):
+    for ja, r, fa in zip(ja_values, res, failed):
         dT = r.superheat * Tc
         rows.append(dict(Ja=float(ja), superheat_over_Tc=r.superheat, q=r.q_qs, h=r.q_qs / dT,
-                         coverage=r.coverage, regime=r.regime))
+                         coverage=r.coverage, regime=r.regime, n_sub=r.n_sub, failed_at=fa))
     return rows, seconds
 
 
@@ -526,12 +534,16 @@ if __name__ == "__main__":
     ap.add_argument("--surrogate-study", action="store_true",
                     help="instead: the early-stop policy on 256 sweep points of sides 256-512 (40,000 steps)")
     ap.add_argument("--cache", type=str, default=None, help="npz of the study's runs (written once, then reused)")
+    ap.add_argument("--checkpoint-dir", type=str, default=None,
+                    help="checkpoint every point there and resume from it (per point) when run again")
+    ap.add_argument("--checkpoint-every", type=int, default=4096)
     a = ap.parse_args()
     if a.surrogate_study:
         print(json.dumps(surrogate_study(cache=a.cache)))
         raise SystemExit(0)
     cp = liquid_cp(hlb.default_params(8, 8)) if a.cp_eos else None
-    rows, sec = paper_curve([float(x) for x in a.ja.split(",")], a.steps, cp=cp)
+    rows, sec = paper_curve([float(x) for x in a.ja.split(",")], a.steps, cp=cp, ckpt_dir=a.checkpoint_dir,
+                            every=a.checkpoint_every)
     for r in rows:
         print(json.dumps(r))
     print(json.dumps({"points": len(rows), "steps": a.steps, "seconds": sec}))

@@ -281,3 +281,23 @@ def test_checkpoint_bytes_covers_header_fields_and_history():
     assert hlb.checkpoint_bytes(p) == 512 + (fields + 7) // 8 * 8 + 8 * 65536
     p.ny = 3
     assert hlb.checkpoint_bytes(p) == 0
+
+
+def test_paper_curve_goes_through_the_resumable_driver(monkeypatch, tmp_path):
+    """paper_curve with a checkpoint directory hands the Fig. 11 cases to
+    run_resumable and reports each point's N and failure step."""
+    from paper_1812_10375_gb300 import build
+    build.build()
+    seen = {}
+
+    def fake_run(cases, steps, hist_steps, ckpt_dir, every=2048, retry=True):
+        seen.update(n=len(cases), steps=steps, dir=ckpt_dir, every=every)
+        res = [sweep.PointResult(c, c.T_bottom_over_Tc - 0.86, len(c.sites), np.zeros(0), 1e-3 * (k + 1), 0.1, 1,
+                                 1 + k) for k, c in enumerate(cases)]
+        return res, [-1, 77][:len(cases)]
+
+    monkeypatch.setattr(sweep, "run_resumable", fake_run)
+    rows, secs = sweep.paper_curve([0.1, 0.2], 1000, ckpt_dir=str(tmp_path), every=128)
+    assert seen == dict(n=2, steps=1000, dir=str(tmp_path), every=128)
+    assert [r["n_sub"] for r in rows] == [1, 2] and [r["failed_at"] for r in rows] == [-1, 77]
+    assert rows[1]["h"] == pytest.approx(rows[1]["q"] / (rows[1]["superheat_over_Tc"] * sweep.paper_cases([0.2])[2]))
