@@ -151,7 +151,8 @@ def run_resumable(cases, steps, hist_steps, ckpt_dir, every=2048, retry=True):
             meta[k] = (blob, m)
     base_n = {k: params_for(cases[k])[0].n_sub for k in range(len(cases)) if results[k] is None}
     # points resumed inside their retry continue alone at their checkpoint's N
-    single = {k: int(meta[k][1].get("n_sub", base_n[k])) for k in meta if int(meta[k][1].get("n_sub", 1)) > base_n[k]}
+    ck_n = {k: int(meta[k][1].get("n_sub", base_n[k])) for k in meta}
+    single = {k: n for k, n in ck_n.items() if n > base_n[k]}
     todo = [k for k in range(len(cases)) if results[k] is None and k not in single]
     if todo:
         plist, tcs = zip(*[params_for(cases[k]) for k in todo])

@@ -159,8 +159,8 @@ def test_stable_substeps_bound(lib):
         w_n = lib.workspace_bytes(q)
         q.n_sub = 0
         assert lib.workspace_bytes(q) == w_n
-        assert lib.lib().hlb_batch_workspace_bytes(1, ctypes.byref(q)) == (0 if N > 1 else
-                                                                          lib.lib().hlb_batch_workspace_bytes(1, ctypes.byref(p)))
+        batch_ws = lib.lib().hlb_batch_workspace_bytes
+        assert batch_ws(1, ctypes.byref(q)) == (0 if N > 1 else batch_ws(1, ctypes.byref(p)))
         solid = np.arange(ny)[:, None] < W
         lam = np.where(solid, q.lambda_w, rho * q.cv * q.k)
         rcv = np.where(solid, 3.0 * rl * q.cv, rho * q.cv)
