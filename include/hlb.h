@@ -142,7 +142,7 @@ void hlb_params_default(hlb_params* p, int nx, int ny);
  * face conductivities at most twice a cell's own.  RK4 is stable on the
  * negative real axis down to -2.785, so N = ceil(16 D / 2.785).  Advection and
  * the latent-heat term are not part of the bound.  Returns 0 on invalid
- * parameters. */
+ * parameters; a parameter set with n_sub = 0 is refused when this N exceeds 64. */
 int hlb_stable_substeps(const hlb_params* p);
 
 /* Host-only: Tc (from a, b, R), and the Maxwell equal-area coexistence
