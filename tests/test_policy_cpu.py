@@ -1,0 +1,107 @@
+"""Host logic of the surrogate's early-stop policy, with a stand-in ensemble
+whose predictions are set by the test: the calibrated threshold and the
+(score, spread) pair are the ones a brute-force search over the same
+candidates picks, the work fraction is the cell-weighted closed form, and the
+features are the block means of the histories.  The regime labels follow the
+coverage edges."""
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+
+from paper_1812_10375_gb300 import sweep
+from paper_1812_10375_gb300 import surrogate as sur
+
+L0 = 8
+
+
+class StandIn:
+    """predict() returns fixed (q_pred, spread, regime probabilities)."""
+
+    def __init__(self, qp, spread, prob):
+        self.out = (np.asarray(qp, float), np.asarray(spread, float), np.asarray(prob, float))
+
+    def predict(self, hist, scal):
+        assert len(hist) == len(self.out[0]) and hist.shape[1] == L0 and scal.shape == (len(hist), 2)
+        return self.out
+
+
+def _results(q, n_hist=40):
+    case = SimpleNamespace(nx=10, ny=10, T_bottom_over_Tc=0.96, sites=[(1.0, 2.0, 0.0)])
+    return [sweep.PointResult(case, 0.1, 1, np.arange(n_hist, dtype=float) + k, float(qk), 0.1, 1)
+            for k, qk in enumerate(q)]
+
+
+def _prob(p_none, p_film):
+    p = np.zeros((len(p_none), 5))
+    p[:, 0] = p_none
+    p[:, -1] = p_film
+    p[:, 1] = 1.0 - p[:, 0] - p[:, -1]
+    return p
+
+
+def test_features_are_block_means():
+    res = _results([1.0, 2.0], n_hist=43)
+    hist, scal, q, lab = sweep.features(res, L0)
+    # 43 // 8 = 5 samples per block, the last 3 dropped
+    np.testing.assert_allclose(hist[1], (np.arange(40, dtype=float) + 1).reshape(8, 5).mean(axis=1))
+    assert scal.tolist() == [[0.1, 0.1], [0.1, 0.1]] and q.tolist() == [1.0, 2.0] and lab.tolist() == [1, 1]
+    with pytest.raises(ValueError):
+        sur.downsample(np.zeros(L0 - 1), L0)
+
+
+def test_threshold_is_the_lowest_safe_score():
+    q = np.ones(5)
+    qp = q * (1 + np.array([0.01, 0.02, 0.05, 0.01, 0.0]))  # relative errors
+    score = np.array([0.9, 0.8, 0.7, 0.6, 0.4])
+    ens = StandIn(qp, np.zeros(5), _prob(np.zeros(5), 1.0 - score))
+    # accepting down to 0.8 keeps every accepted error within 3%; 0.7 adds a 5% one
+    assert sweep.choose_threshold(ens, _results(q), L0, tol=0.03) == pytest.approx(0.8)
+    assert sweep.choose_threshold(ens, _results(q), L0, tol=0.06, floor=0.65) == pytest.approx(0.7)
+    # an unsafe top score accepts nothing
+    ens_bad = StandIn(q * 1.2, np.zeros(5), _prob(np.zeros(5), 1.0 - score))
+    assert sweep.choose_threshold(ens_bad, _results(q), L0, tol=0.03) == 1.01
+
+
+@pytest.mark.parametrize("kind", ["not_film", "no_boiling"])
+def test_policy_pair_matches_brute_force(kind):
+    rng = np.random.default_rng(3)
+    n = 30
+    q = 1.0 + rng.random(n)
+    err = np.abs(rng.normal(0, 0.03, n))
+    qp = q * (1 + err)
+    spread = rng.random(n) * 0.1
+    p_none, p_film = rng.random(n) * 0.5, rng.random(n) * 0.5
+    ens = StandIn(qp, spread, _prob(p_none, p_film))
+    thr, smax = sweep.choose_policy(ens, _results(q), L0, tol=0.03, floor=0.3, kind=kind)
+    score = 1.0 - p_film if kind == "not_film" else p_none
+    best = 0
+    for t in np.unique(score[score >= 0.3]):
+        for s in np.unique(spread):
+            acc = (score >= t) & (spread <= s)
+            if acc.any() and err[acc].max() <= 0.03 + 1e-12:
+                best = max(best, int(acc.sum()))
+    acc = (score >= thr) & (spread <= smax)
+    assert int(acc.sum()) == best and best > 0
+    assert err[acc].max() <= 0.03 + 1e-12
+
+
+def test_work_fraction_is_cell_weighted():
+    q = np.ones(4)
+    score = np.array([0.9, 0.2, 0.95, 0.1])
+    ens = StandIn(q * 1.01, np.array([0.0, 0.0, 0.5, 0.0]), _prob(np.zeros(4), 1.0 - score))
+    cells = [100, 200, 300, 400]
+    acc, err, frac = sweep.evaluate_policy(ens, _results(q), L0, 0.8, hist_steps=10, full_steps=40, cells=cells)
+    assert acc.tolist() == [True, False, True, False]
+    expect = (10 * 100 + 40 * 200 + 10 * 300 + 40 * 400) / (40 * 1000)
+    assert frac == pytest.approx(expect) and np.allclose(err, 0.01)
+    # the spread limit removes the third point
+    acc, _, frac = sweep.evaluate_policy(ens, _results(q), L0, 0.8, 10, 40, cells, spread_max=0.1)
+    assert acc.tolist() == [True, False, False, False]
+    assert frac == pytest.approx((10 * 100 + 40 * 900) / (40 * 1000))
+
+
+def test_regime_labels_follow_the_coverage_edges():
+    edges = list(sur.COVERAGE_EDGES)
+    assert [sur.regime_of(c) for c in [0.0] + edges + [1.0]] == [0] + list(range(1, len(edges) + 1)) + [len(edges)]
+    assert all(sur.regime_of(e - 1e-9) == k for k, e in enumerate(edges))
