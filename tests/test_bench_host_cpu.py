@@ -1,0 +1,42 @@
+"""Host helpers of bench.py: which step kernel a tile variant launches and how
+many launches a step takes, the DRAM bytes read from a profile summary only
+when its kernel-source hash is the current one, and the peak's fallback."""
+import json
+from types import SimpleNamespace
+
+import bench
+
+
+def test_kernel_name_and_launch_count():
+    assert bench.kernel_name((52, 28, 512)) == "k_step_batch"
+    assert bench.kernel_name((0, 48, 0)) == "k_march_batch"
+    cases = [SimpleNamespace(nx=n) for n in (256, 320, 300, 512, 500)]
+    assert bench.step_launches(cases, (52, 20, 512)) == 1
+    # row strides 256, 320 (300 rounds up to 320), 512 (500 too)
+    assert bench.step_launches(cases, (0, 32, 0)) == 3
+
+
+def _profile(root, h, lines):
+    (root / "profiles").mkdir(parents=True, exist_ok=True)
+    body = ["# summary", f"- kernel_source_hash: `{h}`"] + lines
+    (root / "profiles" / "k_step_batch_sweep32.md").write_text("\n".join(body) + "\n")
+
+
+def test_traffic_is_read_only_for_the_current_kernel(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abc123")
+    assert bench.read_traffic((52, 28, 512)) is None  # no summary
+    _profile(tmp_path, "abc123", ["- dram_bytes_per_launch_full_sweep_52x28x512: 351090176",
+                                  "- dram_bytes_per_launch_full_sweep_52x20x512: not-a-number"])
+    assert bench.read_traffic((52, 28, 512)) == 351090176.0
+    assert bench.read_traffic((52, 20, 512)) is None      # unparsable
+    assert bench.read_traffic((52, 16, 256)) is None      # not captured
+    _profile(tmp_path, "stale0", ["- dram_bytes_per_launch_full_sweep_52x28x512: 351090176"])
+    assert bench.read_traffic((52, 28, 512)) is None      # kernel changed since the capture
+
+
+def test_peak_prefers_the_measured_file(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.peak_gbs() == (6800.0, "of fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6789.3}))
+    assert bench.peak_gbs() == (6789.3, "of measured")
