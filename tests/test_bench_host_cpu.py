@@ -40,3 +40,15 @@ def test_peak_prefers_the_measured_file(tmp_path, monkeypatch):
     assert bench.peak_gbs() == (6800.0, "of fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6789.3}))
     assert bench.peak_gbs() == (6789.3, "of measured")
+
+
+def test_clock_samples_are_summarised():
+    lines = ["2070, 2070, 812.5, Not Active, Not Active, Not Active, Not Active",
+             "1995, 2070, 1390.1, Not Active, Not Active, Not Active, Active",
+             "[N/A], 2070, 0, Not Active, Not Active, Not Active, Not Active",
+             "short line",
+             "2040, 2070, 1201.0, Not Active, Active, Not Active, Not Active"]
+    out = bench.parse_clock_lines(lines)
+    assert out == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["hw_thermal_slowdown", "sw_power_cap"],
+                   "samples": 3}
+    assert bench.parse_clock_lines([])["sm_mhz"] is None
