@@ -375,3 +375,36 @@ def test_rk4_step_is_the_fourth_order_taylor_polynomial(coex, N):
     np.testing.assert_allclose(got, expect, rtol=0, atol=1e-12)
     # and the step moved the field (the test is not vacuous)
     assert np.abs(got - t0).max() > 1e-4
+
+
+def test_diagnostics_special_cases(coex):
+    """Closed forms of the step's diagnostics.  A uniform liquid or vapour at
+    rest at Ts in a closed box (no gravity, no wetting force, walls at Ts) is a
+    fixed point of the step: rho_ave is the fill density, the mass its product
+    with the fluid node count, u_top and every wall flux vanish, the energy sum
+    is rho cv Ts over the fluid plus rho_w cv_w Ts over the solid rows, and the
+    vapour coverage of the first fluid row is 0 (liquid) or 1 (vapour), so is
+    its time average.  A first fluid row that is vapour for x < nx / 2 has
+    coverage 1/2 after one step (one streaming of rest equilibria moves no
+    cell across the density threshold)."""
+    Ts, rl, rv = coex["Ts"], coex["rho_l"], coex["rho_v"]
+    nx, ny, W_ = 40, 12, 2
+    n_fluid, n_solid = nx * (ny - W_ - 1), nx * (W_ + 1)
+    for fill, cov in ((rl, 0.0), (rv, 1.0)):
+        p = Params(nx=nx, ny=ny, wall_rows=W_, top_bc="wall", T_bottom=Ts, T_top=Ts, Gw=0.0, g_y=0.0,
+                   rho_l=rl, rho_v=rv)
+        d = Domain(p, np.full((ny, nx), fill), np.full((ny, nx), Ts)).step(5)
+        g = d.diag()
+        pr = p.resolved()
+        assert g["step"] == 5 and g["error_flags"] == 0
+        assert g["rho_ave"] == pytest.approx(fill, rel=1e-13)
+        assert g["mass"] == pytest.approx(fill * n_fluid, rel=1e-13)
+        assert abs(g["u_top"]) < 1e-15
+        assert max(abs(g["q_bottom"]), abs(g["q_top"]), abs(g["q_interface"])) < 1e-13
+        assert g["energy"] == pytest.approx(fill * pr.cv * Ts * n_fluid + pr.rho_w * pr.cv_w * Ts * n_solid,
+                                            rel=1e-13)
+        assert g["vapour_coverage"] == cov and g["vapour_coverage_timeavg"] == cov
+    rho0 = np.full((ny, nx), rl)
+    rho0[W_, : nx // 2] = rv
+    p = Params(nx=nx, ny=ny, wall_rows=W_, top_bc="wall", T_bottom=Ts, T_top=Ts, rho_l=rl, rho_v=rv)
+    assert Domain(p, rho0, np.full((ny, nx), Ts)).step(1).diag()["vapour_coverage"] == 0.5
