@@ -3,7 +3,8 @@
 Workload: the batched boiling-curve sweep of 32 independent square domains
 (sides drawn from {256, 320, 384, 448, 512}, superheats 0.02-0.30 Tc, 3-9
 nucleation sites, 25-row conjugate heater, convective top, gravity 3e-5), all
-advanced by one fused-step launch plus one FP64 reduction launch per step.
+advanced together: per step one flow launch, one energy sub-step launch and one
+FP64 reduction launch (split step), or one fused step launch and the reduction.
 A step is one coupled update of every cell of every domain.  The metric is
 coupled MLUPS over all lattice nodes (fluid and solid).
 
@@ -33,13 +34,18 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled MLUPS (hybrid thermal LB step, batched boiling-curve sweep)"
 UNIT = "MLUPS"
 WORKLOAD = ("boiling-curve sweep: 32 square domains, sides {256..512} seeded, superheat 0.02-0.30 Tc, "
-            "3-9 nucleation sites, 25-row heater, convective top, g = 3e-5; one fused step launch + one "
-            "FP64 reduction launch per step")
+            "3-9 nucleation sites, 25-row heater, convective top, g = 3e-5; all domains advanced together "
+            "by batched launches (step kernels + one FP64 reduction launch per step)")
 BYTES_FLUID = 80  # f read 36 + f write 36 + T read 4 + T write 4
 BYTES_SOLID = 8   # T read + write (no populations in solid rows)
+# the split step's kernels: the flow kernel reads populations and T^n and writes
+# populations, rho^n and u^n; an energy sub-step reads T, rho^n, u^n and writes T
+FLOW_BYTES_FLUID = 36 + 36 + 4 + 12
+ENERGY_BYTES_FLUID = 4 + 12 + 4
+ENERGY_BYTES_SOLID = 8
+KIND_SPLIT, KIND_FUSED, KIND_MARCH = 0, 1, 2
 
-
-KERNEL_SOURCES = ("hlb_internal.cuh", "hlb_kernels.cuh", "hlb_march.cuh")  # the step kernels' device code
+KERNEL_SOURCES = ("hlb_internal.cuh", "hlb_kernels.cuh", "hlb_march.cuh", "hlb_split.cuh")  # step kernels' device code
 
 
 def kernel_source_hash() -> str:
@@ -51,24 +57,34 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def kernel_name(tile):
-    """The step kernel a tile variant launches: row-marching variants report a
-    tile width of 0 (full width)."""
+def kernel_name(tile, kind=KIND_FUSED):
+    """The step kernel(s) a variant launches: the split step's flow and energy
+    kernels, the fused tiled kernel, or the row-marching kernel (tile width 0)."""
+    if kind == KIND_SPLIT:
+        return "k_flow_batch+k_energy_batch"
     return "k_march_batch" if tile[0] == 0 else "k_step_batch"
 
 
-def step_launches(cases, tile):
-    """Step-kernel launches per step: one for a tiled variant, one per distinct
-    row stride (width rounded up to 32) for a row-marching variant."""
+def profile_name(tile, kind=KIND_FUSED):
+    """File stem of the committed ncu summary for a variant's step kernels."""
+    return "k_flow_energy_batch" if kind == KIND_SPLIT else kernel_name(tile, kind)
+
+
+def step_launches(cases, tile, kind=KIND_FUSED, nsub=1):
+    """Step-kernel launches per step (the reduction aside): a flow launch and N
+    energy launches for a split variant, one for a fused tiled variant, one per
+    distinct row stride (width rounded up to 32) for a row-marching variant."""
+    if kind == KIND_SPLIT:
+        return 1 + nsub
     if tile[0] != 0:
         return 1
     return len({(c.nx + 31) // 32 for c in cases})
 
 
-def read_traffic(tile):
+def read_traffic(tile, kind=KIND_FUSED):
     """DRAM bytes per step of the step kernel(s) from the committed ncu summary, if
     it was taken on the current kernel source and the same tile variant."""
-    path = os.path.join(ROOT, "profiles", kernel_name(tile) + "_sweep32.md")
+    path = os.path.join(ROOT, "profiles", profile_name(tile, kind) + "_sweep32.md")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -300,14 +316,16 @@ def run_ours(args):
     # warm-up
     n_ev = min(args.steps, 500)
     ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+    ev_f = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
     ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
     with torch.cuda.stream(stream):
-        for e in ev_b + ev_a:
+        for e in ev_b + ev_f + ev_a:
             e.record(stream)  # creates the underlying cudaEvent_t
     # warm-up: the tile-shape autotuner times every compiled variant on the
     # sweep itself (ordinary steps), then the remaining warm-up steps; a fixed
     # --tile-variant skips the tuning (profiler runs, where tuning times are distorted)
     variants = hlb.tile_variants()
+    kinds = hlb.variant_kinds()
     if args.tile_variant is None:
         chosen, tune_ms = batch.autotune(steps_per_variant=4)
     else:
@@ -317,8 +335,9 @@ def run_ours(args):
         batch.step_profiled(None, None)
     torch.cuda.synchronize()
 
+    kind = kinds[chosen]
     # timed region: K steps as the library takes them (CUDA-graph replay of
-    # 16-step chunks, each step a step launch and a reduction launch), CUDA
+    # 16-step chunks, each step the step kernels and a reduction launch), CUDA
     # events on the batch stream around the whole region
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
@@ -332,10 +351,11 @@ def run_ours(args):
     batch.step(args.steps)
     end.record(stream)
     torch.cuda.synchronize()
-    # the step kernel alone for the roofline: the same steps one launch at a
-    # time, each step kernel bracketed by events on the batch stream
+    # the step kernels alone for the roofline: the same steps launched one at a
+    # time, with events on the batch stream before the step kernels, between
+    # the flow and energy kernels (split step) and after them
     for k in range(n_ev):
-        batch.step_profiled(ev_b[k], ev_a[k])
+        batch.step_phases(ev_b[k], ev_f[k], ev_a[k])
     torch.cuda.synchronize()
     clk = clocks.stop()
     if dist:
@@ -344,6 +364,14 @@ def run_ours(args):
     kern_ms = [ev_b[k].elapsed_time(ev_a[k]) for k in range(n_ev)]
     ms_per_step, value = aggregate(elapsed_ms, cells, args.steps, dist)
     kern_avg_ms = sum(kern_ms) / len(kern_ms)
+    kernels = None
+    if kind == KIND_SPLIT:
+        flow_ms = sum(ev_b[k].elapsed_time(ev_f[k]) for k in range(n_ev)) / n_ev
+        en_ms = sum(ev_f[k].elapsed_time(ev_a[k]) for k in range(n_ev)) / n_ev
+        fb = FLOW_BYTES_FLUID * n_fluid
+        eb = ENERGY_BYTES_FLUID * n_fluid + ENERGY_BYTES_SOLID * n_solid
+        kernels = {"k_flow_batch": {"ms": flow_ms, "bytes_per_launch": fb, "gbs": fb / (flow_ms * 1e-3) / 1e9},
+                   "k_energy_batch": {"ms": en_ms, "bytes_per_launch": eb, "gbs": eb / (en_ms * 1e-3) / 1e9}}
     diag0 = batch.diag(0, check_flags=False)
 
     # end to end through the public API with host buffers
@@ -353,7 +381,10 @@ def run_ours(args):
 
     peak, peak_src = peak_gbs()
     achieved = bytes_per_step / (kern_avg_ms * 1e-3) / 1e9
-    traffic = read_traffic(variants[chosen])
+    traffic = read_traffic(variants[chosen], kind)
+    if kernels:
+        for kv in kernels.values():
+            kv["frac"] = kv["gbs"] / peak
 
     line = None
     if rank == 0:
@@ -372,15 +403,15 @@ def run_ours(args):
                                 "tuning_ms_per_step": [round(m, 4) for m in tune_ms]}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": kernel_name(variants[chosen]), "bytes_per_launch": bytes_per_step,
-                         "kernel_ms": kern_avg_ms, "peak_source": peak_src},
+                         "kernel": kernel_name(variants[chosen], kind), "bytes_per_launch": bytes_per_step,
+                         "bytes_note": "the step's algorithmic bytes (80 B per fluid cell, 8 B per solid cell) "
+                                       "over the step kernels' time per step",
+                         "kernel_ms": kern_avg_ms, "peak_source": peak_src, "per_kernel": kernels},
             "cpu_baseline": {"value": cpu["mlups"], "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"FP64 oracle, sweep domain 0 ({cpu['nx']}x{cpu['ny']}), "
                                        f"{cpu['steps']} steps in {cpu['seconds']:.1f} s, one thread"},
             "e2e": e2e,
-            "gpu_launches": (step_launches(cases, variants[chosen]) + 1) * args.steps,
-            "issue_bound": {"note": "the step kernel is bound by instruction issue and L2 latency of halo reads, "
-                                    "not HBM; see profiles/k_step_batch_sweep32.md"},
+            "gpu_launches": (step_launches(cases, variants[chosen], kind) + 1) * args.steps,
             "clocks": clk,
             "points_per_hour": pph,
             "probe_2048": probe,

@@ -83,9 +83,9 @@ typedef struct {
   int eos_T_fixed;     /* 1: the EOS uses Ts everywhere (Section 3.2)               */
   int n_sub;           /* N of Eq. (27), 1..64, or 0: hlb_stable_substeps (1 for the
                           paper's parameters).  N > 1 holds rho^n and u^n over the
-                          sub-steps and runs for single domains with HLB_DIFF_FV;
-                          batches, the isotropic scheme and hlb_step_static take
-                          N = 1 only                                              */
+                          sub-steps and runs with HLB_DIFF_FV, for single domains
+                          and batches (a batch shares one N); the isotropic scheme
+                          and hlb_step_static take N = 1 only                     */
   int storage;         /* HLB_STORE_DEVIATION | HLB_STORE_PLAIN                      */
   double a, b, R, omega, Ts_over_Tc;   /* Eq. (28): 3/49, 2/21, 1, 0.344, 0.86        */
   double G, sigma, sigma_coef;         /* Eqs. (6)-(8): -1, 0.107, 12                 */
@@ -153,8 +153,8 @@ hlb_status hlb_eos_coexistence(const hlb_params* p, double* Tc, double* rho_l, d
                                double* h_fg);
 
 /* Device bytes one domain needs (fields double-buffered, per-block FP64 partials,
- * site table, flux history; for N > 1 also rho, u and T planes and the
- * sub-steps' partials).  0 on invalid parameters, which include lattices
+ * site table, flux history, the rho^n, u^n and scratch T planes of the split
+ * step; for N > 1 also the fused kernels' sub-step partials).  0 on invalid parameters, which include lattices
  * whose nine population planes would exceed 2^31 floats (about 238 million
  * cells, e.g. 15,000 x 15,000 fits, 16,384 x 16,384 does not). */
 size_t hlb_workspace_bytes(const hlb_params* p);
@@ -181,8 +181,10 @@ hlb_status hlb_set_wall(hlb_domain* d, double T_bottom);
 hlb_status hlb_set_nucleation_sites(hlb_domain* d, int n, const hlb_site* h_sites);
 
 /* Advance nsteps coupled steps (asynchronous on the handle's stream).
- * Repeated calls reuse a captured CUDA graph of the step pair (fused step
- * kernel + FP64 reduction kernel). */
+ * Repeated calls reuse a captured CUDA graph of 16 steps.  A step of the split
+ * form (the default for HLB_DIFF_FV) is a flow kernel, N energy sub-step
+ * kernels and an FP64 reduction kernel; a step of a fused variant is the fused
+ * step kernel and the reduction (see the autotuning section). */
 hlb_status hlb_step(hlb_domain* d, int nsteps);
 
 /* Fields after the last step: rho^n, u^n (the step's pre-collision moments,
@@ -242,11 +244,14 @@ hlb_status hlb_checkpoint_load(hlb_domain* d, const void* h_buf, size_t len);
 
 /* ------------------------------------------------------------------ batch
  * A boiling-curve sweep: n independent domains (each with its own size,
- * superheat and sites) advanced together.  One step is a single launch of the
- * fused step kernel whose blocks cover the tiles of every active domain
- * (a descriptor table maps block -> domain, tile), followed by one FP64
- * reduction launch with one CTA per domain.  Repeated hlb_batch_step calls
- * replay a captured CUDA graph of 16 such steps. */
+ * superheat and sites; one model parameter set, N of Eq. 27 included)
+ * advanced together.  In the split form (default) one step is a single launch
+ * of the flow kernel whose blocks cover the flow tiles of every active domain
+ * (a descriptor table maps block -> domain, tile), N launches of the energy
+ * sub-step kernel over every domain's energy tiles, and one FP64 reduction
+ * launch with one CTA per domain; a fused variant replaces the first two by
+ * one launch of the fused step kernel (N = 1 only).  Repeated hlb_batch_step
+ * calls replay a captured CUDA graph of 16 such steps. */
 
 /* Device bytes for n domains with parameters p[0..n-1]; 0 if any is invalid. */
 size_t hlb_batch_workspace_bytes(int n, const hlb_params* p);
@@ -270,9 +275,15 @@ hlb_status hlb_batch_step(hlb_batch* b, int nsteps);
 
 /* One batch step launched directly (no graph), with the caller's CUDA events
  * (cudaEvent_t as void*, either may be NULL) recorded on the batch stream
- * immediately before and after the fused step kernel, so that its duration
- * can be measured apart from the reduction. */
+ * immediately before and after the step kernels (the fused step kernel, or
+ * the flow and energy kernels of a split step), so that their duration can be
+ * measured apart from the reduction. */
 hlb_status hlb_batch_step_profiled(hlb_batch* b, void* ev_before, void* ev_after);
+
+/* As hlb_batch_step_profiled, with one more event (may be NULL) recorded
+ * between the flow kernel and the energy kernels of a split step (not
+ * recorded by a fused variant), so that each kernel can be timed. */
+hlb_status hlb_batch_step_phases(hlb_batch* b, void* ev_before, void* ev_flow, void* ev_after);
 
 /* As hlb_read / hlb_diag for domain i. */
 hlb_status hlb_batch_read(hlb_batch* b, int i, float* d_rho, float* d_ux, float* d_uy, float* d_T);
@@ -294,14 +305,20 @@ hlb_status hlb_batch_checkpoint_load(hlb_batch* b, int i, const void* h_buf, siz
 hlb_status hlb_batch_destroy(hlb_batch* b);
 
 /* ------------------------------------------------------------- autotuning
- * The fused step is compiled in two forms: tiled kernels (52 columns by a few
- * heights, with 256 or 512 threads per CTA; the default) and row-marching
- * kernels (one CTA per full-width segment of 32, 48 or 64 rows, one thread per
- * column, for lattices up to 512 columns and the finite-volume scheme only;
- * a batch launches one kernel per row stride).  hlb_tile_variants lists them
- * (returns their count; arrays may be NULL): a tiled variant reports its tile
- * width, height and threads, a row-marching one reports width 0, its segment
- * height and 0 threads.  hlb_autotune / hlb_batch_autotune run one untimed and
+ * The step is compiled in three kinds (hlb_variant_kind):
+ *  - HLB_KIND_SPLIT: a flow kernel over tiles of 64 columns by a few fluid-row
+ *    heights, then N energy sub-step kernels over 56 x 24 tiles (finite-volume
+ *    scheme; the default for it);
+ *  - HLB_KIND_FUSED: one fused step kernel over 52-column tiles of a few
+ *    heights, with 256 or 512 threads per CTA (the default for the isotropic
+ *    scheme, which only this kind runs);
+ *  - HLB_KIND_MARCH: one fused kernel per full-width segment of 32, 48 or 64
+ *    rows, one thread per column, for lattices up to 512 columns and the
+ *    finite-volume scheme only (a batch launches one kernel per row stride).
+ * hlb_tile_variants lists them in that order (returns their count; arrays may
+ * be NULL): a split variant reports its flow tile's width, height and threads,
+ * a fused tiled one its tile's, a row-marching one width 0, its segment height
+ * and 0 threads.  hlb_variant_kind(v) returns the kind of variant v, or -1.  hlb_autotune / hlb_batch_autotune run one untimed and
  * then steps_per_variant timed steps of every variant available to the
  * handle on its own state (others report 1e30 ms), keep the fastest for later
  * steps and report its index in *chosen (and the measured ms per step in
@@ -310,22 +327,26 @@ hlb_status hlb_batch_destroy(hlb_batch* b);
  * arithmetic (tiled shapes differ only in the order of the FP64 partial sums,
  * hence in the last bits of the mean density of Eq. 9; the two forms agree to
  * FP32 rounding).  Synchronises the stream. */
+enum { HLB_KIND_SPLIT = 0, HLB_KIND_FUSED = 1, HLB_KIND_MARCH = 2 };
 int hlb_tile_variants(int* h_tile_w, int* h_tile_h, int* h_threads, int max_out);
+int hlb_variant_kind(int v);
 hlb_status hlb_autotune(hlb_domain* d, int steps_per_variant, int* chosen, float* h_ms, int max_out);
 hlb_status hlb_batch_autotune(hlb_batch* b, int steps_per_variant, int* chosen, float* h_ms, int max_out);
 
 /* Select variant v (0 <= v < hlb_tile_variants(...)) for later steps without
  * timing anything, e.g. to reproduce a launch configuration under a profiler.
- * HLB_EINVAL for a NULL handle, v out of range, or a row-marching variant the
- * handle cannot use (a lattice wider than 512 columns, the isotropic scheme). */
+ * HLB_EINVAL for a NULL handle, v out of range, or a variant the handle cannot
+ * use (a row-marching one on a lattice wider than 512 columns; a split or
+ * row-marching one with the isotropic scheme; a fused one in a batch with
+ * N > 1). */
 hlb_status hlb_set_tile_variant(hlb_domain* d, int v);
 hlb_status hlb_batch_set_tile_variant(hlb_batch* b, int v);
 
 /* ------------------------------------------------------- no-allocation step
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory (a plug-in inside an application that owns
- * every allocation through its own pool, a callback running inside another
- * component's graph capture or real-time loop).  One coupled step, exactly as
+ * every allocation through its own pool, or a process whose device memory is
+ * fully reserved up front).  One coupled step, as the fused tiled kernel of
  * hlb_step performs it, of a domain whose state lives in the caller's buffers:
  *   d_f_in / d_f_out   9 planes of nx*ny FP32 populations (plane q at offset
  *                      q*nx*ny), deviations f_q - w_q rho_v for
@@ -345,10 +366,12 @@ hlb_status hlb_batch_set_tile_variant(hlb_batch* b, int v);
  * HLB_STATIC_SCRATCH_BYTES inside the library, held by every GPU that loads it
  * until exit; no call allocates.  Limits: nx <= HLB_STATIC_MAX_NX and at most
  * 17,549 tiles of 52 x 28 cells (about 25.5 million cells); larger lattices
- * return HLB_EINVAL.  The first call on a device resolves the array's address
- * with that device current (make that first call before any stream capture).
- * Every call shares the array and clears what must start at zero; calls that
- * overlap on the GPU race. */
+ * return HLB_EINVAL.  Every call resolves the array's address on the current
+ * device (cudaGetSymbolAddress, which allocates nothing); the first call on a
+ * device also sets that device's kernel attributes, so make it before any
+ * stream capture.  Each call reads the diagnostics record back to h_out and
+ * synchronises the stream before it returns.  Every call shares the array and
+ * clears what must start at zero; calls that overlap on the GPU race. */
 #define HLB_STATIC_SCRATCH_BYTES (1u << 20)
 #define HLB_STATIC_MAX_NX 16384
 #define HLB_STATIC_MAX_SITES 32

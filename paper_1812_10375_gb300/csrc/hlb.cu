@@ -5,13 +5,13 @@
 #include <stdlib.h>
 #include <string.h>
 
-#include <mutex>
 #include <new>
 #include <vector>
 
 #include "hlb.h"
 #include "hlb_kernels.cuh"
 #include "hlb_march.cuh"
+#include "hlb_split.cuh"
 #include "hlb_substep.cuh"
 
 using namespace hlb;
@@ -50,20 +50,64 @@ constexpr int NVARIANTS = (int)(sizeof(VARIANTS) / sizeof(VARIANTS[0]));
 constexpr int TILE_Y = 28;      // the default variant's tile height (variant 0)
 constexpr int MIN_TILE_Y = 16;  // the shortest variant tile (sizes the partial-sum slots)
 
-// Row-marching variants (k_march*): variant NVARIANTS + k walks segments of
-// MARCH_SEGS[k] rows with one thread per column; only for nx <= MARCH_MAX_NX.
+// Split-step variants (k_flow* then k_energy*): the flow tile's fluid rows and
+// threads; the energy tile is the same for all of them.
+struct FlowVariant {
+  int ty, nth;
+  size_t smem;
+  const void* single_fn;
+  const void* batch_fn;
+  void (*launch_single)(dim3, size_t, cudaStream_t, const StepArgs&);
+  void (*launch_batch)(int, size_t, cudaStream_t, const StepArgs&, const DomArgs*, const int2*, const int*,
+                       const float2*);
+};
+template <int TY, int NTH, int MINB>
+void launch_flow_single(dim3 grid, size_t smem, cudaStream_t s, const StepArgs& a) {
+  k_flow<TY, NTH, MINB><<<grid, NTH, smem, s>>>(a);
+}
+template <int TY, int NTH, int MINB>
+void launch_flow_batch(int blocks, size_t smem, cudaStream_t s, const StepArgs& phys, const DomArgs* desc,
+                       const int2* blk, const int* act, const float2* lag) {
+  k_flow_batch<TY, NTH, MINB><<<blocks, NTH, smem, s>>>(phys, desc, blk, act, lag);
+}
+#define HLB_FLOW_ENTRY(TY, NTH, MINB)                                                                     \
+  FlowVariant{TY, NTH, flow_smem_bytes<TY>(), (const void*)k_flow<TY, NTH, MINB>,                         \
+              (const void*)k_flow_batch<TY, NTH, MINB>, launch_flow_single<TY, NTH, MINB>,                \
+              launch_flow_batch<TY, NTH, MINB>},
+const FlowVariant FLOWS[] = {HLB_FLOW_VARIANTS(HLB_FLOW_ENTRY)};
+constexpr int NSPLIT = (int)(sizeof(FLOWS) / sizeof(FLOWS[0]));
+constexpr int MIN_FLOW_TY = 8;  // the shortest flow tile (sizes the flow partial-sum slots)
+
+// Variant numbering: [0, NSPLIT) split step, then the fused tiled kernels
+// (VARIANTS), then the row-marching kernels (k_march*: segments of
+// MARCH_SEGS[k] rows with one thread per column; only for nx <= MARCH_MAX_NX).
 #define HLB_MARCH_ENTRY(S) S,
 constexpr int MARCH_SEGS[] = {HLB_MARCH_SEGMENTS(HLB_MARCH_ENTRY)};
 constexpr int NMARCH = (int)(sizeof(MARCH_SEGS) / sizeof(MARCH_SEGS[0]));
-constexpr int NV_ALL = NVARIANTS + NMARCH;
+constexpr int NV_ALL = NSPLIT + NVARIANTS + NMARCH;
+constexpr int FIRST_TILED = NSPLIT;
 static_assert(MARCH_SEGS[0] >= MIN_TILE_Y, "march segments must not outnumber the partial-sum slots");
-bool is_march(int v) { return v >= NVARIANTS; }
-int march_seg(int v) { return MARCH_SEGS[v - NVARIANTS]; }
+bool is_split(int v) { return v < NSPLIT; }
+bool is_march(int v) { return v >= NSPLIT + NVARIANTS; }
+int tiled_index(int v) { return v - NSPLIT; }  // index into VARIANTS of a fused tiled variant
+int march_seg(int v) { return MARCH_SEGS[v - NSPLIT - NVARIANTS]; }
 size_t march_smem(int nx) { return (size_t)march_smem_floats(nx) * sizeof(float); }
 
-dim3 grid_of(int nx, int ny, int v) {
+int fluid_rows_of(int ny, int W, int top_bc) { return fluid_end(ny, top_bc) - W; }
+
+// Launch grid of the step kernel of variant v (the flow kernel for a split variant).
+dim3 grid_of(int nx, int ny, int W, int top_bc, int v) {
+  if (is_split(v)) {
+    const int ty = FLOWS[v].ty;
+    return dim3((nx + FL_TX - 1) / FL_TX, (fluid_rows_of(ny, W, top_bc) + ty - 1) / ty);
+  }
   if (is_march(v)) return dim3((ny + march_seg(v) - 1) / march_seg(v), 1);
-  return dim3((nx + TILE_X - 1) / TILE_X, (ny + VARIANTS[v].ty - 1) / VARIANTS[v].ty);
+  const int t = tiled_index(v);
+  return dim3((nx + TILE_X - 1) / TILE_X, (ny + VARIANTS[t].ty - 1) / VARIANTS[t].ty);
+}
+dim3 energy_grid_of(int nx, int ny) { return dim3((nx + EN_TX - 1) / EN_TX, (ny + EN_TY - 1) / EN_TY); }
+size_t flow_part_slots(int nx, int ny, int W, int top_bc) {
+  return (size_t)((nx + FL_TX - 1) / FL_TX) * ((fluid_rows_of(ny, W, top_bc) + MIN_FLOW_TY - 1) / MIN_FLOW_TY);
 }
 constexpr int GRAPH_STEPS = 16;     // steps per captured graph (even: buffers return to parity 0)
 constexpr int HIST_CAP = 1 << 16;   // wall-flux history entries kept per domain
@@ -254,6 +298,10 @@ struct hlb_domain {
   float* Tscr = nullptr;
   double* subpart = nullptr;
   dim3 sub_grid;
+  // split step: per-tile partials of the flow and energy kernels, energy grid
+  double* fpart = nullptr;
+  double* epart = nullptr;
+  dim3 egrid;
   int parity = 0;
   long long steps = 0;
   bool fields_set = false;
@@ -269,7 +317,7 @@ struct hlb_domain {
 namespace {
 
 struct Layout {
-  size_t f, T, Gw, ftop, partials, state, hist, sub, total;
+  size_t f, T, Gw, ftop, partials, state, hist, mom, fpart, epart, sub, total;
 };
 
 dim3 sub_grid_of(int nx, int ny) { return dim3((nx + SUB_TX - 1) / SUB_TX, (ny + SUB_TY - 1) / SUB_TY); }
@@ -287,10 +335,15 @@ Layout layout_of(const hlb_params* p) {
   L.partials = o; o += align_up((nblk > INIT_BLOCKS ? nblk : INIT_BLOCKS) * NPART * sizeof(double));
   L.state = o;    o += align_up(sizeof(DevState));
   L.hist = o;     o += align_up(HIST_CAP * sizeof(double));
+  // rho^n, u_x^n, u_y^n of the step and a T plane for sub-steps
+  L.mom = o;      o += align_up(4 * N * sizeof(float));
+  L.fpart = o;    o += align_up(flow_part_slots(p->nx, p->ny, p->wall_rows, p->top_bc) * NFPART * sizeof(double));
+  const dim3 eg = energy_grid_of(p->nx, p->ny);
+  L.epart = o;    o += align_up((size_t)eg.x * eg.y * NEPART * sizeof(double));
   L.sub = o;
   if (resolved_nsub(p) > 1) {
+    // the fused kernels' sub-step partials (Eq. 27)
     const dim3 sg = sub_grid_of(p->nx, p->ny);
-    o += align_up(4 * N * sizeof(float));  // rho, u_x, u_y, T
     o += align_up((size_t)sg.x * sg.y * NSUBPART * sizeof(double));
   }
   L.total = o;
@@ -312,12 +365,33 @@ StepArgs args_for(hlb_domain* d, int par) {
   return a;
 }
 
-hlb_status launch_step(hlb_domain* d) {
+// One step of the split form: the flow kernel, N energy sub-steps, the reduction.
+hlb_status launch_split_step(hlb_domain* d, cudaEvent_t after_flow = nullptr, cudaEvent_t after_energy = nullptr) {
   const StepArgs a = args_for(d, d->parity);
-  if (is_march(d->variant))
+  const FlowVariant& fv = FLOWS[d->variant];
+  fv.launch_single(d->grid, fv.smem, d->stream, a);
+  if (after_flow && cudaEventRecord(after_flow, d->stream) != cudaSuccess) return HLB_ECUDA;
+  const int nsub = d->p.n_sub;
+  for (int s = 1; s <= nsub; ++s) k_energy<<<d->egrid, EN_NT, energy_smem_bytes(), d->stream>>>(a, s, nsub);
+  if (after_energy && cudaEventRecord(after_energy, d->stream) != cudaSuccess) return HLB_ECUDA;
+  k_reduce_split<<<1, 256, 0, d->stream>>>(d->fpart, (int)(d->grid.x * d->grid.y), d->epart,
+                                           (int)(d->egrid.x * d->egrid.y), d->state, 1.0 / (double)d->n_fluid,
+                                           1.0 / (double)d->p.nx, d->hist, HIST_CAP);
+  if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
+  d->parity ^= 1;
+  d->steps += 1;
+  return HLB_OK;
+}
+
+hlb_status launch_step(hlb_domain* d) {
+  if (is_split(d->variant)) return launch_split_step(d);
+  const StepArgs a = args_for(d, d->parity);
+  if (is_march(d->variant)) {
     k_march<<<d->grid, march_row_stride(d->p.nx), march_smem(d->p.nx), d->stream>>>(a, march_seg(d->variant));
-  else
-    VARIANTS[d->variant].launch_single(d->grid, VARIANTS[d->variant].smem, d->stream, a);
+  } else {
+    const Variant& tv = VARIANTS[tiled_index(d->variant)];
+    tv.launch_single(d->grid, tv.smem, d->stream, a);
+  }
   k_reduce<<<1, 256, 0, d->stream>>>(d->partials, (int)(d->grid.x * d->grid.y), d->state, 1.0 / (double)d->n_fluid,
                                      1.0 / (double)d->p.nx, d->hist, HIST_CAP);
   if (d->p.n_sub > 1) {
@@ -381,6 +455,15 @@ hlb_status build_graph(hlb_domain* d) {
 }  // namespace
 
 namespace {
+// Whether variant v can run domain d: the row-marching kernels need nx <=
+// MARCH_MAX_NX; the split step and the row-marching kernels take the
+// finite-volume scheme only; the fused tiled kernel is the isotropic scheme's.
+bool variant_ok(const hlb_domain* d, int v) {
+  if (is_march(v)) return d->p.nx <= MARCH_MAX_NX && d->p.diffusion == HLB_DIFF_FV;
+  if (is_split(v)) return d->p.diffusion == HLB_DIFF_FV;
+  return true;
+}
+
 // Initial state into buffer set `par` (the other T buffer gets the same T, so
 // that hlb_read after an odd number of steps finds T^n).
 hlb_status set_fields_at(hlb_domain* d, const float* d_rho, const float* d_T, int par) {
@@ -427,16 +510,20 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
   d->partials = (double*)(ws + L.partials);
   d->state = (DevState*)(ws + L.state);
   d->hist = (double*)(ws + L.hist);
+  d->mom = (float*)(ws + L.mom);
+  d->Tscr = d->mom + 3 * N;
+  d->fpart = (double*)(ws + L.fpart);
+  d->epart = (double*)(ws + L.epart);
+  d->egrid = energy_grid_of(q.nx, q.ny);
   if (q.n_sub > 1) {
-    d->mom = (float*)(ws + L.sub);
-    d->Tscr = d->mom + 3 * N;
-    d->subpart = (double*)(ws + L.sub + align_up(4 * N * sizeof(float)));
+    d->subpart = (double*)(ws + L.sub);
     d->sub_grid = sub_grid_of(q.nx, q.ny);
   }
   const int fluid_rows = q.ny - q.wall_rows - (q.top_bc == HLB_TOP_WALL ? 1 : 0);
   d->n_fluid = (long long)fluid_rows * q.nx;
-  d->variant = 0;
-  d->grid = grid_of(q.nx, q.ny, d->variant);
+  // the split step for the finite-volume scheme; the fused tiled kernel for the isotropic one
+  d->variant = q.diffusion == HLB_DIFF_FV ? 0 : FIRST_TILED;
+  d->grid = grid_of(q.nx, q.ny, q.wall_rows, q.top_bc, d->variant);
   d->smem = smem_bytes();
 
   StepArgs& a = d->base;
@@ -485,7 +572,23 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
   a.Gw = d->Gw;
   a.partials = d->partials;
   a.state = d->state;
+  a.mom = d->mom;
+  a.T_scr = d->Tscr;
+  a.fpart = d->fpart;
+  a.epart = d->epart;
 
+  for (int v = 0; v < NSPLIT; ++v) {
+    if (cudaFuncSetAttribute(FLOWS[v].single_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FLOWS[v].smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(FLOWS[v].batch_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FLOWS[v].smem) !=
+            cudaSuccess)
+      return HLB_ECUDA;
+  }
+  if (cudaFuncSetAttribute(k_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)energy_smem_bytes()) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_energy_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)energy_smem_bytes()) !=
+          cudaSuccess)
+    return HLB_ECUDA;
   for (int v = 0; v < NVARIANTS; ++v) {
     if (cudaFuncSetAttribute(VARIANTS[v].single_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)VARIANTS[v].smem) != cudaSuccess ||
@@ -516,7 +619,11 @@ struct hlb_batch {
   DomArgs* d_desc = nullptr;   // [2][n]: per-domain descriptors for batch parity 0 and 1
   StepArgs phys;               // model parameters shared by the batch
   ReduceArgs* d_ra = nullptr;  // [n]
+  SplitReduceArgs* d_sra = nullptr;  // [n]: the split step's reduction
   int2* d_blk = nullptr;       // [blocks]: (domain, tile within the domain) of each step block
+  int2* d_eblk = nullptr;      // [energy blocks] of the split step
+  std::vector<int2> eblk;      // host copy of d_eblk
+  int total_etiles = 0;
   int* d_active = nullptr;     // [n]
   float2* d_lag = nullptr;     // [n]: lagged U/(1+U) and mean density, written by the reduction
   std::vector<int> tile_off;
@@ -549,20 +656,26 @@ namespace {
 
 struct BatchLayout {
   std::vector<size_t> dom_off;
-  size_t desc, ra, blk, active, lag, total;
+  size_t desc, ra, sra, blk, eblk, active, lag, total;
 };
 
 BatchLayout batch_layout(int n, const hlb_params* p) {
   BatchLayout L;
-  size_t o = 0, max_blocks = 0;
+  size_t o = 0, max_blocks = 0, max_eblocks = 0;
   for (int i = 0; i < n; ++i) {
     L.dom_off.push_back(o);
     o += layout_of(p + i).total;
-    max_blocks += (size_t)((p[i].nx + TILE_X - 1) / TILE_X) * ((p[i].ny + MIN_TILE_Y - 1) / MIN_TILE_Y);
+    const size_t tiled = (size_t)((p[i].nx + TILE_X - 1) / TILE_X) * ((p[i].ny + MIN_TILE_Y - 1) / MIN_TILE_Y);
+    const size_t flow = flow_part_slots(p[i].nx, p[i].ny, p[i].wall_rows, p[i].top_bc);
+    max_blocks += tiled > flow ? tiled : flow;
+    const dim3 eg = energy_grid_of(p[i].nx, p[i].ny);
+    max_eblocks += (size_t)eg.x * eg.y;
   }
   L.desc = o;     o += align_up(2 * (size_t)n * sizeof(DomArgs));
   L.ra = o;       o += align_up((size_t)n * sizeof(ReduceArgs));
+  L.sra = o;      o += align_up((size_t)n * sizeof(SplitReduceArgs));
   L.blk = o;      o += align_up(max_blocks * sizeof(int2));
+  L.eblk = o;     o += align_up(max_eblocks * sizeof(int2));
   L.active = o;   o += align_up((size_t)n * sizeof(int));
   L.lag = o;      o += align_up((size_t)n * sizeof(float2));
   L.total = o;
@@ -588,6 +701,10 @@ DomArgs dom_args(const StepArgs& a) {
   d.ftop_out = a.ftop_out;
   d.partials = a.partials;
   d.state = a.state;
+  d.mom = a.mom;
+  d.T_scr = a.T_scr;
+  d.fpart = a.fpart;
+  d.epart = a.epart;
   return d;
 }
 
@@ -601,12 +718,15 @@ StepArgs physics_of(const StepArgs& a) {
   p.f_out = p.T_out = p.ftop_out = nullptr;
   p.partials = nullptr;
   p.state = nullptr;
+  p.mom = p.T_scr = nullptr;
+  p.fpart = p.epart = nullptr;
   return p;
 }
 
 hlb_status upload_tables(hlb_batch* b) {
   std::vector<DomArgs> desc(2 * (size_t)b->n);
   std::vector<ReduceArgs> ra(b->n);
+  std::vector<SplitReduceArgs> sra(b->n);
   const std::vector<int2>& blk = b->blk;
   for (int i = 0; i < b->n; ++i) {
     hlb_domain* d = &b->dom[i];
@@ -618,22 +738,58 @@ hlb_status upload_tables(hlb_batch* b) {
     ra[i].nblk = (int)(d->grid.x * d->grid.y);
     ra[i].inv_nfluid = 1.0 / (double)d->n_fluid;
     ra[i].inv_nx = 1.0 / (double)d->p.nx;
+    sra[i].fpart = d->fpart;
+    sra[i].epart = d->epart;
+    sra[i].state = d->state;
+    sra[i].hist = d->hist;
+    sra[i].nf = (int)(d->grid.x * d->grid.y);
+    sra[i].ne = (int)(d->egrid.x * d->egrid.y);
+    sra[i].inv_nfluid = ra[i].inv_nfluid;
+    sra[i].inv_nx = ra[i].inv_nx;
   }
   if (cudaMemcpyAsync(b->d_desc, desc.data(), desc.size() * sizeof(DomArgs), cudaMemcpyHostToDevice, b->stream) !=
           cudaSuccess ||
       cudaMemcpyAsync(b->d_ra, ra.data(), ra.size() * sizeof(ReduceArgs), cudaMemcpyHostToDevice, b->stream) !=
           cudaSuccess ||
+      cudaMemcpyAsync(b->d_sra, sra.data(), sra.size() * sizeof(SplitReduceArgs), cudaMemcpyHostToDevice,
+                      b->stream) != cudaSuccess ||
       cudaMemcpyAsync(b->d_blk, blk.data(), blk.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream) !=
           cudaSuccess ||
+      (!b->eblk.empty() && cudaMemcpyAsync(b->d_eblk, b->eblk.data(), b->eblk.size() * sizeof(int2),
+                                           cudaMemcpyHostToDevice, b->stream) != cudaSuccess) ||
       cudaMemcpyAsync(b->d_active, b->active.data(), b->active.size() * sizeof(int), cudaMemcpyHostToDevice,
                       b->stream) != cudaSuccess)
     return HLB_ECUDA;
   return cudaStreamSynchronize(b->stream) == cudaSuccess ? HLB_OK : HLB_ECUDA;
 }
 
-hlb_status batch_launch(hlb_batch* b, cudaEvent_t before, cudaEvent_t after) {
+// One batched step.  Events (any may be null): `before` the step kernels,
+// `mid` after the flow kernel of a split step, `after` the step kernels
+// (before the reduction).
+hlb_status batch_launch(hlb_batch* b, cudaEvent_t before, cudaEvent_t after, cudaEvent_t mid = nullptr) {
   if (before && cudaEventRecord(before, b->stream) != cudaSuccess) return HLB_ECUDA;
   const DomArgs* desc = b->d_desc + (size_t)b->parity * b->n;
+  if (is_split(b->variant)) {
+    const FlowVariant& fv = FLOWS[b->variant];
+    fv.launch_batch(b->total_tiles, fv.smem, b->stream, b->phys, desc, b->d_blk, b->d_active, b->d_lag);
+    if (mid && cudaEventRecord(mid, b->stream) != cudaSuccess) return HLB_ECUDA;
+    const int nsub = b->dom[0].p.n_sub;
+    for (int s = 1; s <= nsub; ++s)
+      k_energy_batch<<<b->total_etiles, EN_NT, energy_smem_bytes(), b->stream>>>(b->phys, desc, b->d_eblk,
+                                                                                 b->d_active, s, nsub);
+    if (after && cudaEventRecord(after, b->stream) != cudaSuccess) return HLB_ECUDA;
+    k_reduce_split_batch<<<b->n, 256, 0, b->stream>>>(b->d_sra, b->d_active, b->d_lag, HIST_CAP);
+    if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
+    b->parity ^= 1;
+    b->steps += 1;
+    for (int i = 0; i < b->n; ++i) {
+      if (b->active[i]) {
+        b->dom[i].parity ^= 1;
+        b->dom[i].steps += 1;
+      }
+    }
+    return HLB_OK;
+  }
   if (is_march(b->variant)) {
     const int S = march_seg(b->variant);
     if (cudaEventRecord(b->ev_fork, b->stream) != cudaSuccess) return HLB_ECUDA;
@@ -647,8 +803,8 @@ hlb_status batch_launch(hlb_batch* b, cudaEvent_t before, cudaEvent_t after) {
         return HLB_ECUDA;
     }
   } else {
-    VARIANTS[b->variant].launch_batch(b->total_tiles, VARIANTS[b->variant].smem, b->stream, b->phys, desc, b->d_blk,
-                                      b->d_active, b->d_lag);
+    const Variant& tv = VARIANTS[tiled_index(b->variant)];
+    tv.launch_batch(b->total_tiles, tv.smem, b->stream, b->phys, desc, b->d_blk, b->d_active, b->d_lag);
   }
   if (after && cudaEventRecord(after, b->stream) != cudaSuccess) return HLB_ECUDA;
   k_reduce_batch<<<b->n, 256, 0, b->stream>>>(b->d_ra, b->d_active, b->d_lag, HIST_CAP);
@@ -710,19 +866,34 @@ bool batch_march_ok(const hlb_batch* b) {
 
 // Select variant v for every domain of the batch: block table (grouped by row
 // stride for the row-marching variants), side streams, device tables.
+bool batch_variant_ok(const hlb_batch* b, int v) {
+  if (is_march(v) && !batch_march_ok(b)) return false;
+  // energy sub-steps (Eq. 27) run only in the split form
+  if (!is_split(v) && b->dom[0].p.n_sub > 1) return false;
+  return true;
+}
+
 hlb_status set_batch_variant(hlb_batch* b, int v) {
-  if (is_march(v) && !batch_march_ok(b)) return HLB_EINVAL;
+  if (!batch_variant_ok(b, v)) return HLB_EINVAL;
   b->variant = v;
   b->tile_off.assign(b->n + 1, 0);
   for (int i = 0; i < b->n; ++i) {
     hlb_domain* d = &b->dom[i];
     d->variant = v;
-    d->grid = grid_of(d->p.nx, d->p.ny, v);
+    d->grid = grid_of(d->p.nx, d->p.ny, d->p.wall_rows, d->p.top_bc, v);
     b->tile_off[i + 1] = b->tile_off[i] + (int)(d->grid.x * d->grid.y);
   }
   b->total_tiles = b->tile_off[b->n];
   b->blk.clear();
+  b->eblk.clear();
   b->groups.clear();
+  if (is_split(v)) {
+    for (int i = 0; i < b->n; ++i) {
+      const dim3 eg = b->dom[i].egrid;
+      for (int t = 0; t < (int)(eg.x * eg.y); ++t) b->eblk.push_back(make_int2(i, t));
+    }
+  }
+  b->total_etiles = (int)b->eblk.size();
   if (is_march(v)) {
     std::vector<int> strides;
     for (int i = 0; i < b->n; ++i) {
@@ -758,7 +929,7 @@ hlb_status set_batch_variant(hlb_batch* b, int v) {
     for (int i = 0; i < b->n; ++i)
       for (int t = b->tile_off[i]; t < b->tile_off[i + 1]; ++t) b->blk.push_back(make_int2(i, t - b->tile_off[i]));
   }
-  b->smem = is_march(v) ? march_smem(MARCH_MAX_NX) : VARIANTS[v].smem;
+  b->smem = is_split(v) ? FLOWS[v].smem : (is_march(v) ? march_smem(MARCH_MAX_NX) : VARIANTS[tiled_index(v)].smem);
   batch_drop_graph(b);
   return upload_tables(b);
 }
@@ -1107,7 +1278,7 @@ hlb_status hlb_checkpoint_load(hlb_domain* d, const void* h_buf, size_t len) {
 size_t hlb_batch_workspace_bytes(int n, const hlb_params* p) {
   if (n < 1 || !p) return 0;
   for (int i = 0; i < n; ++i)
-    if (!params_valid(p + i) || p[i].diffusion != HLB_DIFF_FV || resolved_nsub(p + i) != 1) return 0;
+    if (!params_valid(p + i) || p[i].diffusion != HLB_DIFF_FV) return 0;
   return batch_layout(n, p).total;
 }
 
@@ -1116,7 +1287,7 @@ hlb_status hlb_batch_init(hlb_batch** out, int n, const hlb_params* p, void* d_w
   if (!out || n < 1 || !p || !d_workspace) return HLB_EINVAL;
   *out = nullptr;
   for (int i = 0; i < n; ++i)
-    if (!params_valid(p + i) || p[i].diffusion != HLB_DIFF_FV || resolved_nsub(p + i) != 1) return HLB_EINVAL;
+    if (!params_valid(p + i) || p[i].diffusion != HLB_DIFF_FV) return HLB_EINVAL;
   if (((uintptr_t)d_workspace & 255) != 0) return HLB_EINVAL;
   const BatchLayout L = batch_layout(n, p);
   if (workspace_bytes < L.total) return HLB_EINVAL;
@@ -1147,7 +1318,9 @@ hlb_status hlb_batch_init(hlb_batch** out, int n, const hlb_params* p, void* d_w
   }
   b->d_desc = (DomArgs*)(ws + L.desc);
   b->d_ra = (ReduceArgs*)(ws + L.ra);
+  b->d_sra = (SplitReduceArgs*)(ws + L.sra);
   b->d_blk = (int2*)(ws + L.blk);
+  b->d_eblk = (int2*)(ws + L.eblk);
   b->d_active = (int*)(ws + L.active);
   b->d_lag = (float2*)(ws + L.lag);
   const hlb_status st = set_batch_variant(b, 0);
@@ -1220,6 +1393,13 @@ hlb_status hlb_batch_step_profiled(hlb_batch* b, void* ev_before, void* ev_after
   for (int i = 0; i < b->n; ++i)
     if (!b->dom[i].fields_set) return HLB_ESTATE;
   return batch_launch(b, (cudaEvent_t)ev_before, (cudaEvent_t)ev_after);
+}
+
+hlb_status hlb_batch_step_phases(hlb_batch* b, void* ev_before, void* ev_flow, void* ev_after) {
+  if (!b) return HLB_EINVAL;
+  for (int i = 0; i < b->n; ++i)
+    if (!b->dom[i].fields_set) return HLB_ESTATE;
+  return batch_launch(b, (cudaEvent_t)ev_before, (cudaEvent_t)ev_after, (cudaEvent_t)ev_flow);
 }
 
 hlb_status hlb_batch_read(hlb_batch* b, int i, float* d_rho, float* d_ux, float* d_uy, float* d_T) {
@@ -1302,12 +1482,12 @@ hlb_status hlb_autotune(hlb_domain* d, int steps_per_variant, int* chosen, float
   int best_v = 0;
   hlb_status st = HLB_OK;
   for (int v = 0; v < NV_ALL && st == HLB_OK; ++v) {
-    if (is_march(v) && (d->p.nx > MARCH_MAX_NX || d->p.diffusion != HLB_DIFF_FV)) {
-      if (h_ms && v < max_out) h_ms[v] = 1e30f;  // not available for this width or scheme
+    if (!variant_ok(d, v)) {
+      if (h_ms && v < max_out) h_ms[v] = 1e30f;  // not available for this width, scheme or N
       continue;
     }
     d->variant = v;
-    d->grid = grid_of(d->p.nx, d->p.ny, v);
+    d->grid = grid_of(d->p.nx, d->p.ny, d->p.wall_rows, d->p.top_bc, v);
     drop_graph(d);
     st = launch_step(d);  // one untimed step per variant (first-launch costs)
     cudaEventRecord(e0, d->stream);
@@ -1326,7 +1506,7 @@ hlb_status hlb_autotune(hlb_domain* d, int steps_per_variant, int* chosen, float
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   d->variant = best_v;
-  d->grid = grid_of(d->p.nx, d->p.ny, best_v);
+  d->grid = grid_of(d->p.nx, d->p.ny, d->p.wall_rows, d->p.top_bc, best_v);
   drop_graph(d);
   *chosen = best_v;
   return st;
@@ -1342,8 +1522,8 @@ hlb_status hlb_batch_autotune(hlb_batch* b, int steps_per_variant, int* chosen, 
   int best_v = 0;
   hlb_status st = HLB_OK;
   for (int v = 0; v < NV_ALL && st == HLB_OK; ++v) {
-    if (is_march(v) && !batch_march_ok(b)) {
-      if (h_ms && v < max_out) h_ms[v] = 1e30f;  // not available for these widths
+    if (!batch_variant_ok(b, v)) {
+      if (h_ms && v < max_out) h_ms[v] = 1e30f;  // not available for these widths or this N
       continue;
     }
     st = set_batch_variant(b, v);
@@ -1372,9 +1552,9 @@ hlb_status hlb_batch_autotune(hlb_batch* b, int steps_per_variant, int* chosen, 
 
 hlb_status hlb_set_tile_variant(hlb_domain* d, int v) {
   if (!d || v < 0 || v >= NV_ALL) return HLB_EINVAL;
-  if (is_march(v) && (d->p.nx > MARCH_MAX_NX || d->p.diffusion != HLB_DIFF_FV)) return HLB_EINVAL;
+  if (!variant_ok(d, v)) return HLB_EINVAL;
   d->variant = v;
-  d->grid = grid_of(d->p.nx, d->p.ny, v);
+  d->grid = grid_of(d->p.nx, d->p.ny, d->p.wall_rows, d->p.top_bc, v);
   drop_graph(d);
   return HLB_OK;
 }
@@ -1386,12 +1566,29 @@ hlb_status hlb_batch_set_tile_variant(hlb_batch* b, int v) {
 
 int hlb_tile_variants(int* h_tile_w, int* h_tile_h, int* h_threads, int max_out) {
   for (int v = 0; v < NV_ALL && v < max_out; ++v) {
-    // row-marching variants: full width (0), segment height, one thread per column (0)
-    if (h_tile_w) h_tile_w[v] = is_march(v) ? 0 : TILE_X;
-    if (h_tile_h) h_tile_h[v] = is_march(v) ? march_seg(v) : VARIANTS[v].ty;
-    if (h_threads) h_threads[v] = is_march(v) ? 0 : VARIANTS[v].nth;
+    // split step: the flow tile (64 columns, fluid rows, threads); fused tiled:
+    // the 52-column tile; row-marching: full width (0), segment height, one
+    // thread per column (0)
+    if (is_split(v)) {
+      if (h_tile_w) h_tile_w[v] = FL_TX;
+      if (h_tile_h) h_tile_h[v] = FLOWS[v].ty;
+      if (h_threads) h_threads[v] = FLOWS[v].nth;
+    } else if (is_march(v)) {
+      if (h_tile_w) h_tile_w[v] = 0;
+      if (h_tile_h) h_tile_h[v] = march_seg(v);
+      if (h_threads) h_threads[v] = 0;
+    } else {
+      if (h_tile_w) h_tile_w[v] = TILE_X;
+      if (h_tile_h) h_tile_h[v] = VARIANTS[tiled_index(v)].ty;
+      if (h_threads) h_threads[v] = VARIANTS[tiled_index(v)].nth;
+    }
   }
   return NV_ALL;
+}
+
+int hlb_variant_kind(int v) {
+  if (v < 0 || v >= NV_ALL) return -1;
+  return is_split(v) ? HLB_KIND_SPLIT : (is_march(v) ? HLB_KIND_MARCH : HLB_KIND_FUSED);
 }
 
 const char* hlb_strerror(hlb_status s) {
@@ -1414,9 +1611,8 @@ const char* hlb_strerror(hlb_status s) {
 //
 // Who needs it: code that runs where no allocator is available or allowed --
 // a solver embedded as a plug-in in a host application that owns every device
-// allocation through its own pool, a callback invoked inside someone else's
-// CUDA-graph capture or real-time loop where cudaMalloc would stall or fail, or
-// a process whose device memory is fully reserved up front.  Such a caller can
+// allocation through its own pool, or a process whose device memory is fully
+// reserved up front.  Such a caller can
 // still hand over its own state buffers (inputs and outputs), but cannot give
 // the library a workspace for the per-block FP64 partial sums, the device-side
 // diagnostics record and the wetting table.  This entry point takes those from
@@ -1428,11 +1624,11 @@ const char* hlb_strerror(hlb_status s) {
 // shares it and it keeps the last call's contents; the diagnostics record is
 // cleared at the start of each call and the partial sums are fully rewritten by
 // each step, so no call sees stale values.  Calls that overlap on the GPU (two
-// streams, or two host threads) race on the shared array.
+// streams, or two host threads) race on the shared array.  Each call reads the
+// step's diagnostics back to the host and synchronises its stream.
 
 namespace {
 
-constexpr int MAX_DEVICES = 64;
 constexpr size_t STATE_BYTES = 256;
 constexpr size_t GW_BYTES = (size_t)HLB_STATIC_MAX_NX * sizeof(float);
 constexpr size_t PART_BYTES = HLB_STATIC_SCRATCH_BYTES - STATE_BYTES - GW_BYTES;
@@ -1442,11 +1638,8 @@ static_assert(sizeof(DevState) <= STATE_BYTES, "device record does not fit its s
 // The scratch itself: [DevState | G_w table | per-block partials].
 static __device__ __align__(256) unsigned char g_scratch[HLB_STATIC_SCRATCH_BYTES];
 
-// Host-side address of g_scratch per device.  In host code the name g_scratch
-// is only a stand-in, not a device address; the real address comes from
-// cudaGetSymbolAddress with the device current.
-void* g_scratch_addr[MAX_DEVICES] = {nullptr};
-std::mutex g_setup_mutex;
+// In host code the name g_scratch is only a stand-in, not a device address;
+// the real address comes from cudaGetSymbolAddress with the device current.
 
 struct StaticSites {
   int n;
@@ -1482,21 +1675,17 @@ __global__ void k_static_prepare(DevState* st, float* Gw, int nx, double Gw0, St
   }
 }
 
-// Once per device, with that device current: resolve the address of g_scratch
-// and allow this translation unit's step kernel its dynamic shared memory.
+// On every call, with the caller's device current: resolve the address of
+// g_scratch (cheap, allocates nothing) and allow the step kernel its dynamic
+// shared memory.  Nothing is cached, so a device reset or a new primary
+// context between calls cannot leave a stale address behind.
 hlb_status setup_device(void** addr) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return HLB_ECUDA;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return HLB_ECUDA;
-    if (cudaFuncSetAttribute(VARIANTS[0].single_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)VARIANTS[0].smem) != cudaSuccess)
-      return HLB_ECUDA;
-    g_scratch_addr[dev] = p;
-  }
-  *addr = g_scratch_addr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return HLB_ECUDA;
+  if (cudaFuncSetAttribute(VARIANTS[0].single_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)VARIANTS[0].smem) != cudaSuccess)
+    return HLB_ECUDA;
+  *addr = p;
   return HLB_OK;
 }
 
@@ -1602,7 +1791,7 @@ extern "C" hlb_status hlb_step_static(const hlb_params* p, int n_sites, const hl
   const double n_fluid = (double)fluid_rows * q.nx;
 
   k_static_prepare<<<(q.nx + 255) / 256, 256, 0, s>>>(state, Gw, q.nx, q.Gw0, sites, rho_ave, U);
-  VARIANTS[0].launch_single(grid_of(q.nx, q.ny, 0), VARIANTS[0].smem, s, a);
+  VARIANTS[0].launch_single(grid_of(q.nx, q.ny, q.wall_rows, q.top_bc, FIRST_TILED), VARIANTS[0].smem, s, a);
   k_reduce<<<1, 256, 0, s>>>(partials, (int)nblk, state, 1.0 / n_fluid, 1.0 / (double)q.nx, nullptr, 0);
   if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;
 

@@ -59,6 +59,13 @@ struct StepArgs {
   float* __restrict__ ftop_out;
   double* __restrict__ partials;
   DevState* state;
+  // split step (flow kernel, then energy sub-steps): rho^n, u_x^n, u_y^n as three
+  // planes of nx ny floats written by the flow kernel, a temperature plane for
+  // sub-steps, and the per-tile partial sums of the two kernels
+  float* __restrict__ mom;
+  float* __restrict__ T_scr;
+  double* __restrict__ fpart;
+  double* __restrict__ epart;
 };
 
 // The per-domain part of StepArgs for the batched kernel (geometry, wall
@@ -77,6 +84,10 @@ struct DomArgs {
   float* ftop_out;
   double* partials;
   DevState* state;
+  float* mom;
+  float* T_scr;
+  double* fpart;
+  double* epart;
 };
 
 }  // namespace hlb

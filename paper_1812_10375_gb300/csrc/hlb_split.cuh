@@ -1,0 +1,643 @@
+// Split form of the coupled step of the hybrid thermal LB phase-change model
+// (Hu & Liu, arXiv 1812.10375): one step of a domain is a flow kernel, N
+// energy sub-step kernels (Eq. 27) and the FP64 reduction.
+//
+// k_flow (one launch per step): pull-streaming with halfway bounce-back and the
+//   open-top rules (Eqs. 1-2, Sections 3.3, 4.2) -> rho (Eq. 5) -> psi from the
+//   Peng-Robinson EOS at T^n (Eqs. 7, 28) -> F = F_m + F_ads + F_b (Eqs. 6, 9,
+//   10) -> u (Eq. 5) -> MRT collision with Li's forcing (Eqs. 2-4, 8).  It
+//   writes the post-collision populations and rho^n, u^n for the energy update.
+//   A tile is 64 columns by TY fluid rows; psi of its cells and of a one-cell
+//   ring around it goes through shared memory (the ring's populations are
+//   pulled again by this CTA, from L2).  Each thread keeps the pulled
+//   populations of its own cells in registers between the psi pass and the
+//   collision, so every population is loaded once and stored once.
+// k_energy (N launches per step): one RK4 sub-step (Eq. 18, dt = 1/N) of the
+//   energy equation (Eq. 17) with the finite-volume harmonic face
+//   conductivities of Eqs. (22)-(26), on rho^n and u^n held over the
+//   sub-steps.  A 56 x 24 tile in a 64 x 32 shared-memory frame; stage k is
+//   evaluated on ring 4 - k of the tile.
+// Both kernels write per-tile partial sums (flow: fluid mass, first-fluid-row
+// vapour count, top outlet velocity; energy: RK-weighted wall fluxes over the
+// sub-steps, sensible energy of T^{n+1}) that k_reduce_split folds into the
+// device record in FP64.
+//
+// HBM bytes per fluid cell and step: populations 36 read + 36 written, T^n 4
+// read and rho^n, u^n 12 written by the flow kernel; T 4 read + 4 written and
+// rho^n, u^n 12 read by each energy sub-step.  108 B at N = 1 against the 80 B
+// of the fused kernel, in exchange for a flow kernel without halo recompute
+// beyond one ring and an energy kernel without the flow's ring-5 halo.
+#pragma once
+#include "hlb_kernels.cuh"
+
+namespace hlb {
+
+enum { FP_MASS = 0, FP_VCOV, FP_UTOP, NFPART };
+enum { EP_QB = 0, EP_QT, EP_QI, EP_E, NEPART };
+
+constexpr int FL_TX = 64;          // flow tile width
+constexpr int FL_FW = FL_TX + 2;   // psi frame: the tile and a one-cell ring
+// Compiled flow-tile variants (fluid rows per tile, threads per CTA, CTAs per SM).
+#define HLB_FLOW_VARIANTS(X) X(16, 256, 3) X(32, 512, 1) X(8, 256, 4)
+
+constexpr int EN_TX = 56, EN_TY = 24, EN_H = 4;
+constexpr int EN_FW = EN_TX + 2 * EN_H;  // 64 frame columns, one per thread
+constexpr int EN_FH = EN_TY + 2 * EN_H;  // 32 frame rows
+constexpr int EN_NT = 256;
+constexpr int EN_NPH = EN_NT / EN_FW;    // 4 row phases
+constexpr int EN_NJ = EN_FH / EN_NPH;    // 8 frame rows per thread
+constexpr int EN_FN = EN_FW * EN_FH;
+constexpr int EN_NARR = 11;
+constexpr size_t energy_smem_bytes() { return (size_t)EN_NARR * EN_FN * sizeof(float); }
+static_assert(EN_FW == 64 && EN_NT % EN_FW == 0 && EN_FH % EN_NPH == 0, "energy frame mapping");
+
+template <int TY>
+constexpr size_t flow_smem_bytes() { return (size_t)FL_FW * (TY + 2) * sizeof(float); }
+
+// The batch kernels' per-domain descriptor applied to the shared model parameters.
+__device__ __forceinline__ void apply_dom(StepArgs& A, const DomArgs& D) {
+  A.nx = D.nx;
+  A.ny = D.ny;
+  A.W = D.W;
+  A.top_bc = D.top_bc;
+  A.eos_T_fixed = D.eos_T_fixed;
+  A.plane = D.plane;
+  A.T_bottom = D.T_bottom;
+  A.T_top = D.T_top;
+  A.f_in = D.f_in;
+  A.f_out = D.f_out;
+  A.T_in = D.T_in;
+  A.T_out = D.T_out;
+  A.Gw = D.Gw;
+  A.ftop_in = D.ftop_in;
+  A.ftop_out = D.ftop_out;
+  A.partials = D.partials;
+  A.state = D.state;
+  A.mom = D.mom;
+  A.T_scr = D.T_scr;
+  A.fpart = D.fpart;
+  A.epart = D.epart;
+}
+
+// Rows of the flow grid: the fluid rows [W, fluid_end).
+__host__ __device__ __forceinline__ int fluid_end(int ny, int top_bc) { return top_bc == 0 ? ny - 1 : ny; }
+
+// A flow tile whose frame rows [y0 - 1, y0 + TY] lie in [W + 1, ny - 3]: every
+// pull of its cells is plain streaming (no solid row within two rows, not the
+// open top row) and none of its cells is a diagnostic or outlet row.
+__device__ __forceinline__ bool flow_interior(const StepArgs& A, int y0, int TY) {
+  return y0 - 1 >= A.W + 1 && y0 + TY <= A.ny - 3;
+}
+
+// Compensated block reduction of NQ per-thread (hi, lo) pairs into FP64 slots
+// out[0..NQ) (one thread writes each; `add` adds to the stored value).
+template <int NTH, int NQ>
+__device__ __forceinline__ void block_partials(float (&ah)[NQ], float (&al)[NQ], float (*s_red)[NQ][2],
+                                               double* out, bool add) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    if (__any_sync(0xffffffffu, ah[q] != 0.f || al[q] != 0.f)) ff_warp_sum(ah[q], al[q]);
+    if (lane == 0) {
+      s_red[warp][q][0] = ah[q];
+      s_red[warp][q][1] = al[q];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    const int q = threadIdx.x;
+    float hi = s_red[0][q][0], lo = s_red[0][q][1];
+#pragma unroll
+    for (int w = 1; w < NTH / 32; ++w) ff_merge(hi, lo, s_red[w][q][0], s_red[w][q][1]);
+    const double v = (double)hi + (double)lo;
+    out[q] = add ? out[q] + v : v;
+  }
+}
+
+// ---------------------------------------------------------------- flow tile
+template <int TY, int NTH, bool INT>
+__device__ __forceinline__ void flow_tile(const StepArgs& A, int bx, int by, int part, float* sPsi, float Uc,
+                                          float rho_ave) {
+  constexpr int NPH = NTH / FL_TX;
+  constexpr int CPT = TY / NPH;  // own cells per thread: a run of CPT rows of one column
+  constexpr int NHALO = 2 * FL_FW + 2 * TY;
+  static_assert(NTH % FL_TX == 0 && TY % NPH == 0, "one thread per tile column and row run");
+  __shared__ float s_red[NTH / 32][NFPART][2];
+  __shared__ int s_err;
+
+  const Geo g = make_geo(A);
+  const int nx = A.nx, ny = A.ny, W = A.W;
+  const int fend = g.top_wall ? ny - 1 : ny;
+  const int x0 = bx * FL_TX, y0 = W + by * TY;
+  const int tid = threadIdx.x;
+  const int i = tid & (FL_TX - 1), jp = tid / FL_TX;
+  const int gxu = x0 + i;
+  const int gx = wrapx(gxu, nx);
+  const int xm = gx == 0 ? nx - 1 : gx - 1;
+  const int xp = gx == nx - 1 ? 0 : gx + 1;
+  const bool colv = gxu < nx;
+  const int P = (int)A.plane;
+  const int NC = nx * ny;
+  if (tid == 0) s_err = 0;
+  int err = 0;
+
+  // psi of a fluid node from its density and temperature (Eq. 7 with Eq. 28)
+  auto psi_of = [&](float rho, float T) -> float {
+    float p2 = pr_psi2(A, rho, A.eos_T_fixed ? A.Ts : T);
+    if (!(p2 >= 0.f)) {
+      err |= ERR_PSI_NEG;
+      p2 = 0.f;
+    }
+    return sqrtf(p2);
+  };
+  // populations of fluid node (x, y) after streaming, with the wall and top rules
+  auto pull_any = [&](int x, int y, float h[9]) {
+    const int hxm = x == 0 ? nx - 1 : x - 1, hxp = x == nx - 1 ? 0 : x + 1;
+    pull(A, g, x, hxm, hxp, y, y - 1 < W, g.top_wall && y + 1 == ny - 1, Uc, h);
+  };
+
+  // ---- pass 1: pull the tile's own cells (kept in registers), rho, psi
+  const int o1 = P + xm - gx, o3 = 3 * P + xp - gx;
+  const int o2 = 2 * P - nx, o5 = 5 * P - nx + xm - gx, o6 = 6 * P - nx + xp - gx;
+  const int o4 = 4 * P + nx, o7 = 7 * P + nx + xp - gx, o8 = 8 * P + nx + xm - gx;
+  float f[CPT][9];
+  float rho[CPT];
+#pragma unroll
+  for (int m = 0; m < CPT; ++m) {
+    const int j = jp * CPT + m;
+    const int gy = y0 + j;
+    float ps = 0.f;
+    rho[m] = 1.f;
+    if (INT || gy < fend) {
+      const int c = gy * nx + gx;
+      if (INT) {
+        const float* __restrict__ F = A.f_in + c;
+        f[m][0] = __ldg(F);
+        f[m][1] = __ldg(F + o1);
+        f[m][3] = __ldg(F + o3);
+        f[m][2] = __ldg(F + o2);
+        f[m][5] = __ldg(F + o5);
+        f[m][6] = __ldg(F + o6);
+        f[m][4] = __ldg(F + o4);
+        f[m][7] = __ldg(F + o7);
+        f[m][8] = __ldg(F + o8);
+      } else {
+        pull(A, g, gx, xm, xp, gy, gy == W, g.top_wall && gy + 1 == ny - 1, Uc, f[m]);
+      }
+      rho[m] = A.rho_ref + sum9(f[m]);
+      ps = psi_of(rho[m], __ldg(A.T_in + c));
+    } else if (g.top_open && gy == ny) {
+      // zero-gradient ghost above an open top: psi of row ny - 1
+      float h[9];
+      pull_any(gx, ny - 1, h);
+      ps = psi_of(A.rho_ref + sum9(h), __ldg(A.T_in + (ny - 1) * nx + gx));
+    }
+    sPsi[(j + 1) * FL_FW + i + 1] = ps;
+  }
+  // ---- the ring: rows y0 - 1 and y0 + TY (all 66 frame columns), columns
+  // x0 - 1 and x0 + 64 (the tile's rows); solid rows carry no psi
+  for (int t = tid; t < NHALO; t += NTH) {
+    int j, ii;
+    if (t < 2 * FL_FW) {
+      j = t < FL_FW ? -1 : TY;
+      ii = (t < FL_FW ? t : t - FL_FW) - 1;
+    } else {
+      const int s = t - 2 * FL_FW;
+      ii = s < TY ? -1 : FL_TX;
+      j = s < TY ? s : s - TY;
+    }
+    int gy = y0 + j;
+    if (g.top_open && gy == ny) gy = ny - 1;  // zero-gradient ghost
+    float ps = 0.f;
+    if (gy >= W && gy < fend) {
+      const int hx = wrapx(x0 + ii, nx);
+      float h[9];
+      pull_any(hx, gy, h);
+      ps = psi_of(A.rho_ref + sum9(h), __ldg(A.T_in + gy * nx + hx));
+    }
+    sPsi[(j + 1) * FL_FW + ii + 1] = ps;
+  }
+  __syncthreads();
+
+  // ---- pass 2: forces, velocity, collision of the own cells
+  float ah[NFPART], al[NFPART];
+#pragma unroll
+  for (int q = 0; q < NFPART; ++q) ah[q] = al[q] = 0.f;
+  const float gw = __ldg(A.Gw + gx);
+#pragma unroll
+  for (int m = 0; m < CPT; ++m) {
+    const int j = jp * CPT + m;
+    const int gy = y0 + j;
+    if (!colv || !(INT || gy < fend)) continue;
+    const int idx = (j + 1) * FL_FW + i + 1;
+    const float psi = sPsi[idx];
+    const float r = rho[m];
+    const bool sol_s = !INT && gy == W;
+    const bool sol_n = !INT && g.top_wall && gy == ny - 2;
+    // Eq. (6); a solid neighbour carries psi(x)
+    const float pE = sPsi[idx + 1], pW = sPsi[idx - 1];
+    const float pN = sol_n ? psi : sPsi[idx + FL_FW];
+    const float pS = sol_s ? psi : sPsi[idx - FL_FW];
+    const float pNE = sol_n ? psi : sPsi[idx + FL_FW + 1];
+    const float pNW = sol_n ? psi : sPsi[idx + FL_FW - 1];
+    const float pSE = sol_s ? psi : sPsi[idx - FL_FW + 1];
+    const float pSW = sol_s ? psi : sPsi[idx - FL_FW - 1];
+    const float sx = (pE - pW) * (1.f / 3.f) + ((pNE - pNW) + (pSE - pSW)) * (1.f / 12.f);
+    const float sy = (pN - pS) * (1.f / 3.f) + ((pNE + pNW) - (pSE + pSW)) * (1.f / 12.f);
+    const float Fmx = -A.G * psi * sx;
+    const float Fmy = -A.G * psi * sy;
+    // Eq. (10) with weights omega/3: only a normal component next to a solid row
+    const float Fay = INT ? 0.f : gw * psi * psi * ((float)sol_n - (float)sol_s) * (1.f / 6.f);
+    const float Fx = Fmx;
+    const float Fy = Fmy + Fay + (r - rho_ave) * A.g_y;  // Eq. (9)
+    const float* fm = f[m];
+    const float jx = (fm[1] - fm[3]) + ((fm[5] - fm[6]) - (fm[7] - fm[8]));
+    const float jy = (fm[2] - fm[4]) + ((fm[5] + fm[6]) - (fm[7] + fm[8]));
+    const float irho = 1.f / r;
+    const float ux = (jx + 0.5f * Fx) * irho;
+    const float uy = (jy + 0.5f * Fy) * irho;
+    const int c = gy * nx + gx;
+    const float fsum = collide_store(A, fm, r, ux, uy, Fx, Fy, A.G * A.G * (sx * sx + sy * sy), c);
+    if (nonfinite(fsum)) err |= ERR_NONFINITE;
+    A.mom[c] = r;
+    A.mom[NC + c] = ux;
+    A.mom[2 * NC + c] = uy;
+    ff_add(ah[FP_MASS], al[FP_MASS], r);
+    if (!INT) {
+      if (gy == W && r < A.rho_mid) ff_add(ah[FP_VCOV], al[FP_VCOV], 1.f);
+      if (gy == ny - 2) ff_add(ah[FP_UTOP], al[FP_UTOP], uy);
+      if (A.top_bc == TOP_CONVECTIVE && gy == ny - 1) {
+        A.ftop_out[gx] = fm[4];
+        A.ftop_out[nx + gx] = fm[7];
+        A.ftop_out[2 * nx + gx] = fm[8];
+      }
+    }
+  }
+  if (err) atomicOr(&s_err, err);
+  block_partials<NTH, NFPART>(ah, al, s_red, A.fpart + (long long)part * NFPART, false);
+  if (tid == 0 && s_err) atomicOr(&A.state->error_flags, s_err);
+}
+
+template <int TY, int NTH, int MINB>
+__global__ void __launch_bounds__(NTH, MINB) k_flow(const StepArgs A) {
+  extern __shared__ float sm[];
+  const float Uc = (float)A.state->Uc, rho_ave = (float)A.state->rho_ave;
+  const int part = blockIdx.y * gridDim.x + blockIdx.x;
+  const int y0 = A.W + blockIdx.y * TY;
+  if (flow_interior(A, y0, TY))
+    flow_tile<TY, NTH, true>(A, blockIdx.x, blockIdx.y, part, sm, Uc, rho_ave);
+  else
+    flow_tile<TY, NTH, false>(A, blockIdx.x, blockIdx.y, part, sm, Uc, rho_ave);
+}
+
+// Loads the domain descriptor of block `b` into shared memory; returns false
+// for a stopped domain.
+template <int NTH>
+__device__ __forceinline__ bool batch_prologue(const DomArgs* __restrict__ desc, const int2* __restrict__ blk,
+                                               const int* __restrict__ active, const float2* __restrict__ lag,
+                                               DomArgs& sD, int2& s_bl, float2& s_lg, int& s_act) {
+  const int2 bl = blk[blockIdx.x];
+  const int* src = reinterpret_cast<const int*>(desc + bl.x);
+  int* dst = reinterpret_cast<int*>(&sD);
+  for (int q = threadIdx.x; q < (int)(sizeof(DomArgs) / sizeof(int)); q += NTH) dst[q] = src[q];
+  if (threadIdx.x == NTH - 1) {
+    s_bl = bl;
+    s_act = active[bl.x];
+    s_lg = lag ? lag[bl.x] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  return s_act != 0;
+}
+
+// Batched flow step: block b takes tile blk[b].y of domain blk[b].x.
+template <int TY, int NTH, int MINB>
+__global__ void __launch_bounds__(NTH, MINB) k_flow_batch(const StepArgs P, const DomArgs* __restrict__ desc,
+                                                          const int2* __restrict__ blk,
+                                                          const int* __restrict__ active,
+                                                          const float2* __restrict__ lag) {
+  extern __shared__ float sm[];
+  __shared__ DomArgs sD;
+  __shared__ int s_act;
+  __shared__ int2 s_bl;
+  __shared__ float2 s_lg;
+  if (!batch_prologue<NTH>(desc, blk, active, lag, sD, s_bl, s_lg, s_act)) return;
+  StepArgs A = P;
+  apply_dom(A, sD);
+  const int local = s_bl.y;
+  const int tx = (A.nx + FL_TX - 1) / FL_TX;
+  const int by = local / tx;
+  if (flow_interior(A, A.W + by * TY, TY))
+    flow_tile<TY, NTH, true>(A, local % tx, by, local, sm, s_lg.x, s_lg.y);
+  else
+    flow_tile<TY, NTH, false>(A, local % tx, by, local, sm, s_lg.x, s_lg.y);
+}
+
+// -------------------------------------------------------------- energy tile
+// An energy tile whose frame rows [y0 - 4, y0 + 28) lie in [W, ny - 2]: no
+// solid, Dirichlet, ghost or wall-flux row in the frame.
+__device__ __forceinline__ bool energy_interior(const StepArgs& A, int y0) {
+  return y0 - EN_H >= A.W && y0 + EN_TY + EN_H <= A.ny - 1;
+}
+
+// Temperature buffers of sub-step s of N: X_0 = T^n (T_in), X_N = T^{n+1}
+// (T_out); the others alternate with the scratch plane so that X_N lands in T_out.
+__device__ __forceinline__ float* substep_buffer(const StepArgs& A, int s, int nsub) {
+  return ((nsub - s) & 1) ? A.T_scr : A.T_out;
+}
+
+template <bool INT>
+__device__ __forceinline__ void energy_tile(const StepArgs& A, int bx, int by, int part, float* sm, int s, int nsub) {
+  float* const sT0 = sm;
+  float* const sTa = sm + EN_FN;
+  float* const sTb = sm + 2 * EN_FN;
+  float* const sRho = sm + 3 * EN_FN;
+  float* const sUx = sm + 4 * EN_FN;
+  float* const sUy = sm + 5 * EN_FN;
+  float* const sLae = sm + 6 * EN_FN;  // east-face conductivity (Eq. 25)
+  float* const sLan = sm + 7 * EN_FN;  // north-face conductivity
+  float* const sIrcv = sm + 8 * EN_FN;
+  float* const sAs = sm + 9 * EN_FN;   // latent-heat source coefficients
+  float* const sBs = sm + 10 * EN_FN;
+  __shared__ float s_red[EN_NT / 32][NEPART][2];
+  __shared__ int s_err;
+
+  const float* __restrict__ T_in = s == 1 ? A.T_in : substep_buffer(A, s - 1, nsub);
+  float* __restrict__ T_out = substep_buffer(A, s, nsub);
+  const bool last = s == nsub;
+  const Geo g = make_geo(A);
+  const int nx = A.nx, ny = A.ny;
+  const int NC = nx * ny;
+  const float* __restrict__ rho_n = A.mom;
+  const float* __restrict__ ux_n = A.mom + NC;
+  const float* __restrict__ uy_n = A.mom + 2 * NC;
+  const int x0 = bx * EN_TX, y0 = by * EN_TY;
+  const int tid = threadIdx.x;
+  const int i = tid % EN_FW, jp = tid / EN_FW;
+  const int gxu = x0 - EN_H + i;
+  const int gx = wrapx(gxu, nx);
+  const bool own_col = i >= EN_H && i < EN_H + EN_TX && gxu < nx;
+  const float lam_w = A.lambda_w, cvk = A.cvk;
+  auto wall_lam = [&](int row) -> float { return g.top_wall && row == ny - 1 ? A.lambda_top : lam_w; };
+  if (tid == 0) s_err = 0;
+  int err = 0;
+
+  // ---- T (the wall value on Dirichlet rows), rho^n and u^n; frame rows above
+  // the lattice copy row ny - 1 (the zero-gradient ghost of an open top), rows
+  // below it are never read
+#pragma unroll
+  for (int m = 0; m < EN_NJ; ++m) {
+    const int j = jp + EN_NPH * m;
+    const int gy = y0 - EN_H + j;
+    const int idx = j * EN_FW + i;
+    if (!INT && gy < 0) {
+      sT0[idx] = sRho[idx] = sUx[idx] = sUy[idx] = 0.f;
+      continue;
+    }
+    const int gr = INT || gy < ny ? gy : ny - 1;
+    const int c = gr * nx + gx;
+    const bool solid = !INT && g.solid_row(gr);
+    sT0[idx] = !INT && g.dirichlet_row(gr) ? (gr == 0 ? A.T_bottom : A.T_top) : __ldg(T_in + c);
+    sRho[idx] = solid ? 0.f : __ldg(rho_n + c);
+    sUx[idx] = solid ? 0.f : __ldg(ux_n + c);
+    sUy[idx] = solid ? 0.f : __ldg(uy_n + c);
+  }
+  __syncthreads();
+
+  // ---- face conductivities on the whole frame; the other coefficients on
+  // ring 3 (rows and columns 1 .. 62)
+#pragma unroll
+  for (int m = 0; m < EN_NJ; ++m) {
+    const int j = jp + EN_NPH * m;
+    const int gy = y0 - EN_H + j;
+    if (!INT && gy < 0) continue;
+    const int idx = j * EN_FW + i;
+    const int gr = INT || gy < ny ? gy : ny - 1;
+    const bool solid = !INT && g.solid_row(gr);
+    const float lam = solid ? wall_lam(gr) : sRho[idx] * cvk;
+    if (i + 1 < EN_FW) {
+      const float le = solid ? wall_lam(gr) : sRho[idx + 1] * cvk;
+      sLae[idx] = 2.f * lam * le / (lam + le);
+    }
+    if (j + 1 < EN_FH) {
+      const int gn = INT || gy + 1 < ny ? gy + 1 : ny - 1;
+      const float ln = !INT && g.solid_row(gn) ? wall_lam(gn) : sRho[idx + EN_FW] * cvk;
+      sLan[idx] = 2.f * lam * ln / (lam + ln);
+    }
+    if (j < 1 || j >= EN_FH - 1 || i < 1 || i >= EN_FW - 1 || (!INT && gy >= ny)) continue;
+    if (solid) {
+      sIrcv[idx] = A.inv_rcv_w;
+      sAs[idx] = 0.f;
+      sBs[idx] = 0.f;
+      continue;
+    }
+    const int js = j - 1, jn = j + 1;
+    const float rho = sRho[idx];
+    const float ircv = 1.f / (rho * A.cv);
+    // div u with the isotropic gradient of Eq. (19)
+    const float dux = (sUx[idx + 1] - sUx[idx - 1]) * (1.f / 3.f) +
+                      ((sUx[jn * EN_FW + i + 1] - sUx[js * EN_FW + i - 1]) +
+                       (sUx[js * EN_FW + i + 1] - sUx[jn * EN_FW + i - 1])) *
+                          (1.f / 12.f);
+    const float duy = (sUy[jn * EN_FW + i] - sUy[js * EN_FW + i]) * (1.f / 3.f) +
+                      ((sUy[jn * EN_FW + i + 1] - sUy[js * EN_FW + i - 1]) +
+                       (sUy[jn * EN_FW + i - 1] - sUy[js * EN_FW + i + 1])) *
+                          (1.f / 12.f);
+    const float divu = dux + duy;
+    const float br = A.b * rho;
+    // T (dp/dT)_rho = As' T + Bs' (1 + kappa (1 - sqrt Tr)) sqrt Tr (Eq. 28)
+    const float Ar = rho * A.R / (1.f - br);
+    const float Br = A.a * rho * rho * A.kappa / (1.f + 2.f * br - br * br);
+    sIrcv[idx] = ircv;
+    sAs[idx] = Ar * ircv * divu;
+    sBs[idx] = Br * ircv * divu;
+  }
+  __syncthreads();
+
+  // ---- RK4 stages (Eq. 18): stage k on ring 4 - k
+  const int jtop = ny - 1 - y0 + EN_H;  // frame row of the lattice's top row
+  const bool has_ghost = !INT && jtop < EN_FH - 1;
+  const float dt = A.dt;
+  float acc[EN_NJ];
+  float ah[NEPART], al[NEPART];
+#pragma unroll
+  for (int q = 0; q < NEPART; ++q) ah[q] = al[q] = 0.f;
+#pragma unroll
+  for (int m = 0; m < EN_NJ; ++m) acc[m] = 0.f;
+#pragma unroll
+  for (int k = 1; k <= 4; ++k) {
+    const float* Tc = k == 1 ? sT0 : (k == 3 ? sTb : sTa);
+    float* Tn = k == 1 ? sTa : (k == 2 ? sTb : sTa);
+    const float cnext = k == 3 ? dt : 0.5f * dt;
+    const float wk = (k == 1 || k == 4) ? dt * (1.f / 6.f) : dt * (2.f / 6.f);
+    const float wacc = (k == 1) ? 1.f : 2.f;
+    const int r = 4 - k;
+#pragma unroll
+    for (int m = 0; m < EN_NJ; ++m) {
+      const int j = jp + EN_NPH * m;
+      const int gy = y0 - EN_H + j;
+      // rows outside ring r are skipped (warp-uniform); every column of a row
+      // is evaluated (columns outside the ring are never read later)
+      if (j < EN_H - r || j >= EN_H + EN_TY + r || (!INT && (gy < 0 || gy >= ny))) continue;
+      const bool own = own_col && j >= EN_H && j < EN_H + EN_TY;
+      const int idx = j * EN_FW + i;
+      const int js = j - 1, jn = j + 1;
+      const float Tp = Tc[idx];
+      float hk = 0.f;
+      // row 0 under an imposed flux (Section 3.3): q_in enters through its bottom face
+      const bool bot = !INT && gy == 0;
+      if (INT || !g.dirichlet_row(gy)) {
+        const float TE = Tc[idx + 1], TW = Tc[idx - 1], TN = Tc[jn * EN_FW + i], TS = Tc[js * EN_FW + i];
+        // Eqs. (22)-(26): the sum of the face fluxes of the control volume
+        float kk = sLae[idx] * (TE - Tp);
+        kk = fmaf(sLae[idx - 1], TW - Tp, kk);
+        kk = fmaf(sLan[idx], TN - Tp, kk);
+        kk = bot ? kk + A.q_in : fmaf(sLan[js * EN_FW + i], TS - Tp, kk);
+        kk *= sIrcv[idx];
+        if (INT || !g.solid_row(gy)) {
+          const float TNE = Tc[jn * EN_FW + i + 1], TNW = Tc[jn * EN_FW + i - 1];
+          const float TSE = Tc[js * EN_FW + i + 1], TSW = Tc[js * EN_FW + i - 1];
+          const float gxT = (TE - TW) * (1.f / 3.f) + ((TNE - TSW) + (TSE - TNW)) * (1.f / 12.f);
+          const float gyT = (TN - TS) * (1.f / 3.f) + ((TNE - TSW) + (TNW - TSE)) * (1.f / 12.f);
+          kk -= sUx[idx] * gxT + sUy[idx] * gyT;
+          const float sTr = sqrtf(fmaxf(Tp, 0.f) * A.invTc);
+          kk -= sAs[idx] * Tp + sBs[idx] * (1.f + A.kappa * (1.f - sTr)) * sTr;
+        }
+        hk = kk;
+      }
+      if (k < 4) acc[m] += wacc * hk;
+      if (own) {
+        if (!INT) {
+          if (gy == 1) ff_add(ah[EP_QB], al[EP_QB], wk * sLan[js * EN_FW + i] * (Tc[js * EN_FW + i] - Tp));
+          if (g.top_wall && gy == ny - 2) ff_add(ah[EP_QT], al[EP_QT], wk * sLan[idx] * (Tp - Tc[jn * EN_FW + i]));
+          if (gy == A.W) ff_add(ah[EP_QI], al[EP_QI], wk * sLan[js * EN_FW + i] * (Tc[js * EN_FW + i] - Tp));
+        }
+        if (k == 4) {
+          const float Tnew = sT0[idx] + dt * (1.f / 6.f) * (acc[m] + hk);
+          if (nonfinite(Tnew)) err |= ERR_NONFINITE;
+          T_out[gy * nx + gx] = Tnew;
+          if (last) ff_add(ah[EP_E], al[EP_E], Tnew / sIrcv[idx]);
+        }
+      }
+      if (k < 4) Tn[idx] = sT0[idx] + cnext * hk;
+    }
+    __syncthreads();
+    if (k < 4 && has_ghost) {
+      for (int jj = jtop + 1 + jp; jj < EN_FH; jj += EN_NPH) Tn[jj * EN_FW + i] = Tn[jtop * EN_FW + i];
+      __syncthreads();
+    }
+  }
+  if (err) atomicOr(&s_err, err);
+  // fluxes add up over the sub-steps; the energy of T^{n+1} comes from the last
+  block_partials<EN_NT, NEPART>(ah, al, s_red, A.epart + (long long)part * NEPART, s > 1);
+  if (tid == 0 && s_err) atomicOr(&A.state->error_flags, s_err);
+}
+
+__global__ void __launch_bounds__(EN_NT, 2) k_energy(const StepArgs A, int s, int nsub) {
+  extern __shared__ float sm[];
+  const int part = blockIdx.y * gridDim.x + blockIdx.x;
+  if (energy_interior(A, blockIdx.y * EN_TY))
+    energy_tile<true>(A, blockIdx.x, blockIdx.y, part, sm, s, nsub);
+  else
+    energy_tile<false>(A, blockIdx.x, blockIdx.y, part, sm, s, nsub);
+}
+
+__global__ void __launch_bounds__(EN_NT, 2) k_energy_batch(const StepArgs P, const DomArgs* __restrict__ desc,
+                                                           const int2* __restrict__ blk,
+                                                           const int* __restrict__ active, int s, int nsub) {
+  extern __shared__ float sm[];
+  __shared__ DomArgs sD;
+  __shared__ int s_act;
+  __shared__ int2 s_bl;
+  __shared__ float2 s_lg;
+  if (!batch_prologue<EN_NT>(desc, blk, active, nullptr, sD, s_bl, s_lg, s_act)) return;
+  StepArgs A = P;
+  apply_dom(A, sD);
+  const int local = s_bl.y;
+  const int tx = (A.nx + EN_TX - 1) / EN_TX;
+  const int by = local / tx;
+  if (energy_interior(A, by * EN_TY))
+    energy_tile<true>(A, local % tx, by, local, sm, s, nsub);
+  else
+    energy_tile<false>(A, local % tx, by, local, sm, s, nsub);
+}
+
+// ------------------------------------------------------------- reduction
+// Sums the flow and energy tiles' partials of one domain (one CTA) and updates
+// the record: lagged mean density (Eq. 9) and outlet velocity for the next
+// step, diagnostics, running sums, flux history.
+__device__ __forceinline__ void reduce_split_block(const double* __restrict__ fpart, int nf,
+                                                   const double* __restrict__ epart, int ne, DevState* st,
+                                                   double inv_nfluid, double inv_nx, double* hist, int hist_cap,
+                                                   float2* lag) {
+  __shared__ double s_red[8][NFPART + NEPART];
+  double v[NFPART + NEPART];
+#pragma unroll
+  for (int q = 0; q < NFPART + NEPART; ++q) v[q] = 0.0;
+  for (int b = threadIdx.x; b < nf; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < NFPART; ++q) v[q] += fpart[(long long)b * NFPART + q];
+  }
+  for (int b = threadIdx.x; b < ne; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < NEPART; ++q) v[NFPART + q] += epart[(long long)b * NEPART + q];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NFPART + NEPART; ++q) {
+    const double s = warp_sum(v[q]);
+    if (lane == 0) s_red[warp][q] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s[NFPART + NEPART];
+#pragma unroll
+    for (int q = 0; q < NFPART + NEPART; ++q) {
+      s[q] = 0.0;
+      for (int w = 0; w < 8; ++w) s[q] += s_red[w][q];
+    }
+    st->rho_ave_prev = st->rho_ave;
+    st->rho_ave = s[FP_MASS] * inv_nfluid;
+    const double ut = s[FP_UTOP] * inv_nx;
+    st->u_top = ut;
+    st->U = ut > 0.0 ? ut : 0.0;
+    st->Uc = st->U / (1.0 + st->U);
+    st->step += 1;
+    st->mass = s[FP_MASS];
+    st->energy = s[NFPART + EP_E];
+    st->q_bottom = s[NFPART + EP_QB] * inv_nx;
+    st->q_top = s[NFPART + EP_QT] * inv_nx;
+    st->q_interface = s[NFPART + EP_QI] * inv_nx;
+    st->q_sum += st->q_bottom;
+    st->q_count += 1;
+    st->vcov = s[FP_VCOV] * inv_nx;
+    st->vcov_sum += st->vcov;
+    if (hist && st->hist_len < hist_cap) hist[st->hist_len++] = st->q_bottom;
+    if (lag) *lag = make_float2((float)st->Uc, (float)st->rho_ave);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_reduce_split(const double* __restrict__ fpart, int nf,
+                                                       const double* __restrict__ epart, int ne, DevState* st,
+                                                       double inv_nfluid, double inv_nx, double* hist, int hist_cap) {
+  reduce_split_block(fpart, nf, epart, ne, st, inv_nfluid, inv_nx, hist, hist_cap, nullptr);
+}
+
+struct SplitReduceArgs {
+  const double* fpart;
+  const double* epart;
+  DevState* state;
+  double* hist;
+  int nf, ne;
+  double inv_nfluid, inv_nx;
+};
+
+__global__ void __launch_bounds__(256) k_reduce_split_batch(const SplitReduceArgs* __restrict__ ra,
+                                                             const int* __restrict__ active, float2* lag,
+                                                             int hist_cap) {
+  const int d = blockIdx.x;
+  if (!active[d]) return;
+  const SplitReduceArgs r = ra[d];
+  reduce_split_block(r.fpart, r.nf, r.epart, r.ne, r.state, r.inv_nfluid, r.inv_nx, r.hist, hist_cap, lag + d);
+}
+
+}  // namespace hlb

@@ -19,6 +19,7 @@ HLB_TOP_WALL, HLB_TOP_CONST_RHO, HLB_TOP_CONVECTIVE = 0, 1, 2
 HLB_STORE_DEVIATION, HLB_STORE_PLAIN = 0, 1
 HLB_DIFF_FV, HLB_DIFF_ISO = 0, 1
 HLB_BOTTOM_DIRICHLET, HLB_BOTTOM_FLUX = 0, 1
+HLB_KIND_SPLIT, HLB_KIND_FUSED, HLB_KIND_MARCH = 0, 1, 2
 TOP_KIND = {"wall": HLB_TOP_WALL, "const_rho": HLB_TOP_CONST_RHO, "convective": HLB_TOP_CONVECTIVE}
 
 
@@ -81,12 +82,14 @@ def lib() -> C.CDLL:
             "hlb_batch_set_nucleation_sites": (st, [vp, C.c_int, C.c_int, P(hlb_site)]),
             "hlb_batch_step": (st, [vp, C.c_int]),
             "hlb_batch_step_profiled": (st, [vp, vp, vp]),
+            "hlb_batch_step_phases": (st, [vp, vp, vp, vp]),
             "hlb_batch_read": (st, [vp, C.c_int, vp, vp, vp, vp]),
             "hlb_batch_diag": (st, [vp, C.c_int, P(hlb_diag_record)]),
             "hlb_batch_flux_history": (st, [vp, C.c_int, P(C.c_double), C.c_int, P(C.c_int)]),
             "hlb_batch_stop": (st, [vp, C.c_int]),
             "hlb_batch_destroy": (st, [vp]),
             "hlb_tile_variants": (C.c_int, [P(C.c_int), P(C.c_int), P(C.c_int), C.c_int]),
+            "hlb_variant_kind": (C.c_int, [C.c_int]),
             "hlb_autotune": (st, [vp, C.c_int, P(C.c_int), P(C.c_float), C.c_int]),
             "hlb_batch_autotune": (st, [vp, C.c_int, P(C.c_int), P(C.c_float), C.c_int]),
             "hlb_set_tile_variant": (st, [vp, C.c_int]),
@@ -196,6 +199,12 @@ def tile_variants():
     w, h, t = (C.c_int * n)(), (C.c_int * n)(), (C.c_int * n)()
     lib().hlb_tile_variants(w, h, t, n)
     return [(w[k], h[k], t[k]) for k in range(n)]
+
+
+def variant_kinds():
+    """HLB_KIND_* of every compiled variant, in the order of tile_variants()."""
+    n = lib().hlb_tile_variants(None, None, None, 0)
+    return [int(lib().hlb_variant_kind(k)) for k in range(n)]
 
 
 def _autotune(fn, handle, steps, stream):
@@ -382,6 +391,13 @@ class Batch:
         (on the batch stream); no stream hand-off, for timing loops."""
         check("hlb_batch_step_profiled",
               lib().hlb_batch_step_profiled(self._h, _event_handle(ev_before), _event_handle(ev_after)))
+
+    def step_phases(self, ev_before, ev_flow, ev_after):
+        """One step with events before the step kernels, between the flow and
+        the energy kernels of a split step, and after the step kernels."""
+        check("hlb_batch_step_phases",
+              lib().hlb_batch_step_phases(self._h, _event_handle(ev_before), _event_handle(ev_flow),
+                                          _event_handle(ev_after)))
 
     def read(self, i):
         import torch

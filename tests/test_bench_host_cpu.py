@@ -10,10 +10,15 @@ import bench
 def test_kernel_name_and_launch_count():
     assert bench.kernel_name((52, 28, 512)) == "k_step_batch"
     assert bench.kernel_name((0, 48, 0)) == "k_march_batch"
+    assert bench.kernel_name((64, 16, 256), bench.KIND_SPLIT) == "k_flow_batch+k_energy_batch"
+    assert bench.profile_name((64, 16, 256), bench.KIND_SPLIT) == "k_flow_energy_batch"
     cases = [SimpleNamespace(nx=n) for n in (256, 320, 300, 512, 500)]
     assert bench.step_launches(cases, (52, 20, 512)) == 1
     # row strides 256, 320 (300 rounds up to 320), 512 (500 too)
-    assert bench.step_launches(cases, (0, 32, 0)) == 3
+    assert bench.step_launches(cases, (0, 32, 0), bench.KIND_MARCH) == 3
+    # a flow launch and one energy launch per sub-step of Eq. (27)
+    assert bench.step_launches(cases, (64, 16, 256), bench.KIND_SPLIT) == 2
+    assert bench.step_launches(cases, (64, 16, 256), bench.KIND_SPLIT, nsub=3) == 4
 
 
 def _profile(root, h, lines):
