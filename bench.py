@@ -266,9 +266,11 @@ print(json.dumps(out))
     return 0
 
 
-def build_sweep(hlb, wl, params_for, coex_lib):
+def build_sweep(hlb, wl, params_for, coex_lib, n_domains=None):
     import torch
     cases = wl.sweep()
+    if n_domains:
+        cases = cases[:n_domains]
     plist, fields, n_fluid, n_solid = [], [], 0, 0
     for c in cases:
         p, Tc = params_for(c)
@@ -298,7 +300,7 @@ def run_ours(args):
     from paper_1812_10375_gb300 import hlb, workloads as wl
     from paper_1812_10375_gb300.config import params_for
 
-    cases, plist, fields, n_fluid, n_solid = build_sweep(hlb, wl, params_for, None)
+    cases, plist, fields, n_fluid, n_solid = build_sweep(hlb, wl, params_for, None, args.domains)
     cells = n_fluid + n_solid
     bytes_per_step = BYTES_FLUID * n_fluid + BYTES_SOLID * n_solid
 
@@ -374,10 +376,11 @@ def run_ours(args):
                    "k_energy_batch": {"ms": en_ms, "bytes_per_launch": eb, "gbs": eb / (en_ms * 1e-3) / 1e9}}
     diag0 = batch.diag(0, check_flags=False)
 
-    # end to end through the public API with host buffers
-    e2e = run_e2e(args, hlb, plist, fields, cases, cells, dist)
-    probe = probe_2048(hlb, wl, params_for, peak_gbs()) if rank == 0 else None
-    pph = points_per_hour(hlb, plist, fields, cases) if rank == 0 else None
+    # end to end through the public API with host buffers (skipped by --quick,
+    # which profiler runs use)
+    e2e = None if args.quick else run_e2e(args, hlb, plist, fields, cases, cells, dist)
+    probe = probe_2048(hlb, wl, params_for, peak_gbs()) if rank == 0 and not args.quick else None
+    pph = points_per_hour(hlb, plist, fields, cases) if rank == 0 and not args.quick else None
 
     peak, peak_src = peak_gbs()
     achieved = bytes_per_step / (kern_avg_ms * 1e-3) / 1e9
@@ -388,7 +391,8 @@ def run_ours(args):
 
     line = None
     if rank == 0:
-        cpu = oracle_cpu_rate(seconds=12.0, domain_index=0)
+        cpu = (oracle_cpu_rate(seconds=12.0, domain_index=0) if not args.quick else
+               {"mlups": None, "nx": None, "ny": None, "steps": 0, "seconds": 0.0})
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -572,6 +576,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--tile-variant", type=int, default=None,
                     help="index into the compiled tile variants; default: autotune during warm-up")
+    ap.add_argument("--domains", type=int, default=None,
+                    help="run only the first N domains of the sweep (profiling on a smaller case)")
+    ap.add_argument("--quick", action="store_true",
+                    help="skip the end-to-end leg, the 2048 probe, points/hour and the CPU baseline")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

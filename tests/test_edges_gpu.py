@@ -55,6 +55,8 @@ def _errors(gd, od):
     fl = od.fluid
     assert np.isfinite(rho_o).all() and np.isfinite(T_o).all()
     du = max(np.abs(ux_g - ux_o)[fl].max(), np.abs(uy_g - uy_o)[fl].max())
+    umax = float(np.sqrt(ux_o ** 2 + uy_o ** 2)[fl].max())
+    print(f"  u relative to max|u| {du / umax:.2e} (max|u| {umax:.2e})")
     return dict(rho=rel_linf(rho_g, rho_o, fl), u=float(du / CS), T=rel_linf(T_g, T_o))
 
 

@@ -2,11 +2,13 @@
 the same seeded inputs, through the C ABI.
 
 Tolerance: relative L-infinity error 1e-5.  rho and T are relative to the
-field's maximum.  u is relative to the lattice sound speed c_s = 1/sqrt(3) (the
-Mach-number scale): FP32 populations of order 0.7 resolve the momentum only to
-about 1e-7 absolute, so an error relative to max|u| (printed as u_rel_max) can
-exceed 1e-5 where the flow is nearly at rest.  Solid nodes are excluded from
-rho and u."""
+field's maximum.  u is bounded twice: by 1e-5 of the lattice sound speed
+c_s = 1/sqrt(3) (the Mach-number scale), and by U_REL_TOL = 1e-4 of max|u|.
+The second bound is not 1e-5 because the FP32-stored state alone moves u by
+2.5e-5 to 3e-5 of max|u| over these runs (tests/test_fp32_floor_cpu.py
+rounds the FP64 oracle's carried state to FP32 every step and measures it);
+1e-4 leaves room for the FP32 arithmetic of the step on top of that floor.
+Solid nodes are excluded from rho and u."""
 import numpy as np
 import pytest
 
@@ -16,6 +18,7 @@ from helpers import coexistence, gpu_domain, oracle_domain, ragged_case, rel_lin
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
+U_REL_TOL = 1e-4
 CS = 1.0 / np.sqrt(3.0)
 
 
@@ -49,7 +52,9 @@ def compare(case, coex, steps, storage=0, tol=TOL, chunks=1):
         u=float(du / CS),
         T=rel_linf(T_g, T_o),
     )
-    print(f"{case.name}: u_rel_max {du / umag_o[fl].max():.2e} (max|u| {umag_o[fl].max():.2e})")
+    u_rel = float(du / umag_o[fl].max())
+    print(f"{case.name}: u_rel_max {u_rel:.2e} (max|u| {umag_o[fl].max():.2e})")
+    assert u_rel <= U_REL_TOL, (case.name, u_rel)
     dg, do = gd.diag(), od.diag()
     return err, dg, do, gd, od
 
