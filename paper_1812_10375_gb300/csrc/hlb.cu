@@ -567,6 +567,7 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
   a.iso = q.diffusion == HLB_DIFF_ISO ? 1 : 0;
   a.kd = (float)q.k;
   a.kd_w = (float)(q.lambda_w / (q.rho_w * q.cv_w));
+  a.inv_k = (float)(1.0 / q.k);
   a.T_bottom = (float)q.T_bottom;
   a.T_top = (float)q.T_top;
   a.Gw = d->Gw;

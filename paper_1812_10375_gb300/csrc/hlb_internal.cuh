@@ -48,6 +48,7 @@ struct StepArgs {
   float q_in;
   int iso;          // isotropic central diffusion (Eqs. 20-21) instead of the finite-volume faces
   float kd, kd_w;   // lambda / (rho cv) of the fluid (k) and of the solid
+  float inv_k;      // 1 / k: rho cv of a fluid cell from its lambda
   float T_bottom, T_top;
   // buffers
   const float* __restrict__ f_in;

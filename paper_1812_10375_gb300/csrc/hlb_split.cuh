@@ -15,8 +15,13 @@
 // k_energy (N launches per step): one RK4 sub-step (Eq. 18, dt = 1/N) of the
 //   energy equation (Eq. 17) with the finite-volume harmonic face
 //   conductivities of Eqs. (22)-(26), on rho^n and u^n held over the
-//   sub-steps.  A 56 x 24 tile in a 64 x 32 shared-memory frame; stage k is
-//   evaluated on ring 4 - k of the tile.
+//   sub-steps.  A 56 x 24 tile in a 64 x 32 frame; stage k is evaluated on
+//   ring 4 - k of the tile.  Each thread owns a run of 8 rows of one frame
+//   column: the per-cell coefficients of Eq. (17) (four face terms with the
+//   axis part of the advection folded in, two diagonal advection terms, the
+//   two latent-heat coefficients, rho cv) and the run's stage values stay in
+//   registers; shared memory carries only what neighbouring threads read (the
+//   stage values, u and lambda).
 // Both kernels write per-tile partial sums (flow: fluid mass, first-fluid-row
 // vapour count, top outlet velocity; energy: RK-weighted wall fluxes over the
 // sub-steps, sensible energy of T^{n+1}) that k_reduce_split folds into the
@@ -47,7 +52,8 @@ constexpr int EN_NT = 256;
 constexpr int EN_NPH = EN_NT / EN_FW;    // 4 row phases
 constexpr int EN_NJ = EN_FH / EN_NPH;    // 8 frame rows per thread
 constexpr int EN_FN = EN_FW * EN_FH;
-constexpr int EN_NARR = 11;
+constexpr int EN_R = EN_NJ;              // rows of a thread's run
+constexpr int EN_NARR = 5;               // T^n, two stage buffers (one doubles as u_x), u_y, lambda
 constexpr size_t energy_smem_bytes() { return (size_t)EN_NARR * EN_FN * sizeof(float); }
 static_assert(EN_FW == 64 && EN_NT % EN_FW == 0 && EN_FH % EN_NPH == 0, "energy frame mapping");
 
@@ -333,196 +339,234 @@ __global__ void __launch_bounds__(NTH, MINB) k_flow_batch(const StepArgs P, cons
 }
 
 // -------------------------------------------------------------- energy tile
-// An energy tile whose frame rows [y0 - 4, y0 + 28) lie in [W, ny - 2]: no
-// solid, Dirichlet, ghost or wall-flux row in the frame.
-__device__ __forceinline__ bool energy_interior(const StepArgs& A, int y0) {
-  return y0 - EN_H >= A.W && y0 + EN_TY + EN_H <= A.ny - 1;
-}
-
 // Temperature buffers of sub-step s of N: X_0 = T^n (T_in), X_N = T^{n+1}
 // (T_out); the others alternate with the scratch plane so that X_N lands in T_out.
 __device__ __forceinline__ float* substep_buffer(const StepArgs& A, int s, int nsub) {
   return ((nsub - s) & 1) ? A.T_scr : A.T_out;
 }
 
-template <bool INT>
+// Harmonic mean of two conductivities (Eq. 25 with dx = 1).
+__device__ __forceinline__ float harm(float a, float b) { return 2.f * a * b / (a + b); }
+
+// Per-cell coefficients of the energy right-hand side K(T) of Eq. (17):
+//   K = aE (T_E - T) + aW (T_W - T) + aN (T_N - T) + aS (T_S - T)
+//       - p (T_NE - T_SW) - q (T_SE - T_NW) - As T - Bs s (1 + kappa - kappa s),
+// s = sqrt(T / Tc).  The face terms are lambda_f / (rho cv) of Eqs. (22)-(26);
+// the isotropic gradient of Eq. (19) in u . grad T contributes -u_x/3, +u_x/3,
+// -u_y/3, +u_y/3 to them and p = (u_x + u_y)/12, q = (u_x - u_y)/12 on the
+// diagonals; As, Bs are the latent-heat coefficients (T dp/dT)_rho div u /
+// (rho cv) of Eq. (28) split into the T and the sqrt(T) parts.  Solid rows
+// keep only the face terms; Dirichlet rows have all coefficients zero.
+enum { C_AE = 0, C_AW, C_AN, C_AS, C_P, C_Q, C_AS_T, C_BS, NCOEF };
+
+template <int R, int NPH>
 __device__ __forceinline__ void energy_tile(const StepArgs& A, int bx, int by, int part, float* sm, int s, int nsub) {
-  float* const sT0 = sm;
-  float* const sTa = sm + EN_FN;
-  float* const sTb = sm + 2 * EN_FN;
-  float* const sRho = sm + 3 * EN_FN;
-  float* const sUx = sm + 4 * EN_FN;
-  float* const sUy = sm + 5 * EN_FN;
-  float* const sLae = sm + 6 * EN_FN;  // east-face conductivity (Eq. 25)
-  float* const sLan = sm + 7 * EN_FN;  // north-face conductivity
-  float* const sIrcv = sm + 8 * EN_FN;
-  float* const sAs = sm + 9 * EN_FN;   // latent-heat source coefficients
-  float* const sBs = sm + 10 * EN_FN;
-  __shared__ float s_red[EN_NT / 32][NEPART][2];
+  constexpr int FW = EN_FW, H = EN_H, FH = R * NPH, TY = FH - 2 * H, FN = FW * FH, NT = FW * NPH;
+  static_assert(TY == EN_TY && NT == EN_NT, "energy tile geometry");
+  float* const sT = sm;           // T^n on the frame: stage-1 input
+  float* const sA = sm + FN;      // stage outputs (stages 1 and 3)
+  float* const sB = sm + 2 * FN;  // stage outputs (stage 2); u_x during the coefficient pass
+  float* const sUy = sm + 3 * FN;
+  float* const sLam = sm + 4 * FN;
+  float* const sUx = sB;
+  __shared__ float s_red[NT / 32][NEPART][2];
   __shared__ int s_err;
 
   const float* __restrict__ T_in = s == 1 ? A.T_in : substep_buffer(A, s - 1, nsub);
   float* __restrict__ T_out = substep_buffer(A, s, nsub);
   const bool last = s == nsub;
   const Geo g = make_geo(A);
-  const int nx = A.nx, ny = A.ny;
+  const int nx = A.nx, ny = A.ny, W = A.W;
   const int NC = nx * ny;
   const float* __restrict__ rho_n = A.mom;
   const float* __restrict__ ux_n = A.mom + NC;
   const float* __restrict__ uy_n = A.mom + 2 * NC;
-  const int x0 = bx * EN_TX, y0 = by * EN_TY;
+  const int x0 = bx * EN_TX, y0 = by * TY;
   const int tid = threadIdx.x;
-  const int i = tid % EN_FW, jp = tid / EN_FW;
-  const int gxu = x0 - EN_H + i;
+  const int i = tid & (FW - 1), jp = tid / FW;
+  const int j0 = jp * R;                 // first frame row of the run
+  const int gy0 = y0 - H + j0;           // its lattice row
+  const int gxu = x0 - H + i;
   const int gx = wrapx(gxu, nx);
-  const bool own_col = i >= EN_H && i < EN_H + EN_TX && gxu < nx;
-  const float lam_w = A.lambda_w, cvk = A.cvk;
-  auto wall_lam = [&](int row) -> float { return g.top_wall && row == ny - 1 ? A.lambda_top : lam_w; };
+  const bool own_col = i >= H && i < H + EN_TX && gxu < nx;
+  const bool top_open = g.top_open;
+  auto wall_lam = [&](int row) -> float { return g.top_wall && row == ny - 1 ? A.lambda_top : A.lambda_w; };
   if (tid == 0) s_err = 0;
   int err = 0;
 
-  // ---- T (the wall value on Dirichlet rows), rho^n and u^n; frame rows above
-  // the lattice copy row ny - 1 (the zero-gradient ghost of an open top), rows
-  // below it are never read
+  // ---- load T (wall values on Dirichlet rows), rho^n, u^n and lambda; frame
+  // rows above the lattice hold copies of row ny - 1, rows below it zeros
+  float T0[R], rho[R], lam[R];
 #pragma unroll
-  for (int m = 0; m < EN_NJ; ++m) {
-    const int j = jp + EN_NPH * m;
-    const int gy = y0 - EN_H + j;
-    const int idx = j * EN_FW + i;
-    if (!INT && gy < 0) {
-      sT0[idx] = sRho[idx] = sUx[idx] = sUy[idx] = 0.f;
-      continue;
+  for (int m = 0; m < R; ++m) {
+    const int j = j0 + m, gy = gy0 + m;
+    float T = 0.f, ux = 0.f, uy = 0.f;
+    rho[m] = 0.f;
+    lam[m] = A.lambda_w;
+    if (gy >= 0) {
+      const int gr = gy < ny ? gy : ny - 1;
+      const int c = gr * nx + gx;
+      T = g.dirichlet_row(gr) ? (gr == 0 ? A.T_bottom : A.T_top) : __ldg(T_in + c);
+      if (g.solid_row(gr)) {
+        lam[m] = wall_lam(gr);
+      } else {
+        rho[m] = __ldg(rho_n + c);
+        ux = __ldg(ux_n + c);
+        uy = __ldg(uy_n + c);
+        lam[m] = rho[m] * A.cvk;
+      }
     }
-    const int gr = INT || gy < ny ? gy : ny - 1;
-    const int c = gr * nx + gx;
-    const bool solid = !INT && g.solid_row(gr);
-    sT0[idx] = !INT && g.dirichlet_row(gr) ? (gr == 0 ? A.T_bottom : A.T_top) : __ldg(T_in + c);
-    sRho[idx] = solid ? 0.f : __ldg(rho_n + c);
-    sUx[idx] = solid ? 0.f : __ldg(ux_n + c);
-    sUy[idx] = solid ? 0.f : __ldg(uy_n + c);
+    T0[m] = T;
+    sT[j * FW + i] = T;
+    sUx[j * FW + i] = ux;
+    sUy[j * FW + i] = uy;
+    sLam[j * FW + i] = lam[m];
   }
   __syncthreads();
 
-  // ---- face conductivities on the whole frame; the other coefficients on
-  // ring 3 (rows and columns 1 .. 62)
+  // ---- coefficients on ring 3 (frame rows 1 .. FH-2, every column; the two
+  // edge columns read neighbours of the adjacent rows and are never used)
+  // div u (Eq. 19), separable: with Dx(r) = u_x(E) - u_x(W) and Sy(r) = u_y(E) + u_y(W)
+  // of row r, div u = Dx(0)/3 + (Dx(+1) + Dx(-1))/12 + (u_y(N) - u_y(S))/3 + (Sy(+1) - Sy(-1))/12
+  float Dx[R + 2], Sy[R + 2], uyc[R + 2];
 #pragma unroll
-  for (int m = 0; m < EN_NJ; ++m) {
-    const int j = jp + EN_NPH * m;
-    const int gy = y0 - EN_H + j;
-    if (!INT && gy < 0) continue;
-    const int idx = j * EN_FW + i;
-    const int gr = INT || gy < ny ? gy : ny - 1;
-    const bool solid = !INT && g.solid_row(gr);
-    const float lam = solid ? wall_lam(gr) : sRho[idx] * cvk;
-    if (i + 1 < EN_FW) {
-      const float le = solid ? wall_lam(gr) : sRho[idx + 1] * cvk;
-      sLae[idx] = 2.f * lam * le / (lam + le);
-    }
-    if (j + 1 < EN_FH) {
-      const int gn = INT || gy + 1 < ny ? gy + 1 : ny - 1;
-      const float ln = !INT && g.solid_row(gn) ? wall_lam(gn) : sRho[idx + EN_FW] * cvk;
-      sLan[idx] = 2.f * lam * ln / (lam + ln);
-    }
-    if (j < 1 || j >= EN_FH - 1 || i < 1 || i >= EN_FW - 1 || (!INT && gy >= ny)) continue;
+  for (int m = -1; m <= R; ++m) {
+    const int j = min(max(j0 + m, 0), FH - 1);
+    const int b = j * FW + i;
+    Dx[m + 1] = sUx[b + 1] - sUx[b - 1 < 0 ? 0 : b - 1];
+    Sy[m + 1] = sUy[b + 1 < FN ? b + 1 : FN - 1] + sUy[b - 1 < 0 ? 0 : b - 1];
+    uyc[m + 1] = sUy[b];
+  }
+  const float lamS_run = sLam[max(j0 - 1, 0) * FW + i];
+  const float lamN_run = sLam[min(j0 + R, FH - 1) * FW + i];
+  float cf[R][NCOEF];
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+    const int j = j0 + m, gy = gy0 + m;
+#pragma unroll
+    for (int q = 0; q < NCOEF; ++q) cf[m][q] = 0.f;
+    if (j < 1 || j >= FH - 1 || gy < 0 || gy >= ny) continue;  // warp-uniform
+    const bool solid = g.solid_row(gy);
+    if (g.dirichlet_row(gy)) continue;  // T held: K = 0
+    const int b = j * FW + i;
+    const float lE = sLam[b + 1], lW = sLam[b - 1];
+    float lN = m + 1 < R ? lam[m + 1] : lamN_run;
+    const float lS = m > 0 ? lam[m - 1] : lamS_run;
+    if (top_open && gy == ny - 1) lN = lam[m];  // zero-gradient ghost above an open top
+    const float ircv = solid ? A.inv_rcv_w : 1.f / (rho[m] * A.cv);
+    const float cE = harm(lam[m], lE) * ircv, cW = harm(lam[m], lW) * ircv;
+    const float cN = harm(lam[m], lN) * ircv;
+    // row 0 under an imposed flux (Section 3.3): no conductive flux through its
+    // bottom face (T below is the edge copy); q_in enters instead (added in the stages)
+    const float cS = gy == 0 ? 0.f : harm(lam[m], lS) * ircv;
     if (solid) {
-      sIrcv[idx] = A.inv_rcv_w;
-      sAs[idx] = 0.f;
-      sBs[idx] = 0.f;
+      cf[m][C_AE] = cE;
+      cf[m][C_AW] = cW;
+      cf[m][C_AN] = cN;
+      cf[m][C_AS] = cS;
       continue;
     }
-    const int js = j - 1, jn = j + 1;
-    const float rho = sRho[idx];
-    const float ircv = 1.f / (rho * A.cv);
-    // div u with the isotropic gradient of Eq. (19)
-    const float dux = (sUx[idx + 1] - sUx[idx - 1]) * (1.f / 3.f) +
-                      ((sUx[jn * EN_FW + i + 1] - sUx[js * EN_FW + i - 1]) +
-                       (sUx[js * EN_FW + i + 1] - sUx[jn * EN_FW + i - 1])) *
-                          (1.f / 12.f);
-    const float duy = (sUy[jn * EN_FW + i] - sUy[js * EN_FW + i]) * (1.f / 3.f) +
-                      ((sUy[jn * EN_FW + i + 1] - sUy[js * EN_FW + i - 1]) +
-                       (sUy[jn * EN_FW + i - 1] - sUy[js * EN_FW + i + 1])) *
-                          (1.f / 12.f);
-    const float divu = dux + duy;
-    const float br = A.b * rho;
-    // T (dp/dT)_rho = As' T + Bs' (1 + kappa (1 - sqrt Tr)) sqrt Tr (Eq. 28)
-    const float Ar = rho * A.R / (1.f - br);
-    const float Br = A.a * rho * rho * A.kappa / (1.f + 2.f * br - br * br);
-    sIrcv[idx] = ircv;
-    sAs[idx] = Ar * ircv * divu;
-    sBs[idx] = Br * ircv * divu;
+    // (above an open top the frame holds copies of row ny - 1: the zero-gradient ghost)
+    const float ux = sUx[b], uy = uyc[m + 1];
+    const float divu = Dx[m + 1] * (1.f / 3.f) + (Dx[m + 2] + Dx[m]) * (1.f / 12.f) +
+                       (uyc[m + 2] - uyc[m]) * (1.f / 3.f) + (Sy[m + 2] - Sy[m]) * (1.f / 12.f);
+    const float br = A.b * rho[m];
+    const float Ar = rho[m] * A.R / (1.f - br);
+    const float Br = A.a * rho[m] * rho[m] * A.kappa / (1.f + 2.f * br - br * br);
+    cf[m][C_AE] = cE - ux * (1.f / 3.f);
+    cf[m][C_AW] = cW + ux * (1.f / 3.f);
+    cf[m][C_AN] = cN - uy * (1.f / 3.f);
+    cf[m][C_AS] = cS + uy * (1.f / 3.f);
+    cf[m][C_P] = (ux + uy) * (1.f / 12.f);
+    cf[m][C_Q] = (ux - uy) * (1.f / 12.f);
+    cf[m][C_AS_T] = Ar * ircv * divu;
+    cf[m][C_BS] = Br * ircv * divu;
   }
-  __syncthreads();
 
-  // ---- RK4 stages (Eq. 18): stage k on ring 4 - k
-  const int jtop = ny - 1 - y0 + EN_H;  // frame row of the lattice's top row
-  const bool has_ghost = !INT && jtop < EN_FH - 1;
+  // ---- RK4 stages (Eq. 18): stage k on ring 4 - k; the run's own values in registers
   const float dt = A.dt;
-  float acc[EN_NJ];
+  const float qc = A.q_in * A.inv_rcv_w;  // row 0 under an imposed flux (solid)
+  const float k1 = 1.f + A.kappa;
+  float cur[R], acc[R];
   float ah[NEPART], al[NEPART];
 #pragma unroll
   for (int q = 0; q < NEPART; ++q) ah[q] = al[q] = 0.f;
 #pragma unroll
-  for (int m = 0; m < EN_NJ; ++m) acc[m] = 0.f;
+  for (int m = 0; m < R; ++m) {
+    cur[m] = T0[m];
+    acc[m] = 0.f;
+  }
 #pragma unroll
   for (int k = 1; k <= 4; ++k) {
-    const float* Tc = k == 1 ? sT0 : (k == 3 ? sTb : sTa);
-    float* Tn = k == 1 ? sTa : (k == 2 ? sTb : sTa);
+    const float* In = k == 1 ? sT : (k == 3 ? sB : sA);
+    float* Out = k == 2 ? sB : sA;
     const float cnext = k == 3 ? dt : 0.5f * dt;
     const float wk = (k == 1 || k == 4) ? dt * (1.f / 6.f) : dt * (2.f / 6.f);
-    const float wacc = (k == 1) ? 1.f : 2.f;
+    const float wacc = k == 1 ? 1.f : 2.f;
     const int r = 4 - k;
+    // neighbours of the run: columns i - 1 and i + 1 as a three-row window
+    // rolling up the run, and column i just below and above it
+    const int ie = i + 1 < FW ? i + 1 : i, iw = i > 0 ? i - 1 : i;
+    const int js = max(j0 - 1, 0), jn = min(j0 + R, FH - 1);
+    float Es = In[js * FW + ie], Ws = In[js * FW + iw];
+    float Ec = In[j0 * FW + ie], Wc = In[j0 * FW + iw];
+    float prev = In[js * FW + i];  // stage input of the row below the current one
+    const float Cn = In[jn * FW + i];
 #pragma unroll
-    for (int m = 0; m < EN_NJ; ++m) {
-      const int j = jp + EN_NPH * m;
-      const int gy = y0 - EN_H + j;
-      // rows outside ring r are skipped (warp-uniform); every column of a row
-      // is evaluated (columns outside the ring are never read later)
-      if (j < EN_H - r || j >= EN_H + EN_TY + r || (!INT && (gy < 0 || gy >= ny))) continue;
-      const bool own = own_col && j >= EN_H && j < EN_H + EN_TY;
-      const int idx = j * EN_FW + i;
-      const int js = j - 1, jn = j + 1;
-      const float Tp = Tc[idx];
-      float hk = 0.f;
-      // row 0 under an imposed flux (Section 3.3): q_in enters through its bottom face
-      const bool bot = !INT && gy == 0;
-      if (INT || !g.dirichlet_row(gy)) {
-        const float TE = Tc[idx + 1], TW = Tc[idx - 1], TN = Tc[jn * EN_FW + i], TS = Tc[js * EN_FW + i];
-        // Eqs. (22)-(26): the sum of the face fluxes of the control volume
-        float kk = sLae[idx] * (TE - Tp);
-        kk = fmaf(sLae[idx - 1], TW - Tp, kk);
-        kk = fmaf(sLan[idx], TN - Tp, kk);
-        kk = bot ? kk + A.q_in : fmaf(sLan[js * EN_FW + i], TS - Tp, kk);
-        kk *= sIrcv[idx];
-        if (INT || !g.solid_row(gy)) {
-          const float TNE = Tc[jn * EN_FW + i + 1], TNW = Tc[jn * EN_FW + i - 1];
-          const float TSE = Tc[js * EN_FW + i + 1], TSW = Tc[js * EN_FW + i - 1];
-          const float gxT = (TE - TW) * (1.f / 3.f) + ((TNE - TSW) + (TSE - TNW)) * (1.f / 12.f);
-          const float gyT = (TN - TS) * (1.f / 3.f) + ((TNE - TSW) + (TNW - TSE)) * (1.f / 12.f);
-          kk -= sUx[idx] * gxT + sUy[idx] * gyT;
-          const float sTr = sqrtf(fmaxf(Tp, 0.f) * A.invTc);
-          kk -= sAs[idx] * Tp + sBs[idx] * (1.f + A.kappa * (1.f - sTr)) * sTr;
+    for (int m = 0; m < R; ++m) {
+      const int j = j0 + m, gy = gy0 + m;
+      const int ja = m + 1 < R ? j + 1 : jn;
+      const float En = In[ja * FW + ie], Wn = In[ja * FW + iw];
+      const float Tp = cur[m];
+      const float TS = prev;
+      prev = Tp;
+      if (!(j < H - r || j >= H + TY + r || gy < 0 || gy >= ny)) {  // warp-uniform ring test
+        float TN = m + 1 < R ? cur[m + 1] : Cn;
+        float TNE = En, TNW = Wn;
+        if (top_open && gy == ny - 1) {  // zero-gradient ghost above an open top
+          TN = Tp;
+          TNE = Ec;
+          TNW = Wc;
         }
-        hk = kk;
-      }
-      if (k < 4) acc[m] += wacc * hk;
-      if (own) {
-        if (!INT) {
-          if (gy == 1) ff_add(ah[EP_QB], al[EP_QB], wk * sLan[js * EN_FW + i] * (Tc[js * EN_FW + i] - Tp));
-          if (g.top_wall && gy == ny - 2) ff_add(ah[EP_QT], al[EP_QT], wk * sLan[idx] * (Tp - Tc[jn * EN_FW + i]));
-          if (gy == A.W) ff_add(ah[EP_QI], al[EP_QI], wk * sLan[js * EN_FW + i] * (Tc[js * EN_FW + i] - Tp));
+        const float* c = cf[m];
+        float kk = c[C_AE] * (Ec - Tp);
+        kk = fmaf(c[C_AW], Wc - Tp, kk);
+        kk = fmaf(c[C_AN], TN - Tp, kk);
+        kk = fmaf(c[C_AS], TS - Tp, kk);
+        kk = fmaf(-c[C_P], TNE - Ws, kk);
+        kk = fmaf(-c[C_Q], Es - TNW, kk);
+        const float sTr = sqrtf(fmaxf(Tp, 0.f) * A.invTc);
+        kk -= fmaf(c[C_AS_T], Tp, c[C_BS] * sTr * fmaf(-A.kappa, sTr, k1));
+        if (gy == 0 && g.bottom_flux) kk += qc;
+        const bool own = own_col && j >= H && j < H + TY;
+        if (own && (gy == 1 || gy == W || (g.top_wall && gy == ny - 2))) {
+          // RK-weighted conductive fluxes through the wall faces (q_bottom, q_interface, q_top)
+          const float lc = sLam[j * FW + i];
+          const float lS = harm(lc, sLam[(j - 1) * FW + i]);
+          if (gy == 1) ff_add(ah[EP_QB], al[EP_QB], wk * lS * (TS - Tp));
+          if (gy == W) ff_add(ah[EP_QI], al[EP_QI], wk * lS * (TS - Tp));
+          if (g.top_wall && gy == ny - 2)
+            ff_add(ah[EP_QT], al[EP_QT], wk * harm(lc, sLam[(j + 1) * FW + i]) * (Tp - TN));
         }
-        if (k == 4) {
-          const float Tnew = sT0[idx] + dt * (1.f / 6.f) * (acc[m] + hk);
+        if (k < 4) {
+          acc[m] = fmaf(wacc, kk, acc[m]);
+          cur[m] = fmaf(cnext, kk, T0[m]);
+        } else if (own) {
+          const float Tnew = T0[m] + dt * (1.f / 6.f) * (acc[m] + kk);
           if (nonfinite(Tnew)) err |= ERR_NONFINITE;
           T_out[gy * nx + gx] = Tnew;
-          if (last) ff_add(ah[EP_E], al[EP_E], Tnew / sIrcv[idx]);
+          // sensible energy rho cv T (lambda = rho cv k in the fluid)
+          if (last) ff_add(ah[EP_E], al[EP_E], Tnew * (g.solid_row(gy) ? A.rcv_w : sLam[j * FW + i] * A.inv_k));
         }
       }
-      if (k < 4) Tn[idx] = sT0[idx] + cnext * hk;
+      Es = Ec;
+      Ws = Wc;
+      Ec = En;
+      Wc = Wn;
     }
-    __syncthreads();
-    if (k < 4 && has_ghost) {
-      for (int jj = jtop + 1 + jp; jj < EN_FH; jj += EN_NPH) Tn[jj * EN_FW + i] = Tn[jtop * EN_FW + i];
+    if (k < 4) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) Out[(j0 + m) * FW + i] = cur[m];
       __syncthreads();
     }
   }
@@ -535,10 +579,7 @@ __device__ __forceinline__ void energy_tile(const StepArgs& A, int bx, int by, i
 __global__ void __launch_bounds__(EN_NT, 2) k_energy(const StepArgs A, int s, int nsub) {
   extern __shared__ float sm[];
   const int part = blockIdx.y * gridDim.x + blockIdx.x;
-  if (energy_interior(A, blockIdx.y * EN_TY))
-    energy_tile<true>(A, blockIdx.x, blockIdx.y, part, sm, s, nsub);
-  else
-    energy_tile<false>(A, blockIdx.x, blockIdx.y, part, sm, s, nsub);
+  energy_tile<EN_R, EN_NPH>(A, blockIdx.x, blockIdx.y, part, sm, s, nsub);
 }
 
 __global__ void __launch_bounds__(EN_NT, 2) k_energy_batch(const StepArgs P, const DomArgs* __restrict__ desc,
@@ -555,10 +596,7 @@ __global__ void __launch_bounds__(EN_NT, 2) k_energy_batch(const StepArgs P, con
   const int local = s_bl.y;
   const int tx = (A.nx + EN_TX - 1) / EN_TX;
   const int by = local / tx;
-  if (energy_interior(A, by * EN_TY))
-    energy_tile<true>(A, local % tx, by, local, sm, s, nsub);
-  else
-    energy_tile<false>(A, local % tx, by, local, sm, s, nsub);
+  energy_tile<EN_R, EN_NPH>(A, local % tx, by, local, sm, s, nsub);
 }
 
 // ------------------------------------------------------------- reduction
