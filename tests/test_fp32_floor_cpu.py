@@ -4,48 +4,30 @@ every step exactly as the GPU library stores it (populations as deviations
 f_i - w_i rho_v, the temperature, the convective-outlet memory).
 
 Over the parity runs of the GPU tests (flat interface 1000 steps, ragged box
-300 steps, film 1000 steps) this storage rounding alone moves u by 2.5e-5 to
-3e-5 of max|u| (max|u| is 2.5e-3 to 1.2e-2: spurious currents and slow
-convection), while rho and T stay within 2e-6 of their maxima.  A relative
-L-infinity bound of 1e-5 on u measured against max|u| is therefore out of
-reach of any FP32-stored state, however its arithmetic is done.  The GPU
-parity tests bound u at U_REL_TOL = 1e-4 of max|u| (about three times this
-floor, leaving room for the FP32 arithmetic of the step itself) in addition
-to 1e-5 of the lattice sound speed."""
+300 steps, film 1000 steps) this storage rounding alone moves u by about 1e-7
+in absolute terms, 2.5e-5 to 3e-5 of max|u| there (max|u| is 2.5e-3 to
+1.2e-2), and by 1.5e-4 of max|u| on a 72 x 60 film whose flow is slower;
+rho and T stay within 2e-6 of their maxima.  A bound of 1e-5 on u relative
+to max|u| is therefore out of reach of any FP32-stored state, and no single
+relative bound fits every case.  The GPU parity tests step this FP32-stored
+twin beside the oracle (helpers.oracle_pair) and bound the GPU's u error by
+U_FLOOR_FACTOR times the twin's, in addition to 1e-5 of the sound speed."""
 import numpy as np
 import pytest
 
-from oracle.lattice import W
 from paper_1812_10375_gb300 import workloads as wl
 
-from helpers import coexistence, oracle_domain, ragged_case
-
-U_REL_TOL = 1e-4  # the GPU parity tests' bound on u, relative to max|u|
-
-
-def _round_state(d, rho_ref):
-    w = W[:, None, None]
-    dev = (d.fs - w * rho_ref).astype(np.float32).astype(np.float64)
-    d.fs = np.where(d.fluid[None], dev + w * rho_ref, 0.0)
-    d.T = d.T.astype(np.float32).astype(np.float64)
-    wt = W[[4, 7, 8]][:, None]
-    d.f_top_prev = (d.f_top_prev - wt * rho_ref).astype(np.float32).astype(np.float64) + wt * rho_ref
+from helpers import coexistence, oracle_pair, ragged_case
 
 
 def _storage_floor(case, steps, coex):
-    exact = oracle_domain(case, coex)
-    stored = oracle_domain(case, coex)
-    _round_state(stored, coex["rho_v"])
-    for _ in range(steps):
-        exact.step(1)
-        stored.step(1)
-        _round_state(stored, coex["rho_v"])
+    exact, stored = oracle_pair(case, coex, steps)
     fl = exact.fluid
     umax = float(np.sqrt(exact.ux ** 2 + exact.uy ** 2)[fl].max())
     du = max(np.abs(exact.ux - stored.ux)[fl].max(), np.abs(exact.uy - stored.uy)[fl].max())
     drho = np.abs(exact.rho - stored.rho)[fl].max() / np.abs(exact.rho[fl]).max()
     dT = np.abs(exact.T - stored.T).max() / np.abs(exact.T).max()
-    return du / umax, drho, dT
+    return du / umax, drho, dT, du
 
 
 @pytest.mark.slow
@@ -53,7 +35,8 @@ def _storage_floor(case, steps, coex):
 def test_fp32_storage_alone_moves_u_above_1e5_of_its_maximum(name, steps):
     coex = coexistence()
     case = {"flat": wl.flat_interface(), "ragged": ragged_case(), "film": wl.film()}[name]
-    eu, erho, eT = _storage_floor(case, steps, coex)
-    print(f"{name}: FP32 storage floor u {eu:.2e} of max|u|, rho {erho:.2e}, T {eT:.2e}")
-    assert 1e-5 < eu < U_REL_TOL / 2
+    eu, erho, eT, du = _storage_floor(case, steps, coex)
+    print(f"{name}: FP32 storage floor u {eu:.2e} of max|u| ({du:.2e} absolute), rho {erho:.2e}, T {eT:.2e}")
+    assert 1e-5 < eu < 1e-4
+    assert 2e-8 < du < 1e-6
     assert erho < 5e-6 and eT < 5e-6
