@@ -51,15 +51,19 @@ constexpr int TILE_Y = 28;      // the default variant's tile height (variant 0)
 constexpr int MIN_TILE_Y = 16;  // the shortest variant tile (sizes the partial-sum slots)
 
 // Split-step variants (k_flow* then k_energy*): the flow tile's fluid rows and
-// threads; the energy tile is the same for all of them.
+// threads, and the energy kernel's thread layout (the energy tile is the same).
 struct FlowVariant {
-  int ty, nth;
+  int ty, nth, er, enph;
   size_t smem;
   const void* single_fn;
   const void* batch_fn;
+  const void* esingle_fn;
+  const void* ebatch_fn;
   void (*launch_single)(dim3, size_t, cudaStream_t, const StepArgs&);
   void (*launch_batch)(int, size_t, cudaStream_t, const StepArgs&, const DomArgs*, const int2*, const int*,
                        const float2*);
+  void (*energy_single)(dim3, cudaStream_t, const StepArgs&, int, int);
+  void (*energy_batch)(int, cudaStream_t, const StepArgs&, const DomArgs*, const int2*, const int*, int, int);
 };
 template <int TY, int NTH, int MINB>
 void launch_flow_single(dim3 grid, size_t smem, cudaStream_t s, const StepArgs& a) {
@@ -70,11 +74,22 @@ void launch_flow_batch(int blocks, size_t smem, cudaStream_t s, const StepArgs& 
                        const int2* blk, const int* act, const float2* lag) {
   k_flow_batch<TY, NTH, MINB><<<blocks, NTH, smem, s>>>(phys, desc, blk, act, lag);
 }
-#define HLB_FLOW_ENTRY(TY, NTH, MINB)                                                                     \
-  FlowVariant{TY, NTH, flow_smem_bytes<TY>(), (const void*)k_flow<TY, NTH, MINB>,                         \
-              (const void*)k_flow_batch<TY, NTH, MINB>, launch_flow_single<TY, NTH, MINB>,                \
-              launch_flow_batch<TY, NTH, MINB>},
-const FlowVariant FLOWS[] = {HLB_FLOW_VARIANTS(HLB_FLOW_ENTRY)};
+template <int R, int NPH, int MINB>
+void launch_energy_single(dim3 grid, cudaStream_t s, const StepArgs& a, int sub, int nsub) {
+  k_energy<R, NPH, MINB><<<grid, 64 * NPH, energy_smem_bytes(), s>>>(a, sub, nsub);
+}
+template <int R, int NPH, int MINB>
+void launch_energy_batch(int blocks, cudaStream_t s, const StepArgs& phys, const DomArgs* desc, const int2* blk,
+                         const int* act, int sub, int nsub) {
+  k_energy_batch<R, NPH, MINB><<<blocks, 64 * NPH, energy_smem_bytes(), s>>>(phys, desc, blk, act, sub, nsub);
+}
+#define HLB_SPLIT_ENTRY(TY, NTH, MINB, ER, ENPH, EMINB)                                                         \
+  FlowVariant{TY, NTH, ER, ENPH, flow_smem_bytes<TY>(), (const void*)k_flow<TY, NTH, MINB>,                     \
+              (const void*)k_flow_batch<TY, NTH, MINB>, (const void*)k_energy<ER, ENPH, EMINB>,               \
+              (const void*)k_energy_batch<ER, ENPH, EMINB>, launch_flow_single<TY, NTH, MINB>,                \
+              launch_flow_batch<TY, NTH, MINB>, launch_energy_single<ER, ENPH, EMINB>,                        \
+              launch_energy_batch<ER, ENPH, EMINB>},
+const FlowVariant FLOWS[] = {HLB_SPLIT_VARIANTS(HLB_SPLIT_ENTRY)};
 constexpr int NSPLIT = (int)(sizeof(FLOWS) / sizeof(FLOWS[0]));
 constexpr int MIN_FLOW_TY = 8;  // the shortest flow tile (sizes the flow partial-sum slots)
 
@@ -372,7 +387,7 @@ hlb_status launch_split_step(hlb_domain* d, cudaEvent_t after_flow = nullptr, cu
   fv.launch_single(d->grid, fv.smem, d->stream, a);
   if (after_flow && cudaEventRecord(after_flow, d->stream) != cudaSuccess) return HLB_ECUDA;
   const int nsub = d->p.n_sub;
-  for (int s = 1; s <= nsub; ++s) k_energy<<<d->egrid, EN_NT, energy_smem_bytes(), d->stream>>>(a, s, nsub);
+  for (int s = 1; s <= nsub; ++s) fv.energy_single(d->egrid, d->stream, a, s, nsub);
   if (after_energy && cudaEventRecord(after_energy, d->stream) != cudaSuccess) return HLB_ECUDA;
   k_reduce_split<<<1, 256, 0, d->stream>>>(d->fpart, (int)(d->grid.x * d->grid.y), d->epart,
                                            (int)(d->egrid.x * d->egrid.y), d->state, 1.0 / (double)d->n_fluid,
@@ -585,11 +600,13 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
             cudaSuccess)
       return HLB_ECUDA;
   }
-  if (cudaFuncSetAttribute(k_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)energy_smem_bytes()) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_energy_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)energy_smem_bytes()) !=
-          cudaSuccess)
-    return HLB_ECUDA;
+  for (int v = 0; v < NSPLIT; ++v) {
+    if (cudaFuncSetAttribute(FLOWS[v].esingle_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)energy_smem_bytes()) != cudaSuccess ||
+        cudaFuncSetAttribute(FLOWS[v].ebatch_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)energy_smem_bytes()) != cudaSuccess)
+      return HLB_ECUDA;
+  }
   for (int v = 0; v < NVARIANTS; ++v) {
     if (cudaFuncSetAttribute(VARIANTS[v].single_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)VARIANTS[v].smem) != cudaSuccess ||
@@ -776,8 +793,7 @@ hlb_status batch_launch(hlb_batch* b, cudaEvent_t before, cudaEvent_t after, cud
     if (mid && cudaEventRecord(mid, b->stream) != cudaSuccess) return HLB_ECUDA;
     const int nsub = b->dom[0].p.n_sub;
     for (int s = 1; s <= nsub; ++s)
-      k_energy_batch<<<b->total_etiles, EN_NT, energy_smem_bytes(), b->stream>>>(b->phys, desc, b->d_eblk,
-                                                                                 b->d_active, s, nsub);
+      fv.energy_batch(b->total_etiles, b->stream, b->phys, desc, b->d_eblk, b->d_active, s, nsub);
     if (after && cudaEventRecord(after, b->stream) != cudaSuccess) return HLB_ECUDA;
     k_reduce_split_batch<<<b->n, 256, 0, b->stream>>>(b->d_sra, b->d_active, b->d_lag, HIST_CAP);
     if (cudaGetLastError() != cudaSuccess) return HLB_ECUDA;

@@ -42,20 +42,19 @@ enum { EP_QB = 0, EP_QT, EP_QI, EP_E, NEPART };
 
 constexpr int FL_TX = 64;          // flow tile width
 constexpr int FL_FW = FL_TX + 2;   // psi frame: the tile and a one-cell ring
-// Compiled flow-tile variants (fluid rows per tile, threads per CTA, CTAs per SM).
-#define HLB_FLOW_VARIANTS(X) X(16, 256, 3) X(32, 512, 1) X(8, 256, 4)
+// Compiled split-step variants: flow tile (fluid rows, threads per CTA, CTAs
+// per SM) and energy layout (rows per thread run, runs, CTAs per SM).
+#define HLB_SPLIT_VARIANTS(X) X(16, 256, 3, 8, 4, 2) X(16, 256, 3, 4, 8, 1) X(8, 256, 4, 8, 4, 2) X(32, 512, 1, 4, 8, 1)
 
 constexpr int EN_TX = 56, EN_TY = 24, EN_H = 4;
 constexpr int EN_FW = EN_TX + 2 * EN_H;  // 64 frame columns, one per thread
 constexpr int EN_FH = EN_TY + 2 * EN_H;  // 32 frame rows
-constexpr int EN_NT = 256;
-constexpr int EN_NPH = EN_NT / EN_FW;    // 4 row phases
-constexpr int EN_NJ = EN_FH / EN_NPH;    // 8 frame rows per thread
 constexpr int EN_FN = EN_FW * EN_FH;
-constexpr int EN_R = EN_NJ;              // rows of a thread's run
 constexpr int EN_NARR = 5;               // T^n, two stage buffers (one doubles as u_x), u_y, lambda
 constexpr size_t energy_smem_bytes() { return (size_t)EN_NARR * EN_FN * sizeof(float); }
-static_assert(EN_FW == 64 && EN_NT % EN_FW == 0 && EN_FH % EN_NPH == 0, "energy frame mapping");
+static_assert(EN_FW == 64, "energy frame mapping");
+// Energy-kernel thread layouts over the 64 x 32 frame: rows per thread run R
+// and runs NPH (R * NPH = 32 frame rows, 64 * NPH threads).
 
 template <int TY>
 constexpr size_t flow_smem_bytes() { return (size_t)FL_FW * (TY + 2) * sizeof(float); }
@@ -359,10 +358,182 @@ __device__ __forceinline__ float harm(float a, float b) { return 2.f * a * b / (
 // keep only the face terms; Dirichlet rows have all coefficients zero.
 enum { C_AE = 0, C_AW, C_AN, C_AS, C_P, C_Q, C_AS_T, C_BS, NCOEF };
 
+// An energy tile whose frame rows [y0 - 4, y0 + 28) all lie in [W, ny - 2]:
+// no solid, Dirichlet, ghost or wall-flux row in the frame.
+__device__ __forceinline__ bool energy_interior(const StepArgs& A, int y0) {
+  return y0 - EN_H >= A.W && y0 + EN_TY + EN_H <= A.ny - 1;
+}
+
+// The same sub-step on an interior tile, without branches: every frame row of
+// every run is evaluated in every stage (rows outside a stage's ring get
+// values that nothing valid reads), and the coefficients use that
+// lambda = rho cv k in the fluid: lambda_f / (rho cv) = 2 k lambda_nb /
+// (lambda + lambda_nb), and the latent-heat coefficients need no 1/(rho cv).
+template <int R, int NPH>
+__device__ __forceinline__ void energy_tile_int(const StepArgs& A, int bx, int by, int part, float* sm, int s,
+                                                int nsub) {
+  constexpr int FW = EN_FW, H = EN_H, FH = R * NPH, TY = FH - 2 * H, FN = FW * FH, NT = FW * NPH;
+  static_assert(TY == EN_TY && FH == EN_FH, "energy tile geometry");
+  float* const sT = sm;
+  float* const sA = sm + FN;
+  float* const sB = sm + 2 * FN;
+  float* const sUy = sm + 3 * FN;
+  float* const sLam = sm + 4 * FN;
+  float* const sUx = sB;
+  __shared__ float s_red[NT / 32][NEPART][2];
+  __shared__ int s_err;
+
+  const float* __restrict__ T_in = s == 1 ? A.T_in : substep_buffer(A, s - 1, nsub);
+  float* __restrict__ T_out = substep_buffer(A, s, nsub);
+  const bool last = s == nsub;
+  const int nx = A.nx, ny = A.ny;
+  const int NC = nx * ny;
+  const float* __restrict__ rho_n = A.mom;
+  const float* __restrict__ ux_n = A.mom + NC;
+  const float* __restrict__ uy_n = A.mom + 2 * NC;
+  const int x0 = bx * EN_TX, y0 = by * TY;
+  const int tid = threadIdx.x;
+  const int i = tid & (FW - 1), jp = tid / FW;
+  const int j0 = jp * R;
+  const int gy0 = y0 - H + j0;
+  const int gxu = x0 - H + i;
+  const int gx = wrapx(gxu, nx);
+  const bool own_col = i >= H && i < H + EN_TX && gxu < nx;
+  const int ie = i + 1 < FW ? i + 1 : i, iw = i > 0 ? i - 1 : i;  // frame-edge columns read themselves
+  if (tid == 0) s_err = 0;
+  int err = 0;
+
+  // ---- load T^n, rho^n, u^n; lambda = rho cv k
+  float T0[R], rho[R], lam[R];
+  const float* tp = T_in + gy0 * nx + gx;
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+    const int o = m * nx;
+    const float T = __ldg(tp + o);
+    rho[m] = __ldg(rho_n + (tp - T_in) + o);
+    const float ux = __ldg(ux_n + (tp - T_in) + o);
+    const float uy = __ldg(uy_n + (tp - T_in) + o);
+    lam[m] = rho[m] * A.cvk;
+    T0[m] = T;
+    const int b = (j0 + m) * FW + i;
+    sT[b] = T;
+    sUx[b] = ux;
+    sUy[b] = uy;
+    sLam[b] = lam[m];
+  }
+  __syncthreads();
+
+  // ---- coefficients (every row of the run; see energy_tile for the form)
+  float Dx[R + 2], Sy[R + 2], uyc[R + 2];
+#pragma unroll
+  for (int m = -1; m <= R; ++m) {
+    const int j = min(max(j0 + m, 0), FH - 1);
+    Dx[m + 1] = sUx[j * FW + ie] - sUx[j * FW + iw];
+    Sy[m + 1] = sUy[j * FW + ie] + sUy[j * FW + iw];
+    uyc[m + 1] = sUy[j * FW + i];
+  }
+  const float lamS_run = sLam[max(j0 - 1, 0) * FW + i];
+  const float lamN_run = sLam[min(j0 + R, FH - 1) * FW + i];
+  const float two_k = 2.f * A.kd;
+  const float Rc = A.R / A.cv, akc = A.a * A.kappa / A.cv;
+  float cf[R][NCOEF];
+  float rS = 1.f / (lam[0] + lamS_run);  // 1 / (lambda + lambda_S) of the run's first row
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+    const int b = (j0 + m) * FW;
+    const float l = lam[m];
+    const float lE = sLam[b + ie], lW = sLam[b + iw];
+    const float lN = m + 1 < R ? lam[m + 1] : lamN_run;
+    const float lS = m > 0 ? lam[m - 1] : lamS_run;
+    const float rN = 1.f / (l + lN);
+    const float cE = two_k * lE / (l + lE), cW = two_k * lW / (l + lW);
+    const float cN = two_k * lN * rN, cS = two_k * lS * rS;
+    rS = rN;  // the next row's south face is this row's north face
+    const float ux = sUx[b + i], uy = uyc[m + 1];
+    const float divu = Dx[m + 1] * (1.f / 3.f) + (Dx[m + 2] + Dx[m]) * (1.f / 12.f) +
+                       (uyc[m + 2] - uyc[m]) * (1.f / 3.f) + (Sy[m + 2] - Sy[m]) * (1.f / 12.f);
+    const float br = A.b * rho[m];
+    cf[m][C_AE] = fmaf(ux, -1.f / 3.f, cE);
+    cf[m][C_AW] = fmaf(ux, 1.f / 3.f, cW);
+    cf[m][C_AN] = fmaf(uy, -1.f / 3.f, cN);
+    cf[m][C_AS] = fmaf(uy, 1.f / 3.f, cS);
+    cf[m][C_P] = (ux + uy) * (1.f / 12.f);
+    cf[m][C_Q] = (ux - uy) * (1.f / 12.f);
+    cf[m][C_AS_T] = divu * Rc / (1.f - br);
+    cf[m][C_BS] = divu * akc * rho[m] / fmaf(br, 2.f - br, 1.f);
+  }
+
+  // ---- RK4 stages (Eq. 18)
+  const float dt = A.dt;
+  const float k1 = 1.f + A.kappa;
+  float cur[R], acc[R];
+  float eh = 0.f, el = 0.f;
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+    cur[m] = T0[m];
+    acc[m] = 0.f;
+  }
+#pragma unroll
+  for (int k = 1; k <= 4; ++k) {
+    const float* In = k == 1 ? sT : (k == 3 ? sB : sA);
+    float* Out = k == 2 ? sB : sA;
+    const float cnext = k == 3 ? dt : 0.5f * dt;
+    const float wacc = k == 1 ? 1.f : 2.f;
+    const int js = max(j0 - 1, 0), jn = min(j0 + R, FH - 1);
+    float Es = In[js * FW + ie], Ws = In[js * FW + iw];
+    float Ec = In[j0 * FW + ie], Wc = In[j0 * FW + iw];
+    float prev = In[js * FW + i];
+    const float Cn = In[jn * FW + i];
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int ja = m + 1 < R ? j0 + m + 1 : jn;
+      const float En = In[ja * FW + ie], Wn = In[ja * FW + iw];
+      const float Tp = cur[m];
+      const float TS = prev;
+      prev = Tp;
+      const float TN = m + 1 < R ? cur[m + 1] : Cn;
+      const float* c = cf[m];
+      float kk = c[C_AE] * (Ec - Tp);
+      kk = fmaf(c[C_AW], Wc - Tp, kk);
+      kk = fmaf(c[C_AN], TN - Tp, kk);
+      kk = fmaf(c[C_AS], TS - Tp, kk);
+      kk = fmaf(-c[C_P], En - Ws, kk);
+      kk = fmaf(-c[C_Q], Es - Wn, kk);
+      const float sTr = sqrtf(fmaxf(Tp, 0.f) * A.invTc);
+      kk -= fmaf(c[C_AS_T], Tp, c[C_BS] * sTr * fmaf(-A.kappa, sTr, k1));
+      if (k < 4) {
+        acc[m] = fmaf(wacc, kk, acc[m]);
+        cur[m] = fmaf(cnext, kk, T0[m]);
+      } else {
+        const int j = j0 + m;
+        if (own_col && j >= H && j < H + TY) {
+          const float Tnew = T0[m] + dt * (1.f / 6.f) * (acc[m] + kk);
+          if (nonfinite(Tnew)) err |= ERR_NONFINITE;
+          T_out[(gy0 + m) * nx + gx] = Tnew;
+          if (last) ff_add(eh, el, Tnew * (rho[m] * A.cv));
+        }
+      }
+      Es = Ec;
+      Ws = Wc;
+      Ec = En;
+      Wc = Wn;
+    }
+    if (k < 4) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) Out[(j0 + m) * FW + i] = cur[m];
+      __syncthreads();
+    }
+  }
+  float ah[NEPART] = {0.f, 0.f, 0.f, eh}, al[NEPART] = {0.f, 0.f, 0.f, el};
+  if (err) atomicOr(&s_err, err);
+  block_partials<NT, NEPART>(ah, al, s_red, A.epart + (long long)part * NEPART, s > 1);
+  if (tid == 0 && s_err) atomicOr(&A.state->error_flags, s_err);
+}
+
 template <int R, int NPH>
 __device__ __forceinline__ void energy_tile(const StepArgs& A, int bx, int by, int part, float* sm, int s, int nsub) {
   constexpr int FW = EN_FW, H = EN_H, FH = R * NPH, TY = FH - 2 * H, FN = FW * FH, NT = FW * NPH;
-  static_assert(TY == EN_TY && NT == EN_NT, "energy tile geometry");
+  static_assert(TY == EN_TY && FH == EN_FH, "energy tile geometry");
   float* const sT = sm;           // T^n on the frame: stage-1 input
   float* const sA = sm + FN;      // stage outputs (stages 1 and 3)
   float* const sB = sm + 2 * FN;  // stage outputs (stage 2); u_x during the coefficient pass
@@ -572,31 +743,39 @@ __device__ __forceinline__ void energy_tile(const StepArgs& A, int bx, int by, i
   }
   if (err) atomicOr(&s_err, err);
   // fluxes add up over the sub-steps; the energy of T^{n+1} comes from the last
-  block_partials<EN_NT, NEPART>(ah, al, s_red, A.epart + (long long)part * NEPART, s > 1);
+  block_partials<NT, NEPART>(ah, al, s_red, A.epart + (long long)part * NEPART, s > 1);
   if (tid == 0 && s_err) atomicOr(&A.state->error_flags, s_err);
 }
 
-__global__ void __launch_bounds__(EN_NT, 2) k_energy(const StepArgs A, int s, int nsub) {
+template <int R, int NPH, int MINB>
+__global__ void __launch_bounds__(64 * NPH, MINB) k_energy(const StepArgs A, int s, int nsub) {
   extern __shared__ float sm[];
   const int part = blockIdx.y * gridDim.x + blockIdx.x;
-  energy_tile<EN_R, EN_NPH>(A, blockIdx.x, blockIdx.y, part, sm, s, nsub);
+  if (energy_interior(A, blockIdx.y * EN_TY))
+    energy_tile_int<R, NPH>(A, blockIdx.x, blockIdx.y, part, sm, s, nsub);
+  else
+    energy_tile<R, NPH>(A, blockIdx.x, blockIdx.y, part, sm, s, nsub);
 }
 
-__global__ void __launch_bounds__(EN_NT, 2) k_energy_batch(const StepArgs P, const DomArgs* __restrict__ desc,
-                                                           const int2* __restrict__ blk,
-                                                           const int* __restrict__ active, int s, int nsub) {
+template <int R, int NPH, int MINB>
+__global__ void __launch_bounds__(64 * NPH, MINB) k_energy_batch(const StepArgs P, const DomArgs* __restrict__ desc,
+                                                                 const int2* __restrict__ blk,
+                                                                 const int* __restrict__ active, int s, int nsub) {
   extern __shared__ float sm[];
   __shared__ DomArgs sD;
   __shared__ int s_act;
   __shared__ int2 s_bl;
   __shared__ float2 s_lg;
-  if (!batch_prologue<EN_NT>(desc, blk, active, nullptr, sD, s_bl, s_lg, s_act)) return;
+  if (!batch_prologue<64 * NPH>(desc, blk, active, nullptr, sD, s_bl, s_lg, s_act)) return;
   StepArgs A = P;
   apply_dom(A, sD);
   const int local = s_bl.y;
   const int tx = (A.nx + EN_TX - 1) / EN_TX;
   const int by = local / tx;
-  energy_tile<EN_R, EN_NPH>(A, local % tx, by, local, sm, s, nsub);
+  if (energy_interior(A, by * EN_TY))
+    energy_tile_int<R, NPH>(A, local % tx, by, local, sm, s, nsub);
+  else
+    energy_tile<R, NPH>(A, local % tx, by, local, sm, s, nsub);
 }
 
 // ------------------------------------------------------------- reduction
