@@ -12,6 +12,7 @@
 #include "hlb_kernels.cuh"
 #include "hlb_march.cuh"
 #include "hlb_split.cuh"
+#include "hlb_energy_walk.cuh"
 #include "hlb_substep.cuh"
 
 using namespace hlb;
@@ -53,17 +54,23 @@ constexpr int MIN_TILE_Y = 16;  // the shortest variant tile (sizes the partial-
 // Split-step variants (k_flow* then k_energy*): the flow tile's fluid rows and
 // threads, and the energy kernel's thread layout (the energy tile is the same).
 struct FlowVariant {
-  int ty, nth, er, enph;
+  int ty, nth;
+  int ewalk;   // energy kernel: 0 tile, 1 row walk
+  int ep;      // energy tile: rows per run; walk: segment rows
   size_t smem;
   const void* single_fn;
   const void* batch_fn;
   const void* esingle_fn;
   const void* ebatch_fn;
+  size_t esmem;  // dynamic shared memory of the energy kernels
   void (*launch_single)(dim3, size_t, cudaStream_t, const StepArgs&);
   void (*launch_batch)(int, size_t, cudaStream_t, const StepArgs&, const DomArgs*, const int2*, const int*,
                        const float2*);
   void (*energy_single)(dim3, cudaStream_t, const StepArgs&, int, int);
   void (*energy_batch)(int, cudaStream_t, const StepArgs&, const DomArgs*, const int2*, const int*, int, int);
+  dim3 egrid(int nx, int ny) const {
+    return ewalk ? dim3((nx + EW_OUT - 1) / EW_OUT, (ny + ep - 1) / ep) : dim3((nx + EN_TX - 1) / EN_TX, (ny + EN_TY - 1) / EN_TY);
+  }
 };
 template <int TY, int NTH, int MINB>
 void launch_flow_single(dim3 grid, size_t smem, cudaStream_t s, const StepArgs& a) {
@@ -83,13 +90,27 @@ void launch_energy_batch(int blocks, cudaStream_t s, const StepArgs& phys, const
                          const int* act, int sub, int nsub) {
   k_energy_batch<R, NPH, MINB><<<blocks, 64 * NPH, energy_smem_bytes(), s>>>(phys, desc, blk, act, sub, nsub);
 }
-#define HLB_SPLIT_ENTRY(TY, NTH, MINB, ER, ENPH, EMINB)                                                         \
-  FlowVariant{TY, NTH, ER, ENPH, flow_smem_bytes<TY>(), (const void*)k_flow<TY, NTH, MINB>,                     \
+template <int L>
+void launch_walk_single(dim3 grid, cudaStream_t s, const StepArgs& a, int sub, int nsub) {
+  k_energy_walk<L><<<grid, EW_W, 0, s>>>(a, sub, nsub);
+}
+template <int L>
+void launch_walk_batch(int blocks, cudaStream_t s, const StepArgs& phys, const DomArgs* desc, const int2* blk,
+                       const int* act, int sub, int nsub) {
+  k_energy_walk_batch<L><<<blocks, EW_W, 0, s>>>(phys, desc, blk, act, sub, nsub);
+}
+#define HLB_SPLIT_TILE(TY, NTH, MINB, ER, ENPH, EMINB)                                                          \
+  FlowVariant{TY, NTH, 0, ER, flow_smem_bytes<TY>(), (const void*)k_flow<TY, NTH, MINB>,                        \
               (const void*)k_flow_batch<TY, NTH, MINB>, (const void*)k_energy<ER, ENPH, EMINB>,               \
-              (const void*)k_energy_batch<ER, ENPH, EMINB>, launch_flow_single<TY, NTH, MINB>,                \
+              (const void*)k_energy_batch<ER, ENPH, EMINB>, energy_smem_bytes(), launch_flow_single<TY, NTH, MINB>, \
               launch_flow_batch<TY, NTH, MINB>, launch_energy_single<ER, ENPH, EMINB>,                        \
               launch_energy_batch<ER, ENPH, EMINB>},
-const FlowVariant FLOWS[] = {HLB_SPLIT_VARIANTS(HLB_SPLIT_ENTRY)};
+#define HLB_SPLIT_WALK(TY, NTH, MINB, L)                                                                        \
+  FlowVariant{TY, NTH, 1, L, flow_smem_bytes<TY>(), (const void*)k_flow<TY, NTH, MINB>,                         \
+              (const void*)k_flow_batch<TY, NTH, MINB>, (const void*)k_energy_walk<L>,                        \
+              (const void*)k_energy_walk_batch<L>, 0, launch_flow_single<TY, NTH, MINB>,                      \
+              launch_flow_batch<TY, NTH, MINB>, launch_walk_single<L>, launch_walk_batch<L>},
+const FlowVariant FLOWS[] = {HLB_SPLIT_VARIANTS(HLB_SPLIT_TILE, HLB_SPLIT_WALK)};
 constexpr int NSPLIT = (int)(sizeof(FLOWS) / sizeof(FLOWS[0]));
 constexpr int MIN_FLOW_TY = 8;  // the shortest flow tile (sizes the flow partial-sum slots)
 
@@ -120,7 +141,9 @@ dim3 grid_of(int nx, int ny, int W, int top_bc, int v) {
   const int t = tiled_index(v);
   return dim3((nx + TILE_X - 1) / TILE_X, (ny + VARIANTS[t].ty - 1) / VARIANTS[t].ty);
 }
+// The largest energy grid of any split variant (sizes the energy partial-sum slots).
 dim3 energy_grid_of(int nx, int ny) { return dim3((nx + EN_TX - 1) / EN_TX, (ny + EN_TY - 1) / EN_TY); }
+static_assert(EW_OUT == EN_TX, "walk strips and energy tiles share the column split");
 size_t flow_part_slots(int nx, int ny, int W, int top_bc) {
   return (size_t)((nx + FL_TX - 1) / FL_TX) * ((fluid_rows_of(ny, W, top_bc) + MIN_FLOW_TY - 1) / MIN_FLOW_TY);
 }
@@ -331,6 +354,17 @@ struct hlb_domain {
 
 namespace {
 
+// Variant v for domain d: launch grids of its step kernel(s).
+void set_variant_grids(hlb_domain* d, int v) {
+  d->variant = v;
+  d->grid = grid_of(d->p.nx, d->p.ny, d->p.wall_rows, d->p.top_bc, v);
+  d->egrid = is_split(v) ? FLOWS[v].egrid(d->p.nx, d->p.ny) : energy_grid_of(d->p.nx, d->p.ny);
+}
+
+}  // namespace
+
+namespace {
+
 struct Layout {
   size_t f, T, Gw, ftop, partials, state, hist, mom, fpart, epart, sub, total;
 };
@@ -529,7 +563,6 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
   d->Tscr = d->mom + 3 * N;
   d->fpart = (double*)(ws + L.fpart);
   d->epart = (double*)(ws + L.epart);
-  d->egrid = energy_grid_of(q.nx, q.ny);
   if (q.n_sub > 1) {
     d->subpart = (double*)(ws + L.sub);
     d->sub_grid = sub_grid_of(q.nx, q.ny);
@@ -537,8 +570,7 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
   const int fluid_rows = q.ny - q.wall_rows - (q.top_bc == HLB_TOP_WALL ? 1 : 0);
   d->n_fluid = (long long)fluid_rows * q.nx;
   // the split step for the finite-volume scheme; the fused tiled kernel for the isotropic one
-  d->variant = q.diffusion == HLB_DIFF_FV ? 0 : FIRST_TILED;
-  d->grid = grid_of(q.nx, q.ny, q.wall_rows, q.top_bc, d->variant);
+  set_variant_grids(d, q.diffusion == HLB_DIFF_FV ? 0 : FIRST_TILED);
   d->smem = smem_bytes();
 
   StepArgs& a = d->base;
@@ -602,9 +634,9 @@ hlb_status init_domain(hlb_domain* d, const hlb_params* p, char* ws, cudaStream_
   }
   for (int v = 0; v < NSPLIT; ++v) {
     if (cudaFuncSetAttribute(FLOWS[v].esingle_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)energy_smem_bytes()) != cudaSuccess ||
+                             (int)FLOWS[v].esmem) != cudaSuccess ||
         cudaFuncSetAttribute(FLOWS[v].ebatch_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)energy_smem_bytes()) != cudaSuccess)
+                             (int)FLOWS[v].esmem) != cudaSuccess)
       return HLB_ECUDA;
   }
   for (int v = 0; v < NVARIANTS; ++v) {
@@ -896,8 +928,7 @@ hlb_status set_batch_variant(hlb_batch* b, int v) {
   b->tile_off.assign(b->n + 1, 0);
   for (int i = 0; i < b->n; ++i) {
     hlb_domain* d = &b->dom[i];
-    d->variant = v;
-    d->grid = grid_of(d->p.nx, d->p.ny, d->p.wall_rows, d->p.top_bc, v);
+    set_variant_grids(d, v);
     b->tile_off[i + 1] = b->tile_off[i] + (int)(d->grid.x * d->grid.y);
   }
   b->total_tiles = b->tile_off[b->n];
@@ -1503,8 +1534,7 @@ hlb_status hlb_autotune(hlb_domain* d, int steps_per_variant, int* chosen, float
       if (h_ms && v < max_out) h_ms[v] = 1e30f;  // not available for this width, scheme or N
       continue;
     }
-    d->variant = v;
-    d->grid = grid_of(d->p.nx, d->p.ny, d->p.wall_rows, d->p.top_bc, v);
+    set_variant_grids(d, v);
     drop_graph(d);
     st = launch_step(d);  // one untimed step per variant (first-launch costs)
     cudaEventRecord(e0, d->stream);
@@ -1522,8 +1552,7 @@ hlb_status hlb_autotune(hlb_domain* d, int steps_per_variant, int* chosen, float
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  d->variant = best_v;
-  d->grid = grid_of(d->p.nx, d->p.ny, d->p.wall_rows, d->p.top_bc, best_v);
+  set_variant_grids(d, best_v);
   drop_graph(d);
   *chosen = best_v;
   return st;
@@ -1570,8 +1599,7 @@ hlb_status hlb_batch_autotune(hlb_batch* b, int steps_per_variant, int* chosen, 
 hlb_status hlb_set_tile_variant(hlb_domain* d, int v) {
   if (!d || v < 0 || v >= NV_ALL) return HLB_EINVAL;
   if (!variant_ok(d, v)) return HLB_EINVAL;
-  d->variant = v;
-  d->grid = grid_of(d->p.nx, d->p.ny, d->p.wall_rows, d->p.top_bc, v);
+  set_variant_grids(d, v);
   drop_graph(d);
   return HLB_OK;
 }

@@ -1,0 +1,359 @@
+// Energy sub-step of the split step in row-walking form (Hu & Liu, arXiv
+// 1812.10375, Eqs. 17-19, 22-27): one RK4 sub-step (Eq. 18, dt = 1/N) of the
+// energy equation with finite-volume harmonic face conductivities, on rho^n and
+// u^n held over the sub-steps.
+//
+// A CTA of 64 threads owns a strip of 56 output columns of one domain (one
+// thread per frame column, a 4-column halo on either side recomputed by the
+// neighbouring strips) and a segment of L output rows, and walks up the rows
+// once.  At walk step t (row r = t) it loads row r, computes the coefficients
+// of Eq. (17) and RK4 stage 1 at row r - 1, stage 2 at row r - 2, stage 3 at
+// r - 3 and stage 4 (the new temperature) at r - 4.  A stage at row y reads the
+// previous stage at rows y - 1 .. y + 1; the row y + 1 value was produced
+// earlier in the same walk step, so four CTA barriers separate the phases.
+// Row quantities that neighbouring threads read (T^n, the stage values, u and
+// lambda) pass through shared-memory rings of a few rows; everything a thread
+// needs only for its own column (the coefficients of the four rows in flight,
+// the RK accumulators, T^n, the stage values) stays in registers, addressed by
+// row mod 4 with the walk unrolled by four.  The y halo is 4 rows below and 4
+// above a segment; every row test depends only on the walk step, so branches
+// are uniform across the CTA.
+#pragma once
+#include "hlb_split.cuh"
+
+namespace hlb {
+
+constexpr int EW_W = 64;      // frame columns = threads per CTA
+constexpr int EW_OUT = 56;    // output columns of a strip
+constexpr int EW_H = 4;       // x halo
+constexpr int EW_RTN = 8;     // depth of the T^n ring
+constexpr int EW_R = 4;       // depth of the other rings
+// shared floats: T^n ring, three stage rings, u_x, u_y, lambda rings
+constexpr int EW_SMEM_FLOATS = (EW_RTN + 6 * EW_R) * EW_W;
+
+// Per-thread state of the walk.  Arrays indexed [row & 3] are row rings; the
+// walk is unrolled by four so that every index is a compile-time constant.
+struct WalkState {
+  float tn[4];      // T^n of rows r .. r-3
+  float t1[4], t2[4], t3[4];  // stage values of the rows in flight
+  float acc[4];     // K1 + 2 K2 + 2 K3
+  float cf[4][NCOEF];
+  float rcv[4];     // rho cv of a row (energy sum)
+  float qf[4];      // unscaled wall-face conductivity of a wall-flux row
+  float dx[4], sy[4], uy[4], lam[4];
+  float rho1;       // rho of row r - 1 (coefficient pass)
+  float pT, pR, pUx, pUy;  // prefetched row
+  float eh, el, qbh, qbl, qih, qil, qth, qtl;
+  int err;
+};
+
+struct WalkCtx {
+  const float* T_in;
+  float* T_out;
+  const float* rho_n;
+  const float* ux_n;
+  const float* uy_n;
+  float* sTn;
+  float* sT1;
+  float* sT2;
+  float* sT3;
+  float* sUx;
+  float* sUy;
+  float* sLam;
+  int i, ie, iw, gx;
+  bool own_col;
+  int ys, ye;  // output rows of the segment
+  bool last;
+};
+
+// RK4 right-hand side at one cell from the coefficient row and the 3 x 3 stencil.
+__device__ __forceinline__ float walk_K(const StepArgs& A, const float* c, float Tp, float TE, float TW, float TN,
+                                        float TS, float TNE, float TNW, float TSE, float TSW) {
+  float kk = c[C_AE] * (TE - Tp);
+  kk = fmaf(c[C_AW], TW - Tp, kk);
+  kk = fmaf(c[C_AN], TN - Tp, kk);
+  kk = fmaf(c[C_AS], TS - Tp, kk);
+  kk = fmaf(-c[C_P], TNE - TSW, kk);
+  kk = fmaf(-c[C_Q], TSE - TNW, kk);
+  const float sTr = sqrtf(fmaxf(Tp, 0.f) * A.invTc);
+  return kk - fmaf(c[C_AS_T], Tp, c[C_BS] * sTr * fmaf(-A.kappa, sTr, 1.f + A.kappa));
+}
+
+__device__ __forceinline__ void walk_load(const StepArgs& A, const WalkCtx& C, WalkState& S, int row) {
+  S.pT = S.pR = S.pUx = S.pUy = 0.f;
+  if (row < 0) return;
+  const Geo g = make_geo(A);
+  const int gr = row < A.ny ? row : A.ny - 1;  // zero-gradient ghost above the lattice
+  const int c = gr * A.nx + C.gx;
+  S.pT = g.dirichlet_row(gr) ? (gr == 0 ? A.T_bottom : A.T_top) : __ldg(C.T_in + c);
+  if (!g.solid_row(gr)) {
+    S.pR = __ldg(C.rho_n + c);
+    S.pUx = __ldg(C.ux_n + c);
+    S.pUy = __ldg(C.uy_n + c);
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, WalkState& S, int t) {
+  constexpr int P0 = P & 3, P1 = (P + 3) & 3, P2 = (P + 2) & 3, P3 = (P + 1) & 3;  // rows r, r-1, r-2, r-3
+  const Geo g = make_geo(A);
+  const int ny = A.ny, W = A.W;
+  const int i = C.i, ie = C.ie, iw = C.iw;
+  const float dt = A.dt;
+  const int r = t;
+  auto wall_lam = [&](int row) -> float { return g.top_wall && row == ny - 1 ? A.lambda_top : A.lambda_w; };
+
+  // ---- load phase: row r (prefetched) into the rings; prefetch row r + 1
+  {
+    const int gr = r < ny ? r : ny - 1;
+    const bool solid = r >= 0 && g.solid_row(gr);
+    const float lam = r < 0 ? A.lambda_w : (solid ? wall_lam(gr) : S.pR * A.cvk);
+    S.tn[P0] = S.pT;
+    S.lam[P0] = lam;
+    S.uy[P0] = S.pUy;
+    C.sTn[(r & (EW_RTN - 1)) * EW_W + i] = S.pT;
+    C.sUx[P0 * EW_W + i] = S.pUx;
+    C.sUy[P0 * EW_W + i] = S.pUy;
+    C.sLam[P0 * EW_W + i] = lam;
+    const float rho_r = S.pR;
+    walk_load(A, C, S, r + 1);
+    __syncthreads();
+    S.dx[P0] = C.sUx[P0 * EW_W + ie] - C.sUx[P0 * EW_W + iw];
+    S.sy[P0] = C.sUy[P0 * EW_W + ie] + C.sUy[P0 * EW_W + iw];
+    // ---- coefficients of row y = r - 1 (ring 3 of the segment)
+    const int y = r - 1;
+    if (y >= C.ys - 3 && y < C.ye + 3 && y >= 0 && y < ny) {
+      float* cf = S.cf[P1];
+#pragma unroll
+      for (int q = 0; q < NCOEF; ++q) cf[q] = 0.f;
+      const bool ysolid = g.solid_row(y);
+      S.rcv[P1] = ysolid ? A.rcv_w : S.rho1 * A.cv;
+      const float l = S.lam[P1];
+      const float lS = y > 0 ? S.lam[P2] : l;
+      S.qf[P1] = y == ny - 2 ? harm(l, S.lam[P0]) : harm(l, lS);
+      if (!g.dirichlet_row(y)) {
+        // lambda_f / (rho cv) = 2 kd lambda_nb / (lambda + lambda_nb), kd = lambda / (rho cv) of the row
+        const float kd = ysolid ? l * A.inv_rcv_w : A.kd;
+        const float lE = C.sLam[P1 * EW_W + ie], lW = C.sLam[P1 * EW_W + iw];
+        const float lN = (g.top_open && y == ny - 1) ? l : S.lam[P0];
+        const float cE = 2.f * kd * lE / (l + lE), cW = 2.f * kd * lW / (l + lW);
+        const float cN = 2.f * kd * lN / (l + lN);
+        // row 0 under an imposed flux: no conductive flux through its bottom face
+        const float cS = y == 0 ? 0.f : 2.f * kd * lS / (l + lS);
+        if (ysolid) {
+          cf[C_AE] = cE;
+          cf[C_AW] = cW;
+          cf[C_AN] = cN;
+          cf[C_AS] = cS;
+        } else {
+          const float ux = C.sUx[P1 * EW_W + i], uy = S.uy[P1];
+          const float divu = S.dx[P1] * (1.f / 3.f) + (S.dx[P0] + S.dx[P2]) * (1.f / 12.f) +
+                             (S.uy[P0] - S.uy[P2]) * (1.f / 3.f) + (S.sy[P0] - S.sy[P2]) * (1.f / 12.f);
+          const float br = A.b * S.rho1;
+          cf[C_AE] = fmaf(ux, -1.f / 3.f, cE);
+          cf[C_AW] = fmaf(ux, 1.f / 3.f, cW);
+          cf[C_AN] = fmaf(uy, -1.f / 3.f, cN);
+          cf[C_AS] = fmaf(uy, 1.f / 3.f, cS);
+          cf[C_P] = (ux + uy) * (1.f / 12.f);
+          cf[C_Q] = (ux - uy) * (1.f / 12.f);
+          cf[C_AS_T] = divu * (A.R / A.cv) / (1.f - br);
+          cf[C_BS] = divu * (A.a * A.kappa / A.cv) * S.rho1 / fmaf(br, 2.f - br, 1.f);
+        }
+      }
+    }
+    S.rho1 = rho_r;
+  }
+
+  // q_bottom (face 0|1), q_interface (face W-1|W) and q_top (face ny-2|ny-1 under
+  // a top wall) accumulate the RK-weighted conductive flux of every stage
+  auto wall_flux = [&](int y, float wk, float qf, float TS, float Tp, float TN) {
+    if (!C.own_col) return;
+    if (y == 1) ff_add(S.qbh, S.qbl, wk * qf * (TS - Tp));
+    if (y == W) ff_add(S.qih, S.qil, wk * qf * (TS - Tp));
+    if (g.top_wall && y == ny - 2) ff_add(S.qth, S.qtl, wk * qf * (Tp - TN));
+  };
+  auto is_wall_flux_row = [&](int y) -> bool { return y == 1 || y == W || (g.top_wall && y == ny - 2); };
+  const float qc = A.q_in * A.inv_rcv_w;
+
+  // ---- stage 1 at y = r - 1: T^n at rows r - 2 .. r
+  {
+    const int y = r - 1;
+    if (y >= C.ys - 3 && y < C.ye + 3 && y >= 0) {
+      float v;
+      if (y < ny) {
+        const float* s0 = C.sTn + ((r - 2) & (EW_RTN - 1)) * EW_W;
+        const float* s1 = C.sTn + ((r - 1) & (EW_RTN - 1)) * EW_W;
+        const float* s2 = C.sTn + (r & (EW_RTN - 1)) * EW_W;
+        const float Tp = S.tn[P1];
+        const float TS = y > 0 ? S.tn[P2] : Tp;
+        const float TN = S.tn[P0];
+        float kk = walk_K(A, S.cf[P1], Tp, s1[ie], s1[iw], TN, TS, s2[ie], s2[iw], s0[ie], s0[iw]);
+        if (y == 0 && g.bottom_flux) kk += qc;
+        if (is_wall_flux_row(y)) wall_flux(y, dt * (1.f / 6.f), S.qf[P1], TS, Tp, TN);
+        S.acc[P1] = kk;
+        v = fmaf(0.5f * dt, kk, Tp);
+      } else {
+        v = S.t1[P2];  // zero-gradient ghost above an open top: row ny - 1
+      }
+      S.t1[P1] = v;
+      C.sT1[P1 * EW_W + i] = v;
+    }
+  }
+  __syncthreads();
+
+  // ---- stage 2 at y = r - 2: T1 at rows r - 3 .. r - 1
+  {
+    const int y = r - 2;
+    if (y >= C.ys - 2 && y < C.ye + 2 && y >= 0) {
+      float v;
+      if (y < ny) {
+        const float* s0 = C.sT1 + P3 * EW_W;
+        const float* s1 = C.sT1 + P2 * EW_W;
+        const float* s2 = C.sT1 + P1 * EW_W;
+        const float Tp = S.t1[P2];
+        const float TS = y > 0 ? S.t1[P3] : Tp;
+        const float TN = S.t1[P1];
+        float kk = walk_K(A, S.cf[P2], Tp, s1[ie], s1[iw], TN, TS, s2[ie], s2[iw], s0[ie], s0[iw]);
+        if (y == 0 && g.bottom_flux) kk += qc;
+        if (is_wall_flux_row(y)) wall_flux(y, dt * (2.f / 6.f), S.qf[P2], TS, Tp, TN);
+        S.acc[P2] = fmaf(2.f, kk, S.acc[P2]);
+        v = fmaf(0.5f * dt, kk, S.tn[P2]);
+      } else {
+        v = S.t2[P3];
+      }
+      S.t2[P2] = v;
+      C.sT2[P2 * EW_W + i] = v;
+    }
+  }
+  __syncthreads();
+
+  // ---- stage 3 at y = r - 3: T2 at rows r - 4 .. r - 2
+  {
+    const int y = r - 3;
+    if (y >= C.ys - 1 && y < C.ye + 1 && y >= 0) {
+      float v;
+      if (y < ny) {
+        const float* s0 = C.sT2 + P0 * EW_W;  // row r - 4
+        const float* s1 = C.sT2 + P3 * EW_W;
+        const float* s2 = C.sT2 + P2 * EW_W;
+        const float Tp = S.t2[P3];
+        const float TS = y > 0 ? S.t2[P0] : Tp;
+        const float TN = S.t2[P2];
+        float kk = walk_K(A, S.cf[P3], Tp, s1[ie], s1[iw], TN, TS, s2[ie], s2[iw], s0[ie], s0[iw]);
+        if (y == 0 && g.bottom_flux) kk += qc;
+        if (is_wall_flux_row(y)) wall_flux(y, dt * (2.f / 6.f), S.qf[P3], TS, Tp, TN);
+        S.acc[P3] = fmaf(2.f, kk, S.acc[P3]);
+        v = fmaf(dt, kk, S.tn[P3]);
+      } else {
+        v = S.t3[P0];
+      }
+      S.t3[P3] = v;
+      C.sT3[P3 * EW_W + i] = v;
+    }
+  }
+  __syncthreads();
+
+  // ---- stage 4 at y = r - 4: T3 at rows r - 5 .. r - 3; the new temperature
+  {
+    const int y = r - 4;
+    if (y >= C.ys && y < C.ye) {
+      const float* s0 = C.sT3 + P1 * EW_W;  // row r - 5
+      const float* s1 = C.sT3 + P0 * EW_W;
+      const float* s2 = C.sT3 + P3 * EW_W;
+      const float Tp = S.t3[P0];
+      const float TS = y > 0 ? S.t3[P1] : Tp;
+      const float TN = S.t3[P3];
+      float kk = walk_K(A, S.cf[P0], Tp, s1[ie], s1[iw], TN, TS, s2[ie], s2[iw], s0[ie], s0[iw]);
+      if (y == 0 && g.bottom_flux) kk += qc;
+      if (is_wall_flux_row(y)) wall_flux(y, dt * (1.f / 6.f), S.qf[P0], TS, Tp, TN);
+      if (C.own_col) {
+        const float T0 = C.sTn[(y & (EW_RTN - 1)) * EW_W + i];
+        const float Tnew = T0 + dt * (1.f / 6.f) * (S.acc[P0] + kk);
+        if (nonfinite(Tnew)) S.err |= ERR_NONFINITE;
+        C.T_out[y * A.nx + C.gx] = Tnew;
+        if (C.last) ff_add(S.eh, S.el, Tnew * S.rcv[P0]);
+      }
+    }
+  }
+}
+
+// Walk of strip sx, segment sg of one domain.
+template <int L>
+__device__ __forceinline__ void energy_walk(const StepArgs& A, int sx, int sg, int part, float* sm, int s, int nsub) {
+  static_assert(L % 4 == 0, "segments start on a multiple of four rows");
+  __shared__ float s_red[EW_W / 32][NEPART][2];
+  __shared__ int s_err;
+  WalkCtx C;
+  const int NC = A.nx * A.ny;
+  C.T_in = s == 1 ? A.T_in : substep_buffer(A, s - 1, nsub);
+  C.T_out = substep_buffer(A, s, nsub);
+  C.rho_n = A.mom;
+  C.ux_n = A.mom + NC;
+  C.uy_n = A.mom + 2 * NC;
+  C.sTn = sm;
+  C.sT1 = sm + EW_RTN * EW_W;
+  C.sT2 = C.sT1 + EW_R * EW_W;
+  C.sT3 = C.sT2 + EW_R * EW_W;
+  C.sUx = C.sT3 + EW_R * EW_W;
+  C.sUy = C.sUx + EW_R * EW_W;
+  C.sLam = C.sUy + EW_R * EW_W;
+  C.i = threadIdx.x;
+  C.ie = C.i + 1 < EW_W ? C.i + 1 : C.i;  // frame-edge columns read themselves
+  C.iw = C.i > 0 ? C.i - 1 : C.i;
+  const int gxu = sx * EW_OUT - EW_H + C.i;
+  C.gx = wrapx(gxu, A.nx);
+  C.own_col = C.i >= EW_H && C.i < EW_H + EW_OUT && gxu < A.nx;
+  C.ys = sg * L;
+  C.ye = C.ys + L < A.ny ? C.ys + L : A.ny;
+  C.last = s == nsub;
+  if (threadIdx.x == 0) s_err = 0;
+
+  WalkState S;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    S.tn[q] = S.t1[q] = S.t2[q] = S.t3[q] = S.acc[q] = S.rcv[q] = S.qf[q] = 0.f;
+    S.dx[q] = S.sy[q] = S.uy[q] = S.lam[q] = 0.f;
+#pragma unroll
+    for (int c = 0; c < NCOEF; ++c) S.cf[q][c] = 0.f;
+  }
+  S.rho1 = 0.f;
+  S.eh = S.el = S.qbh = S.qbl = S.qih = S.qil = S.qth = S.qtl = 0.f;
+  S.err = 0;
+  const int t0 = C.ys - 4;  // a multiple of four: t & 3 is the unrolled phase
+  walk_load(A, C, S, t0);
+  for (int t = t0; t < C.ye + 4; t += 4) {
+    walk_step<0>(A, C, S, t);
+    walk_step<1>(A, C, S, t + 1);
+    walk_step<2>(A, C, S, t + 2);
+    walk_step<3>(A, C, S, t + 3);
+  }
+  float ah[NEPART] = {S.qbh, S.qth, S.qih, S.eh}, al[NEPART] = {S.qbl, S.qtl, S.qil, S.el};
+  if (S.err) atomicOr(&s_err, S.err);
+  block_partials<EW_W, NEPART>(ah, al, s_red, A.epart + (long long)part * NEPART, s > 1);
+  if (threadIdx.x == 0 && s_err) atomicOr(&A.state->error_flags, s_err);
+}
+
+template <int L>
+__global__ void __launch_bounds__(EW_W, 8) k_energy_walk(const StepArgs A, int s, int nsub) {
+  __shared__ float sm[EW_SMEM_FLOATS];
+  energy_walk<L>(A, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, sm, s, nsub);
+}
+
+template <int L>
+__global__ void __launch_bounds__(EW_W, 8) k_energy_walk_batch(const StepArgs P, const DomArgs* __restrict__ desc,
+                                                               const int2* __restrict__ blk,
+                                                               const int* __restrict__ active, int s, int nsub) {
+  __shared__ float sm[EW_SMEM_FLOATS];
+  __shared__ DomArgs sD;
+  __shared__ int s_act;
+  __shared__ int2 s_bl;
+  __shared__ float2 s_lg;
+  if (!batch_prologue<EW_W>(desc, blk, active, nullptr, sD, s_bl, s_lg, s_act)) return;
+  StepArgs A = P;
+  apply_dom(A, sD);
+  const int local = s_bl.y;
+  const int strips = (A.nx + EW_OUT - 1) / EW_OUT;
+  energy_walk<L>(A, local % strips, local / strips, local, sm, s, nsub);
+}
+
+}  // namespace hlb
