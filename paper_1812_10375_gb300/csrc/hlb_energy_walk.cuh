@@ -30,6 +30,12 @@ constexpr int EW_RTN = 8;     // depth of the T^n ring
 constexpr int EW_R = 4;       // depth of the other rings
 // shared floats: T^n ring, three stage rings, u_x, u_y, lambda rings
 constexpr int EW_SMEM_FLOATS = (EW_RTN + 6 * EW_R) * EW_W;
+constexpr int EW_OFF_TN = 0, EW_OFF_T1 = EW_RTN * EW_W, EW_OFF_T2 = EW_OFF_T1 + EW_R * EW_W,
+              EW_OFF_T3 = EW_OFF_T2 + EW_R * EW_W, EW_OFF_UX = EW_OFF_T3 + EW_R * EW_W,
+              EW_OFF_UY = EW_OFF_UX + EW_R * EW_W, EW_OFF_LAM = EW_OFF_UY + EW_R * EW_W;
+// The rings of the walking kernels, at a fixed layout so that every access is
+// an immediate offset from one shared-memory base.
+__shared__ float s_walk[EW_SMEM_FLOATS];
 
 // Per-thread state of the walk.  Arrays indexed [row & 3] are row rings; the
 // walk is unrolled by four so that every index is a compile-time constant.
@@ -53,13 +59,6 @@ struct WalkCtx {
   const float* rho_n;
   const float* ux_n;
   const float* uy_n;
-  float* sTn;
-  float* sT1;
-  float* sT2;
-  float* sT3;
-  float* sUx;
-  float* sUy;
-  float* sLam;
   int i, ie, iw, gx;
   bool own_col;
   int ys, ye;  // output rows of the segment
@@ -79,7 +78,16 @@ __device__ __forceinline__ float walk_K(const StepArgs& A, const float* c, float
   return kk - fmaf(c[C_AS_T], Tp, c[C_BS] * sTr * fmaf(-A.kappa, sTr, 1.f + A.kappa));
 }
 
+template <bool STEADY>
 __device__ __forceinline__ void walk_load(const StepArgs& A, const WalkCtx& C, WalkState& S, int row) {
+  if (STEADY) {  // an interior fluid row
+    const int c = row * A.nx + C.gx;
+    S.pT = __ldg(C.T_in + c);
+    S.pR = __ldg(C.rho_n + c);
+    S.pUx = __ldg(C.ux_n + c);
+    S.pUy = __ldg(C.uy_n + c);
+    return;
+  }
   S.pT = S.pR = S.pUx = S.pUy = 0.f;
   if (row < 0) return;
   const Geo g = make_geo(A);
@@ -93,7 +101,12 @@ __device__ __forceinline__ void walk_load(const StepArgs& A, const WalkCtx& C, W
   }
 }
 
-template <int P>
+#define SW(off, slot, col) s_walk[(off) + (slot) * EW_W + (col)]
+
+// One walk step.  STEADY: an interior segment past its first eight steps:
+// every phase is active and no row of the step is solid, Dirichlet, a ghost,
+// a wall-flux row or the top row, so all row tests compile away.
+template <int P, bool STEADY>
 __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, WalkState& S, int t) {
   constexpr int P0 = P & 3, P1 = (P + 3) & 3, P2 = (P + 2) & 3, P3 = (P + 1) & 3;  // rows r, r-1, r-2, r-3
   const Geo g = make_geo(A);
@@ -105,48 +118,53 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
 
   // ---- load phase: row r (prefetched) into the rings; prefetch row r + 1
   {
-    const int gr = r < ny ? r : ny - 1;
-    const bool solid = r >= 0 && g.solid_row(gr);
-    const float lam = r < 0 ? A.lambda_w : (solid ? wall_lam(gr) : S.pR * A.cvk);
+    float lam;
+    if (STEADY) {
+      lam = S.pR * A.cvk;
+    } else {
+      const int gr = r < ny ? r : ny - 1;
+      const bool solid = r >= 0 && g.solid_row(gr);
+      lam = r < 0 ? A.lambda_w : (solid ? wall_lam(gr) : S.pR * A.cvk);
+    }
     S.tn[P0] = S.pT;
     S.lam[P0] = lam;
     S.uy[P0] = S.pUy;
-    C.sTn[(r & (EW_RTN - 1)) * EW_W + i] = S.pT;
-    C.sUx[P0 * EW_W + i] = S.pUx;
-    C.sUy[P0 * EW_W + i] = S.pUy;
-    C.sLam[P0 * EW_W + i] = lam;
+    SW(EW_OFF_TN, r & (EW_RTN - 1), i) = S.pT;
+    SW(EW_OFF_UX, P0, i) = S.pUx;
+    SW(EW_OFF_UY, P0, i) = S.pUy;
+    SW(EW_OFF_LAM, P0, i) = lam;
     const float rho_r = S.pR;
-    walk_load(A, C, S, r + 1);
+    walk_load<STEADY>(A, C, S, r + 1);
     __syncthreads();
-    S.dx[P0] = C.sUx[P0 * EW_W + ie] - C.sUx[P0 * EW_W + iw];
-    S.sy[P0] = C.sUy[P0 * EW_W + ie] + C.sUy[P0 * EW_W + iw];
+    S.dx[P0] = SW(EW_OFF_UX, P0, ie) - SW(EW_OFF_UX, P0, iw);
+    S.sy[P0] = SW(EW_OFF_UY, P0, ie) + SW(EW_OFF_UY, P0, iw);
     // ---- coefficients of row y = r - 1 (ring 3 of the segment)
     const int y = r - 1;
-    if (y >= C.ys - 3 && y < C.ye + 3 && y >= 0 && y < ny) {
+    if (STEADY || (y >= C.ys - 3 && y < C.ye + 3 && y >= 0 && y < ny)) {
       float* cf = S.cf[P1];
 #pragma unroll
       for (int q = 0; q < NCOEF; ++q) cf[q] = 0.f;
-      const bool ysolid = g.solid_row(y);
+      const bool ysolid = !STEADY && g.solid_row(y);
       S.rcv[P1] = ysolid ? A.rcv_w : S.rho1 * A.cv;
       const float l = S.lam[P1];
-      const float lS = y > 0 ? S.lam[P2] : l;
-      S.qf[P1] = y == ny - 2 ? harm(l, S.lam[P0]) : harm(l, lS);
-      if (!g.dirichlet_row(y)) {
+      const float lS = (STEADY || y > 0) ? S.lam[P2] : l;
+      if (!STEADY) S.qf[P1] = y == ny - 2 ? harm(l, S.lam[P0]) : harm(l, lS);
+      if (STEADY || !g.dirichlet_row(y)) {
         // lambda_f / (rho cv) = 2 kd lambda_nb / (lambda + lambda_nb), kd = lambda / (rho cv) of the row
         const float kd = ysolid ? l * A.inv_rcv_w : A.kd;
-        const float lE = C.sLam[P1 * EW_W + ie], lW = C.sLam[P1 * EW_W + iw];
-        const float lN = (g.top_open && y == ny - 1) ? l : S.lam[P0];
+        const float lE = SW(EW_OFF_LAM, P1, ie), lW = SW(EW_OFF_LAM, P1, iw);
+        const float lN = (!STEADY && g.top_open && y == ny - 1) ? l : S.lam[P0];
         const float cE = 2.f * kd * lE / (l + lE), cW = 2.f * kd * lW / (l + lW);
         const float cN = 2.f * kd * lN / (l + lN);
         // row 0 under an imposed flux: no conductive flux through its bottom face
-        const float cS = y == 0 ? 0.f : 2.f * kd * lS / (l + lS);
+        const float cS = (!STEADY && y == 0) ? 0.f : 2.f * kd * lS / (l + lS);
         if (ysolid) {
           cf[C_AE] = cE;
           cf[C_AW] = cW;
           cf[C_AN] = cN;
           cf[C_AS] = cS;
         } else {
-          const float ux = C.sUx[P1 * EW_W + i], uy = S.uy[P1];
+          const float ux = SW(EW_OFF_UX, P1, i), uy = S.uy[P1];
           const float divu = S.dx[P1] * (1.f / 3.f) + (S.dx[P0] + S.dx[P2]) * (1.f / 12.f) +
                              (S.uy[P0] - S.uy[P2]) * (1.f / 3.f) + (S.sy[P0] - S.sy[P2]) * (1.f / 12.f);
           const float br = A.b * S.rho1;
@@ -167,36 +185,40 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
   // q_bottom (face 0|1), q_interface (face W-1|W) and q_top (face ny-2|ny-1 under
   // a top wall) accumulate the RK-weighted conductive flux of every stage
   auto wall_flux = [&](int y, float wk, float qf, float TS, float Tp, float TN) {
-    if (!C.own_col) return;
+    if (STEADY || !C.own_col) return;
     if (y == 1) ff_add(S.qbh, S.qbl, wk * qf * (TS - Tp));
     if (y == W) ff_add(S.qih, S.qil, wk * qf * (TS - Tp));
     if (g.top_wall && y == ny - 2) ff_add(S.qth, S.qtl, wk * qf * (Tp - TN));
   };
-  auto is_wall_flux_row = [&](int y) -> bool { return y == 1 || y == W || (g.top_wall && y == ny - 2); };
+  auto special = [&](int y) -> bool {
+    return !STEADY && (y == 1 || y == W || (g.top_wall && y == ny - 2) || (y == 0 && g.bottom_flux));
+  };
   const float qc = A.q_in * A.inv_rcv_w;
 
   // ---- stage 1 at y = r - 1: T^n at rows r - 2 .. r
   {
     const int y = r - 1;
-    if (y >= C.ys - 3 && y < C.ye + 3 && y >= 0) {
+    if (STEADY || (y >= C.ys - 3 && y < C.ye + 3 && y >= 0)) {
       float v;
-      if (y < ny) {
-        const float* s0 = C.sTn + ((r - 2) & (EW_RTN - 1)) * EW_W;
-        const float* s1 = C.sTn + ((r - 1) & (EW_RTN - 1)) * EW_W;
-        const float* s2 = C.sTn + (r & (EW_RTN - 1)) * EW_W;
+      if (STEADY || y < ny) {
+        const int lo = EW_OFF_TN + ((r - 2) & (EW_RTN - 1)) * EW_W, mid = EW_OFF_TN + ((r - 1) & (EW_RTN - 1)) * EW_W,
+                  hi = EW_OFF_TN + (r & (EW_RTN - 1)) * EW_W;
         const float Tp = S.tn[P1];
-        const float TS = y > 0 ? S.tn[P2] : Tp;
+        const float TS = (STEADY || y > 0) ? S.tn[P2] : Tp;
         const float TN = S.tn[P0];
-        float kk = walk_K(A, S.cf[P1], Tp, s1[ie], s1[iw], TN, TS, s2[ie], s2[iw], s0[ie], s0[iw]);
-        if (y == 0 && g.bottom_flux) kk += qc;
-        if (is_wall_flux_row(y)) wall_flux(y, dt * (1.f / 6.f), S.qf[P1], TS, Tp, TN);
+        float kk = walk_K(A, S.cf[P1], Tp, s_walk[mid + ie], s_walk[mid + iw], TN, TS, s_walk[hi + ie],
+                          s_walk[hi + iw], s_walk[lo + ie], s_walk[lo + iw]);
+        if (special(y)) {
+          if (y == 0 && g.bottom_flux) kk += qc;
+          wall_flux(y, dt * (1.f / 6.f), S.qf[P1], TS, Tp, TN);
+        }
         S.acc[P1] = kk;
         v = fmaf(0.5f * dt, kk, Tp);
       } else {
         v = S.t1[P2];  // zero-gradient ghost above an open top: row ny - 1
       }
       S.t1[P1] = v;
-      C.sT1[P1 * EW_W + i] = v;
+      SW(EW_OFF_T1, P1, i) = v;
     }
   }
   __syncthreads();
@@ -204,25 +226,26 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
   // ---- stage 2 at y = r - 2: T1 at rows r - 3 .. r - 1
   {
     const int y = r - 2;
-    if (y >= C.ys - 2 && y < C.ye + 2 && y >= 0) {
+    if (STEADY || (y >= C.ys - 2 && y < C.ye + 2 && y >= 0)) {
       float v;
-      if (y < ny) {
-        const float* s0 = C.sT1 + P3 * EW_W;
-        const float* s1 = C.sT1 + P2 * EW_W;
-        const float* s2 = C.sT1 + P1 * EW_W;
+      if (STEADY || y < ny) {
+        const int lo = EW_OFF_T1 + P3 * EW_W, mid = EW_OFF_T1 + P2 * EW_W, hi = EW_OFF_T1 + P1 * EW_W;
         const float Tp = S.t1[P2];
-        const float TS = y > 0 ? S.t1[P3] : Tp;
+        const float TS = (STEADY || y > 0) ? S.t1[P3] : Tp;
         const float TN = S.t1[P1];
-        float kk = walk_K(A, S.cf[P2], Tp, s1[ie], s1[iw], TN, TS, s2[ie], s2[iw], s0[ie], s0[iw]);
-        if (y == 0 && g.bottom_flux) kk += qc;
-        if (is_wall_flux_row(y)) wall_flux(y, dt * (2.f / 6.f), S.qf[P2], TS, Tp, TN);
+        float kk = walk_K(A, S.cf[P2], Tp, s_walk[mid + ie], s_walk[mid + iw], TN, TS, s_walk[hi + ie],
+                          s_walk[hi + iw], s_walk[lo + ie], s_walk[lo + iw]);
+        if (special(y)) {
+          if (y == 0 && g.bottom_flux) kk += qc;
+          wall_flux(y, dt * (2.f / 6.f), S.qf[P2], TS, Tp, TN);
+        }
         S.acc[P2] = fmaf(2.f, kk, S.acc[P2]);
         v = fmaf(0.5f * dt, kk, S.tn[P2]);
       } else {
         v = S.t2[P3];
       }
       S.t2[P2] = v;
-      C.sT2[P2 * EW_W + i] = v;
+      SW(EW_OFF_T2, P2, i) = v;
     }
   }
   __syncthreads();
@@ -230,25 +253,26 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
   // ---- stage 3 at y = r - 3: T2 at rows r - 4 .. r - 2
   {
     const int y = r - 3;
-    if (y >= C.ys - 1 && y < C.ye + 1 && y >= 0) {
+    if (STEADY || (y >= C.ys - 1 && y < C.ye + 1 && y >= 0)) {
       float v;
-      if (y < ny) {
-        const float* s0 = C.sT2 + P0 * EW_W;  // row r - 4
-        const float* s1 = C.sT2 + P3 * EW_W;
-        const float* s2 = C.sT2 + P2 * EW_W;
+      if (STEADY || y < ny) {
+        const int lo = EW_OFF_T2 + P0 * EW_W, mid = EW_OFF_T2 + P3 * EW_W, hi = EW_OFF_T2 + P2 * EW_W;
         const float Tp = S.t2[P3];
-        const float TS = y > 0 ? S.t2[P0] : Tp;
+        const float TS = (STEADY || y > 0) ? S.t2[P0] : Tp;
         const float TN = S.t2[P2];
-        float kk = walk_K(A, S.cf[P3], Tp, s1[ie], s1[iw], TN, TS, s2[ie], s2[iw], s0[ie], s0[iw]);
-        if (y == 0 && g.bottom_flux) kk += qc;
-        if (is_wall_flux_row(y)) wall_flux(y, dt * (2.f / 6.f), S.qf[P3], TS, Tp, TN);
+        float kk = walk_K(A, S.cf[P3], Tp, s_walk[mid + ie], s_walk[mid + iw], TN, TS, s_walk[hi + ie],
+                          s_walk[hi + iw], s_walk[lo + ie], s_walk[lo + iw]);
+        if (special(y)) {
+          if (y == 0 && g.bottom_flux) kk += qc;
+          wall_flux(y, dt * (2.f / 6.f), S.qf[P3], TS, Tp, TN);
+        }
         S.acc[P3] = fmaf(2.f, kk, S.acc[P3]);
         v = fmaf(dt, kk, S.tn[P3]);
       } else {
         v = S.t3[P0];
       }
       S.t3[P3] = v;
-      C.sT3[P3 * EW_W + i] = v;
+      SW(EW_OFF_T3, P3, i) = v;
     }
   }
   __syncthreads();
@@ -256,18 +280,19 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
   // ---- stage 4 at y = r - 4: T3 at rows r - 5 .. r - 3; the new temperature
   {
     const int y = r - 4;
-    if (y >= C.ys && y < C.ye) {
-      const float* s0 = C.sT3 + P1 * EW_W;  // row r - 5
-      const float* s1 = C.sT3 + P0 * EW_W;
-      const float* s2 = C.sT3 + P3 * EW_W;
+    if (STEADY || (y >= C.ys && y < C.ye)) {
+      const int lo = EW_OFF_T3 + P1 * EW_W, mid = EW_OFF_T3 + P0 * EW_W, hi = EW_OFF_T3 + P3 * EW_W;
       const float Tp = S.t3[P0];
-      const float TS = y > 0 ? S.t3[P1] : Tp;
+      const float TS = (STEADY || y > 0) ? S.t3[P1] : Tp;
       const float TN = S.t3[P3];
-      float kk = walk_K(A, S.cf[P0], Tp, s1[ie], s1[iw], TN, TS, s2[ie], s2[iw], s0[ie], s0[iw]);
-      if (y == 0 && g.bottom_flux) kk += qc;
-      if (is_wall_flux_row(y)) wall_flux(y, dt * (1.f / 6.f), S.qf[P0], TS, Tp, TN);
+      float kk = walk_K(A, S.cf[P0], Tp, s_walk[mid + ie], s_walk[mid + iw], TN, TS, s_walk[hi + ie],
+                        s_walk[hi + iw], s_walk[lo + ie], s_walk[lo + iw]);
+      if (special(y)) {
+        if (y == 0 && g.bottom_flux) kk += qc;
+        wall_flux(y, dt * (1.f / 6.f), S.qf[P0], TS, Tp, TN);
+      }
       if (C.own_col) {
-        const float T0 = C.sTn[(y & (EW_RTN - 1)) * EW_W + i];
+        const float T0 = SW(EW_OFF_TN, y & (EW_RTN - 1), i);
         const float Tnew = T0 + dt * (1.f / 6.f) * (S.acc[P0] + kk);
         if (nonfinite(Tnew)) S.err |= ERR_NONFINITE;
         C.T_out[y * A.nx + C.gx] = Tnew;
@@ -276,11 +301,10 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
     }
   }
 }
+#undef SW
 
-// Walk of strip sx, segment sg of one domain.
-template <int L>
-__device__ __forceinline__ void energy_walk(const StepArgs& A, int sx, int sg, int part, float* sm, int s, int nsub) {
-  static_assert(L % 4 == 0, "segments start on a multiple of four rows");
+// Walk of strip sx, segment sg (rows [sg L, sg L + L)) of one domain.
+__device__ __forceinline__ void energy_walk(const StepArgs& A, int L, int sx, int sg, int part, int s, int nsub) {
   __shared__ float s_red[EW_W / 32][NEPART][2];
   __shared__ int s_err;
   WalkCtx C;
@@ -290,13 +314,6 @@ __device__ __forceinline__ void energy_walk(const StepArgs& A, int sx, int sg, i
   C.rho_n = A.mom;
   C.ux_n = A.mom + NC;
   C.uy_n = A.mom + 2 * NC;
-  C.sTn = sm;
-  C.sT1 = sm + EW_RTN * EW_W;
-  C.sT2 = C.sT1 + EW_R * EW_W;
-  C.sT3 = C.sT2 + EW_R * EW_W;
-  C.sUx = C.sT3 + EW_R * EW_W;
-  C.sUy = C.sUx + EW_R * EW_W;
-  C.sLam = C.sUy + EW_R * EW_W;
   C.i = threadIdx.x;
   C.ie = C.i + 1 < EW_W ? C.i + 1 : C.i;  // frame-edge columns read themselves
   C.iw = C.i > 0 ? C.i - 1 : C.i;
@@ -320,12 +337,24 @@ __device__ __forceinline__ void energy_walk(const StepArgs& A, int sx, int sg, i
   S.eh = S.el = S.qbh = S.qbl = S.qih = S.qil = S.qth = S.qtl = 0.f;
   S.err = 0;
   const int t0 = C.ys - 4;  // a multiple of four: t & 3 is the unrolled phase
-  walk_load(A, C, S, t0);
+  walk_load<false>(A, C, S, t0);
+  // Steps t .. t+3 touch rows t - 5 .. t + 4.  They run in the steady form when
+  // every phase of each is active (t >= ys + 4, t + 3 < ye + 4) and those rows
+  // are fluid rows at least two rows from the wall rows and three from the top
+  // (no solid, Dirichlet, ghost, top or wall-flux row).
+  const int t_lo = max(C.ys + 4, A.W + 7), t_hi = min(C.ye, A.ny - 7);  // steady groups: t_lo <= t <= t_hi
   for (int t = t0; t < C.ye + 4; t += 4) {
-    walk_step<0>(A, C, S, t);
-    walk_step<1>(A, C, S, t + 1);
-    walk_step<2>(A, C, S, t + 2);
-    walk_step<3>(A, C, S, t + 3);
+    if (t >= t_lo && t <= t_hi) {
+      walk_step<0, true>(A, C, S, t);
+      walk_step<1, true>(A, C, S, t + 1);
+      walk_step<2, true>(A, C, S, t + 2);
+      walk_step<3, true>(A, C, S, t + 3);
+    } else {
+      walk_step<0, false>(A, C, S, t);
+      walk_step<1, false>(A, C, S, t + 1);
+      walk_step<2, false>(A, C, S, t + 2);
+      walk_step<3, false>(A, C, S, t + 3);
+    }
   }
   float ah[NEPART] = {S.qbh, S.qth, S.qih, S.eh}, al[NEPART] = {S.qbl, S.qtl, S.qil, S.el};
   if (S.err) atomicOr(&s_err, S.err);
@@ -335,15 +364,15 @@ __device__ __forceinline__ void energy_walk(const StepArgs& A, int sx, int sg, i
 
 template <int L>
 __global__ void __launch_bounds__(EW_W, 8) k_energy_walk(const StepArgs A, int s, int nsub) {
-  __shared__ float sm[EW_SMEM_FLOATS];
-  energy_walk<L>(A, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, sm, s, nsub);
+  static_assert(L % 4 == 0, "segments start on a multiple of four rows");
+  energy_walk(A, L, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, s, nsub);
 }
 
 template <int L>
 __global__ void __launch_bounds__(EW_W, 8) k_energy_walk_batch(const StepArgs P, const DomArgs* __restrict__ desc,
                                                                const int2* __restrict__ blk,
                                                                const int* __restrict__ active, int s, int nsub) {
-  __shared__ float sm[EW_SMEM_FLOATS];
+  static_assert(L % 4 == 0, "segments start on a multiple of four rows");
   __shared__ DomArgs sD;
   __shared__ int s_act;
   __shared__ int2 s_bl;
@@ -353,7 +382,7 @@ __global__ void __launch_bounds__(EW_W, 8) k_energy_walk_batch(const StepArgs P,
   apply_dom(A, sD);
   const int local = s_bl.y;
   const int strips = (A.nx + EW_OUT - 1) / EW_OUT;
-  energy_walk<L>(A, local % strips, local / strips, local, sm, s, nsub);
+  energy_walk(A, L, local % strips, local / strips, local, s, nsub);
 }
 
 }  // namespace hlb
