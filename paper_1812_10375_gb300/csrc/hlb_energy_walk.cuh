@@ -362,14 +362,14 @@ __device__ __forceinline__ void energy_walk(const StepArgs& A, int L, int sx, in
   if (threadIdx.x == 0 && s_err) atomicOr(&A.state->error_flags, s_err);
 }
 
-template <int L>
-__global__ void __launch_bounds__(EW_W, 8) k_energy_walk(const StepArgs A, int s, int nsub) {
+template <int L, int MINB>
+__global__ void __launch_bounds__(EW_W, MINB) k_energy_walk(const StepArgs A, int s, int nsub) {
   static_assert(L % 4 == 0, "segments start on a multiple of four rows");
   energy_walk(A, L, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, s, nsub);
 }
 
-template <int L>
-__global__ void __launch_bounds__(EW_W, 8) k_energy_walk_batch(const StepArgs P, const DomArgs* __restrict__ desc,
+template <int L, int MINB>
+__global__ void __launch_bounds__(EW_W, MINB) k_energy_walk_batch(const StepArgs P, const DomArgs* __restrict__ desc,
                                                                const int2* __restrict__ blk,
                                                                const int* __restrict__ active, int s, int nsub) {
   static_assert(L % 4 == 0, "segments start on a multiple of four rows");
