@@ -152,14 +152,20 @@ def parse_clock_lines(lines):
         parts = [p.strip() for p in ln.split(",")]
         if len(parts) < 7:
             continue
-        try:
-            sm.append(float(parts[0]))
-            smax = float(parts[1])
-        except ValueError:
-            continue
+        # throttle reasons count whenever the line has its seven fields, even
+        # if a clock field is not a number ("[N/A]")
         for nm, v in zip(names, parts[3:7]):
             if v.lower() == "active":
                 reasons.add(nm)
+        try:
+            clk = float(parts[0])
+        except ValueError:
+            continue
+        sm.append(clk)
+        try:
+            smax = float(parts[1])
+        except ValueError:
+            pass
     return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
             "reasons": sorted(reasons), "samples": len(sm)}
 

@@ -336,6 +336,13 @@ __device__ __forceinline__ void energy_walk(const StepArgs& A, int L, int sx, in
   S.rho1 = 0.f;
   S.eh = S.el = S.qbh = S.qbl = S.qih = S.qil = S.qth = S.qtl = 0.f;
   S.err = 0;
+  // The stage rings of row -1 are read (times a zero coefficient) by row 0 of
+  // the first segment but never written: start them at zero, not at whatever an
+  // earlier kernel left in shared memory (a NaN there would survive 0 * NaN).
+  // Each thread clears its own column; the first step's barrier orders these
+  // stores before any read.
+#pragma unroll
+  for (int q = 0; q < 3 * EW_R; ++q) s_walk[EW_OFF_T1 + q * EW_W + C.i] = 0.f;
   const int t0 = C.ys - 4;  // a multiple of four: t & 3 is the unrolled phase
   walk_load<false>(A, C, S, t0);
   // Steps t .. t+3 touch rows t - 5 .. t + 4.  They run in the steady form when

@@ -247,3 +247,37 @@ class Ensemble:
         mean = qs.mean(axis=0)
         spread = (qs.max(axis=0) - qs.min(axis=0)) / np.maximum(np.abs(mean), 1e-12)
         return mean, spread, np.mean(np.stack(ps), axis=0)
+
+    _CFG = ("L0", "C1", "C2", "C3", "K", "S", "NS", "H", "NOUT")
+
+    def save(self, path, **meta):
+        """Weights, input/target scaling and configuration of every member, plus
+        scalar metadata (the frozen early-stop policy), as one .npz file."""
+        arrays = {f"m{k}_params": m.net.params.cpu().numpy() for k, m in enumerate(self.members)}
+        for k, m in enumerate(self.members):
+            sc = m.scaler
+            arrays[f"m{k}_scaler"] = np.concatenate([[sc.h_mean, sc.h_std], sc.s_mean, sc.s_std,
+                                                     [sc.t_mean, sc.t_std]])
+        cfg = self.members[0].net.cfg
+        arrays["cfg"] = np.array([getattr(cfg, f) for f in self._CFG], dtype=np.int64)
+        np.savez(path, members=len(self.members), **arrays, **{k: np.asarray(v) for k, v in meta.items()})
+
+    @classmethod
+    def load(cls, path, max_batch=256):
+        """(ensemble, metadata dict) from a file written by save()."""
+        import torch
+        z = np.load(path)
+        cfg = default_config()
+        for f, v in zip(cls._CFG, z["cfg"]):
+            setattr(cfg, f, int(v))
+        n = int(z["members"])
+        ens = cls(members=n, cfg=cfg, max_batch=max_batch)
+        for k, m in enumerate(ens.members):
+            m.net.params.copy_(torch.tensor(z[f"m{k}_params"], dtype=torch.float32, device="cuda"))
+            v = z[f"m{k}_scaler"]
+            ns = (len(v) - 4) // 2
+            m.scaler = Scaler(float(v[0]), float(v[1]), v[2:2 + ns].copy(), v[2 + ns:2 + 2 * ns].copy(),
+                              float(v[-2]), float(v[-1]))
+        skip = {"members", "cfg"} | {f"m{k}_params" for k in range(n)} | {f"m{k}_scaler" for k in range(n)}
+        meta = {k: z[k][()] for k in z.files if k not in skip}
+        return ens, meta

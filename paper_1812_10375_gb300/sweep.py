@@ -396,6 +396,187 @@ def evaluate_policy(ens, results, L0, threshold, hist_steps, full_steps, cells, 
     return acc, err[acc], float(spent.sum() / (full_steps * cells.sum()))
 
 
+# ------------------------------------------------------------------ frozen policy and points/hour
+POLICY_FILE = "surrogate_policy.npz"  # in the package directory, written by train_policy
+TRAIN_SEED = wl.BASE_SEED          # the training and calibration points
+STUDY_SEED = wl.BASE_SEED + 7777    # fresh points for the points/hour measurement
+
+
+def policy_path() -> str:
+    import os
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), POLICY_FILE)
+
+
+def train_policy(n=256, full=40000, hist_steps=5000, n_fit=160, members=4, epochs=600, tol=0.02, out=None,
+                 cache=None):
+    """Train the early-stop ensemble and freeze its policy on calibration data.
+
+    n sweep points (seed TRAIN_SEED, sides 256-512) run `full` steps in one
+    batch; the ensemble is fitted by the CUDA kernels on the first n_fit; on
+    the remaining points (calibration only) the policy kind ('no_boiling' or
+    'not_film'), the score threshold and the ensemble-spread limit are chosen
+    that accept the most calibration points with every accepted one within
+    `tol` of its full run (2%, under the 3% bar, to leave room for unseen
+    points).  Writes the ensemble and the policy to `out` (policy_path())."""
+    import os
+    from .surrogate import Ensemble
+    pts = make_points(n, seed=TRAIN_SEED)
+    if cache and os.path.exists(cache):
+        res = _load_results(cache, pts)
+    else:
+        res, _ = run_batched(pts, full, hist_steps)
+        if cache:
+            _save_results(cache, res)
+    fit, cal = res[:n_fit], res[n_fit:]
+    ens = Ensemble(members=members, seed=3, max_batch=max(n_fit, 64))
+    L0 = ens.members[0].net.cfg.L0
+    hist, scal, q, lab = features(fit, L0)
+    ens.fit(hist, scal, q, lab, epochs=epochs, batch=64, lr=1e-3)
+    best = None
+    for kind in ("no_boiling", "not_film"):
+        thr, smax = choose_policy(ens, cal, L0, tol=tol, kind=kind)
+        acc, err, _ = evaluate_policy(ens, cal, L0, thr, hist_steps, full, [r.case.nx * r.case.ny for r in cal],
+                                      spread_max=smax, kind=kind)
+        if best is None or int(acc.sum()) > best[3]:
+            best = (kind, thr, smax, int(acc.sum()), float(err.max()) if len(err) else 0.0)
+    kind, thr, smax, n_acc, e_max = best
+    meta = dict(kind=kind, threshold=thr, spread_max=smax, hist_steps=hist_steps, full_steps=full, tol=tol,
+                calibration_points=len(cal), calibration_accepted=n_acc, calibration_max_error=e_max,
+                train_seed=TRAIN_SEED, fit_points=n_fit)
+    ens.save(out or policy_path(), **meta)
+    return meta
+
+
+def _q_second_half(h):
+    n = len(h)
+    return float(np.mean(h[n // 2:])) if n >= 2 else float("nan")
+
+
+def pph_study(n=32, full=40000, slots_per_size=None, seed=STUDY_SEED, policy=None):
+    """Boiling-curve points per hour, measured in three arms on n fresh points
+    (seed STUDY_SEED, C4-shaped: square sides 256-512, 3-9 sites, superheats
+    0.02-0.30 Tc), each point `full` steps unless stopped early:
+
+    plain      one domain at a time (graph-captured single-domain steps);
+    batched    a batch whose slots hold half of each size's points; a slot is
+               refilled with the next point of its size when its point ends
+               at `full` steps;
+    surrogate  the same slots; after `hist_steps` steps the frozen policy
+               (train_policy) either accepts a point, whose prediction is
+               then its result and whose slot is refilled at once, or lets
+               it run to `full`.
+
+    The timed regions cover stepping, refills, history reads and policy
+    calls; creating the domains or batch and their first fields is set-up,
+    timed separately and excluded from all three arms.  The batched arm gives
+    the full-run wall flux of every point, against which the surrogate arm's
+    accepted points are checked."""
+    import torch
+    from .surrogate import Ensemble
+    ens, meta = Ensemble.load(policy or policy_path())
+    kind, thr = str(meta["kind"]), float(meta["threshold"])
+    smax, hs = float(meta["spread_max"]), int(meta["hist_steps"])
+    L0 = ens.members[0].net.cfg.L0
+    pts = make_points(n, seed=seed)
+    sizes = sorted(set(c.nx for c in pts))
+    by_size = {s: [k for k, c in enumerate(pts) if c.nx == s] for s in sizes}
+    nslot = {s: max(1, (len(v) + 1) // 2) if slots_per_size is None else min(slots_per_size, len(v))
+             for s, v in by_size.items()}
+    params = [params_for(c) for c in pts]
+
+    # ---- plain: one domain at a time
+    t_plain = setup_plain = 0.0
+    for k, c in enumerate(pts):
+        p, Tc = params[k]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d = hlb.Domain(p)
+        _setup_domain(d, c, p, Tc)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        d.step(full)
+        d.diag(check_flags=False)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        d.close()
+        setup_plain += t1 - t0
+        t_plain += t2 - t1
+
+    def slot_arm(use_policy):
+        """Run all points through the slots; returns (seconds, set-up seconds, per-point record)."""
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        slot_pts = []  # point of each slot
+        for s in sizes:
+            slot_pts += by_size[s][:nslot[s]]
+        queue = {s: list(by_size[s][nslot[s]:]) for s in sizes}
+        b = hlb.Batch([params[k][0] for k in slot_pts])
+        for i, k in enumerate(slot_pts):
+            _setup(b, i, pts[k], params[k][0], params[k][1])
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        age = [0] * len(slot_pts)
+        rec = {}
+        live = set(range(len(slot_pts)))
+        chunk = hs if use_policy else full
+        while live:
+            step = min(chunk - age[i] % chunk if age[i] < full else 0 for i in live) or chunk
+            b.step(step)
+            for i in list(live):
+                age[i] += step
+                k = slot_pts[i]
+                done = None
+                if age[i] >= full:
+                    h = b.flux_history(i)
+                    done = dict(q=_q_second_half(h[:full]), steps=full, accepted=False)
+                elif use_policy and age[i] == hs:
+                    h = b.flux_history(i)[:hs]
+                    c = pts[k]
+                    hist = downsample(h, L0)[None]
+                    scal = np.array([[c.T_bottom_over_Tc - wl.TS_OVER_TC, len(c.sites) / 10.0]])
+                    qp, spread, prob = ens.predict(hist, scal)
+                    if policy_score(prob, kind)[0] >= thr and spread[0] <= smax:
+                        done = dict(q=float(qp[0]), steps=hs, accepted=True)
+                if done is None:
+                    continue
+                rec[k] = done
+                s = pts[k].nx
+                if queue[s]:
+                    nk = queue[s].pop(0)
+                    slot_pts[i] = nk
+                    p, Tc = params[nk]
+                    b.set_wall(i, p.T_bottom)
+                    _setup(b, i, pts[nk], p, Tc)
+                    age[i] = 0
+                else:
+                    b.stop(i)
+                    live.discard(i)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        b.close()
+        return t2 - t1, t1 - t0, rec
+
+    t_batch, setup_batch, full_rec = slot_arm(False)
+    t_sur, setup_sur, sur_rec = slot_arm(True)
+    acc = [k for k, r in sur_rec.items() if r["accepted"]]
+    err = [abs(sur_rec[k]["q"] - full_rec[k]["q"]) / max(abs(full_rec[k]["q"]), 1e-12) for k in acc]
+    cells = np.array([c.nx * c.ny for c in pts], dtype=np.float64)
+    spent = sum(cells[k] * sur_rec[k]["steps"] for k in sur_rec) / (cells.sum() * full)
+    ph = lambda secs: n * 3600.0 / secs
+    return {"unit": f"boiling-curve points/hour at {full} steps per point (measured, no extrapolation)",
+            "points": n, "plain": ph(t_plain), "batched": ph(t_batch), "batched_with_surrogate": ph(t_sur),
+            "seconds": {"plain": t_plain, "batched": t_batch, "batched_with_surrogate": t_sur},
+            "setup_seconds_excluded": {"plain": setup_plain, "batched": setup_batch,
+                                       "batched_with_surrogate": setup_sur},
+            "slots": int(sum(nslot.values())), "accepted": len(acc),
+            "accepted_max_error": max(err) if err else 0.0, "work_fraction": float(spent),
+            "policy": {"kind": kind, "threshold": thr, "spread_max": smax, "hist_steps": hs,
+                       "calibration_max_error": float(meta["calibration_max_error"]),
+                       "calibration_accepted": int(meta["calibration_accepted"]),
+                       "calibration_points": int(meta["calibration_points"])},
+            "seed": seed}
+
+
 # ------------------------------------------------------------------ Fig. 11 at the paper's scale
 PAPER_SITE_MINIMA = (0.0, -0.3, -0.6)
 
@@ -538,7 +719,16 @@ if __name__ == "__main__":
     ap.add_argument("--checkpoint-dir", type=str, default=None,
                     help="checkpoint every point there and resume from it (per point) when run again")
     ap.add_argument("--checkpoint-every", type=int, default=4096)
+    ap.add_argument("--train-policy", action="store_true",
+                    help="instead: train the early-stop ensemble and freeze its policy (writes %s)" % POLICY_FILE)
+    ap.add_argument("--pph-study", action="store_true", help="instead: measure points/hour in three arms")
     a = ap.parse_args()
+    if a.train_policy:
+        print(json.dumps({k: (v.item() if hasattr(v, "item") else v) for k, v in train_policy(cache=a.cache).items()}))
+        raise SystemExit(0)
+    if a.pph_study:
+        print(json.dumps(pph_study()))
+        raise SystemExit(0)
     if a.surrogate_study:
         print(json.dumps(surrogate_study(cache=a.cache)))
         raise SystemExit(0)

@@ -57,3 +57,6 @@ def test_clock_samples_are_summarised():
     assert out == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["hw_thermal_slowdown", "sw_power_cap"],
                    "samples": 3}
     assert bench.parse_clock_lines([])["sm_mhz"] is None
+    # a malformed maximum-clock field keeps the sample's clock and its throttle reasons
+    out = bench.parse_clock_lines(["1980, [N/A], 1000.0, Active, Not Active, Not Active, Not Active"])
+    assert out["sm_mhz"] == 1980.0 and out["sm_max_mhz"] is None and out["reasons"] == ["hw_slowdown"]

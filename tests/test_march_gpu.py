@@ -3,8 +3,8 @@ the tiled step kernel on the same domains: the two evaluate every cell's update
 with the same arithmetic, so their fields agree to FP32 rounding, over segment
 heights that split each lattice into several segments with a ragged last one
 and over all three top boundaries.  Both kernels are also checked against the
-FP64 oracle by the parity tests (the row-marching kernel is the default for
-lattices up to 512 columns wide)."""
+FP64 oracle by the parity tests; both are selectable variants beside the
+default split step."""
 import dataclasses
 
 import numpy as np
@@ -32,9 +32,11 @@ def coex():
 
 def _variants():
     from paper_1812_10375_gb300 import hlb
-    v = hlb.tile_variants()
-    tiles = [k for k, (w, h, t) in enumerate(v) if w > 0]
-    marches = [k for k, (w, h, t) in enumerate(v) if w == 0]
+    kinds = hlb.variant_kinds()
+    # the fused tile kernels evaluate each cell with the row-marching kernel's
+    # arithmetic; the split step's coefficient form rounds differently
+    tiles = [k for k, kind in enumerate(kinds) if kind == hlb.HLB_KIND_FUSED]
+    marches = [k for k, kind in enumerate(kinds) if kind == hlb.HLB_KIND_MARCH]
     return tiles, marches
 
 
