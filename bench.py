@@ -45,7 +45,8 @@ ENERGY_BYTES_FLUID = 4 + 12 + 4
 ENERGY_BYTES_SOLID = 8
 KIND_SPLIT, KIND_FUSED, KIND_MARCH = 0, 1, 2
 
-KERNEL_SOURCES = ("hlb_internal.cuh", "hlb_kernels.cuh", "hlb_march.cuh", "hlb_split.cuh")  # step kernels' device code
+KERNEL_SOURCES = ("hlb_internal.cuh", "hlb_kernels.cuh", "hlb_march.cuh", "hlb_split.cuh",
+                  "hlb_energy_walk.cuh")  # step kernels' device code
 
 
 def kernel_source_hash() -> str:
@@ -57,12 +58,27 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def kernel_name(tile, kind=KIND_FUSED):
+def energy_kernel_name(erows):
+    """The split step's energy kernel: the row-walking one (segments of erows
+    rows) or the tiled one (erows = 0)."""
+    return "k_energy_walk_batch" if erows > 0 else "k_energy_batch"
+
+
+def kernel_name(tile, kind=KIND_FUSED, erows=-1):
     """The step kernel(s) a variant launches: the split step's flow and energy
     kernels, the fused tiled kernel, or the row-marching kernel (tile width 0)."""
     if kind == KIND_SPLIT:
-        return "k_flow_batch+k_energy_batch"
+        return "k_flow_batch+" + energy_kernel_name(erows)
     return "k_march_batch" if tile[0] == 0 else "k_step_batch"
+
+
+def variant_key(tile, kind=KIND_FUSED, erows=-1):
+    """Suffix naming a variant in the committed ncu summary: the tile, and for a
+    split variant its energy kernel (walk<rows> or tile)."""
+    key = "x".join(str(t) for t in tile)
+    if kind == KIND_SPLIT:
+        key += "_walk%d" % erows if erows > 0 else "_tile"
+    return key
 
 
 def profile_name(tile, kind=KIND_FUSED):
@@ -81,7 +97,7 @@ def step_launches(cases, tile, kind=KIND_FUSED, nsub=1):
     return len({(c.nx + 31) // 32 for c in cases})
 
 
-def read_traffic(tile, kind=KIND_FUSED):
+def read_traffic(tile, kind=KIND_FUSED, erows=-1):
     """DRAM bytes per step of the step kernel(s) from the committed ncu summary, if
     it was taken on the current kernel source and the same tile variant."""
     path = os.path.join(ROOT, "profiles", profile_name(tile, kind) + "_sweep32.md")
@@ -95,7 +111,7 @@ def read_traffic(tile, kind=KIND_FUSED):
                 vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_hash") != kernel_source_hash():
         return None
-    key = "dram_bytes_per_launch_full_sweep_" + "x".join(str(t) for t in tile)
+    key = "dram_bytes_per_launch_full_sweep_" + variant_key(tile, kind, erows)
     try:
         return float(vals[key])
     except (KeyError, ValueError):
@@ -334,6 +350,7 @@ def run_ours(args):
     # --tile-variant skips the tuning (profiler runs, where tuning times are distorted)
     variants = hlb.tile_variants()
     kinds = hlb.variant_kinds()
+    erows_all = hlb.variant_energy_rows()
     if args.tile_variant is None:
         chosen, tune_ms = batch.autotune(steps_per_variant=4)
     else:
@@ -344,6 +361,7 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     kind = kinds[chosen]
+    erows = erows_all[chosen]
     # timed region: K steps as the library takes them (CUDA-graph replay of
     # 16-step chunks, each step the step kernels and a reduction launch), CUDA
     # events on the batch stream around the whole region
@@ -379,7 +397,8 @@ def run_ours(args):
         fb = FLOW_BYTES_FLUID * n_fluid
         eb = ENERGY_BYTES_FLUID * n_fluid + ENERGY_BYTES_SOLID * n_solid
         kernels = {"k_flow_batch": {"ms": flow_ms, "bytes_per_launch": fb, "gbs": fb / (flow_ms * 1e-3) / 1e9},
-                   "k_energy_batch": {"ms": en_ms, "bytes_per_launch": eb, "gbs": eb / (en_ms * 1e-3) / 1e9}}
+                   energy_kernel_name(erows): {"ms": en_ms, "bytes_per_launch": eb,
+                                               "gbs": eb / (en_ms * 1e-3) / 1e9}}
     diag0 = batch.diag(0, check_flags=False)
 
     # end to end through the public API with host buffers (skipped by --quick,
@@ -390,7 +409,7 @@ def run_ours(args):
 
     peak, peak_src = peak_gbs()
     achieved = bytes_per_step / (kern_avg_ms * 1e-3) / 1e9
-    traffic = read_traffic(variants[chosen], kind)
+    traffic = read_traffic(variants[chosen], kind, erows)
     if kernels:
         for kv in kernels.values():
             kv["frac"] = kv["gbs"] / peak
@@ -409,11 +428,13 @@ def run_ours(args):
                            (36 + 4) * cells / 1e6),
                        "timing": "CUDA events on the batch stream around K graph-replayed steps; the step "
                                  "kernel bracketed per step over %d further launches for the roofline" % n_ev,
-                       "tile": {"chosen": list(variants[chosen]), "candidates_w_h_threads": [list(v) for v in variants],
+                       "tile": {"chosen": list(variants[chosen]), "chosen_index": chosen,
+                                "chosen_energy_walk_rows": erows,
+                                "candidates_w_h_threads": [list(v) for v in variants],
                                 "tuning_ms_per_step": [round(m, 4) for m in tune_ms]}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": kernel_name(variants[chosen], kind), "bytes_per_launch": bytes_per_step,
+                         "kernel": kernel_name(variants[chosen], kind, erows), "bytes_per_launch": bytes_per_step,
                          "bytes_note": "the step's algorithmic bytes (80 B per fluid cell, 8 B per solid cell) "
                                        "over the step kernels' time per step",
                          "kernel_ms": kern_avg_ms, "peak_source": peak_src, "per_kernel": kernels},

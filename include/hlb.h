@@ -307,8 +307,9 @@ hlb_status hlb_batch_destroy(hlb_batch* b);
 /* ------------------------------------------------------------- autotuning
  * The step is compiled in three kinds (hlb_variant_kind):
  *  - HLB_KIND_SPLIT: a flow kernel over tiles of 64 columns by a few fluid-row
- *    heights, then N energy sub-step kernels over 56 x 24 tiles (finite-volume
- *    scheme; the default for it);
+ *    heights, then N energy sub-step kernels: a row-walking kernel over strips
+ *    of 56 columns and segments of 96, 64 or 32 rows, or a tiled one over
+ *    56 x 24 tiles (finite-volume scheme; the default for it);
  *  - HLB_KIND_FUSED: one fused step kernel over 52-column tiles of a few
  *    heights, with 256 or 512 threads per CTA (the default for the isotropic
  *    scheme, which only this kind runs);
@@ -318,7 +319,10 @@ hlb_status hlb_batch_destroy(hlb_batch* b);
  * hlb_tile_variants lists them in that order (returns their count; arrays may
  * be NULL): a split variant reports its flow tile's width, height and threads,
  * a fused tiled one its tile's, a row-marching one width 0, its segment height
- * and 0 threads.  hlb_variant_kind(v) returns the kind of variant v, or -1.  hlb_autotune / hlb_batch_autotune run one untimed and
+ * and 0 threads.  hlb_variant_kind(v) returns the kind of variant v, or -1;
+ * hlb_variant_energy_rows(v) the segment height of a split variant's
+ * row-walking energy kernel, 0 for a split variant with the tiled energy
+ * kernel, -1 for the other kinds or v out of range.  hlb_autotune / hlb_batch_autotune run one untimed and
  * then steps_per_variant timed steps of every variant available to the
  * handle on its own state (others report 1e30 ms), keep the fastest for later
  * steps and report its index in *chosen (and the measured ms per step in
@@ -330,6 +334,7 @@ hlb_status hlb_batch_destroy(hlb_batch* b);
 enum { HLB_KIND_SPLIT = 0, HLB_KIND_FUSED = 1, HLB_KIND_MARCH = 2 };
 int hlb_tile_variants(int* h_tile_w, int* h_tile_h, int* h_threads, int max_out);
 int hlb_variant_kind(int v);
+int hlb_variant_energy_rows(int v);
 hlb_status hlb_autotune(hlb_domain* d, int steps_per_variant, int* chosen, float* h_ms, int max_out);
 hlb_status hlb_batch_autotune(hlb_batch* b, int steps_per_variant, int* chosen, float* h_ms, int max_out);
 

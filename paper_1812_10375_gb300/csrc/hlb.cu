@@ -90,14 +90,14 @@ void launch_energy_batch(int blocks, cudaStream_t s, const StepArgs& phys, const
                          const int* act, int sub, int nsub) {
   k_energy_batch<R, NPH, MINB><<<blocks, 64 * NPH, energy_smem_bytes(), s>>>(phys, desc, blk, act, sub, nsub);
 }
-template <int L, int MINB>
+template <int L, int MINB, int PF>
 void launch_walk_single(dim3 grid, cudaStream_t s, const StepArgs& a, int sub, int nsub) {
-  k_energy_walk<L, MINB><<<grid, EW_W, 0, s>>>(a, sub, nsub);
+  k_energy_walk<L, MINB, PF><<<grid, EW_W, 0, s>>>(a, sub, nsub);
 }
-template <int L, int MINB>
+template <int L, int MINB, int PF>
 void launch_walk_batch(int blocks, cudaStream_t s, const StepArgs& phys, const DomArgs* desc, const int2* blk,
                        const int* act, int sub, int nsub) {
-  k_energy_walk_batch<L, MINB><<<blocks, EW_W, 0, s>>>(phys, desc, blk, act, sub, nsub);
+  k_energy_walk_batch<L, MINB, PF><<<blocks, EW_W, 0, s>>>(phys, desc, blk, act, sub, nsub);
 }
 #define HLB_SPLIT_TILE(TY, NTH, MINB, ER, ENPH, EMINB)                                                          \
   FlowVariant{TY, NTH, 0, ER, flow_smem_bytes<TY>(), (const void*)k_flow<TY, NTH, MINB>,                        \
@@ -105,11 +105,12 @@ void launch_walk_batch(int blocks, cudaStream_t s, const StepArgs& phys, const D
               (const void*)k_energy_batch<ER, ENPH, EMINB>, energy_smem_bytes(), launch_flow_single<TY, NTH, MINB>, \
               launch_flow_batch<TY, NTH, MINB>, launch_energy_single<ER, ENPH, EMINB>,                        \
               launch_energy_batch<ER, ENPH, EMINB>},
-#define HLB_SPLIT_WALK(TY, NTH, MINB, L, EMINB)                                                                 \
+#define HLB_SPLIT_WALK(TY, NTH, MINB, L, EMINB, PF)                                                             \
   FlowVariant{TY, NTH, 1, L, flow_smem_bytes<TY>(), (const void*)k_flow<TY, NTH, MINB>,                         \
-              (const void*)k_flow_batch<TY, NTH, MINB>, (const void*)k_energy_walk<L, EMINB>,                 \
-              (const void*)k_energy_walk_batch<L, EMINB>, 0, launch_flow_single<TY, NTH, MINB>,               \
-              launch_flow_batch<TY, NTH, MINB>, launch_walk_single<L, EMINB>, launch_walk_batch<L, EMINB>},
+              (const void*)k_flow_batch<TY, NTH, MINB>, (const void*)k_energy_walk<L, EMINB, PF>,             \
+              (const void*)k_energy_walk_batch<L, EMINB, PF>, 0, launch_flow_single<TY, NTH, MINB>,           \
+              launch_flow_batch<TY, NTH, MINB>, launch_walk_single<L, EMINB, PF>,                             \
+              launch_walk_batch<L, EMINB, PF>},
 const FlowVariant FLOWS[] = {HLB_SPLIT_VARIANTS(HLB_SPLIT_TILE, HLB_SPLIT_WALK)};
 constexpr int NSPLIT = (int)(sizeof(FLOWS) / sizeof(FLOWS[0]));
 constexpr int MIN_FLOW_TY = 8;  // the shortest flow tile (sizes the flow partial-sum slots)
@@ -1634,6 +1635,11 @@ int hlb_tile_variants(int* h_tile_w, int* h_tile_h, int* h_threads, int max_out)
 int hlb_variant_kind(int v) {
   if (v < 0 || v >= NV_ALL) return -1;
   return is_split(v) ? HLB_KIND_SPLIT : (is_march(v) ? HLB_KIND_MARCH : HLB_KIND_FUSED);
+}
+
+int hlb_variant_energy_rows(int v) {
+  if (v < 0 || v >= NV_ALL || !is_split(v)) return -1;
+  return FLOWS[v].ewalk ? FLOWS[v].ep : 0;
 }
 
 const char* hlb_strerror(hlb_status s) {

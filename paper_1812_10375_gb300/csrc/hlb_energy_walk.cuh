@@ -28,11 +28,14 @@ constexpr int EW_OUT = 56;    // output columns of a strip
 constexpr int EW_H = 4;       // x halo
 constexpr int EW_RTN = 8;     // depth of the T^n ring
 constexpr int EW_R = 4;       // depth of the other rings
-// shared floats: T^n ring, three stage rings, u_x, u_y, lambda rings
-constexpr int EW_SMEM_FLOATS = (EW_RTN + 6 * EW_R) * EW_W;
+constexpr int EW_RPF = 8;     // slots of the prefetch ring (rows r .. r + PF, PF < 8)
+// shared floats: T^n ring, three stage rings, u_x, u_y, lambda rings, and the
+// prefetch ring (T^n, rho^n, u_x, u_y of the rows the asynchronous copies fill)
+constexpr int EW_SMEM_FLOATS = (EW_RTN + 6 * EW_R + 4 * EW_RPF) * EW_W;
 constexpr int EW_OFF_TN = 0, EW_OFF_T1 = EW_RTN * EW_W, EW_OFF_T2 = EW_OFF_T1 + EW_R * EW_W,
               EW_OFF_T3 = EW_OFF_T2 + EW_R * EW_W, EW_OFF_UX = EW_OFF_T3 + EW_R * EW_W,
-              EW_OFF_UY = EW_OFF_UX + EW_R * EW_W, EW_OFF_LAM = EW_OFF_UY + EW_R * EW_W;
+              EW_OFF_UY = EW_OFF_UX + EW_R * EW_W, EW_OFF_LAM = EW_OFF_UY + EW_R * EW_W,
+              EW_OFF_PF = EW_OFF_LAM + EW_R * EW_W;
 // The rings of the walking kernels, at a fixed layout so that every access is
 // an immediate offset from one shared-memory base.
 __shared__ float s_walk[EW_SMEM_FLOATS];
@@ -101,12 +104,54 @@ __device__ __forceinline__ void walk_load(const StepArgs& A, const WalkCtx& C, W
   }
 }
 
+// Prefetch ring: slot row & 7 of the four planes (T, rho, u_x, u_y).
+#define PFW(plane, row, col) s_walk[EW_OFF_PF + ((plane) * EW_RPF + ((row) & (EW_RPF - 1))) * EW_W + (col)]
+
+// Start the copies of row `row` (clamped to the lattice: the ghost rows above
+// it repeat row ny - 1) into its prefetch slot; rows below the lattice are not
+// read.  Every call commits one group, empty or not, so that the groups of the
+// rows in flight stay counted.
+__device__ __forceinline__ void walk_fetch(const StepArgs& A, const WalkCtx& C, int row) {
+  if (row >= 0) {
+    const int gr = row < A.ny ? row : A.ny - 1;
+    const int c = gr * A.nx + C.gx;
+    cp_async4(&PFW(0, row, C.i), C.T_in + c);
+    cp_async4(&PFW(1, row, C.i), C.rho_n + c);
+    cp_async4(&PFW(2, row, C.i), C.ux_n + c);
+    cp_async4(&PFW(3, row, C.i), C.uy_n + c);
+  }
+  cp_async_commit();
+}
+
+// Row `row` from its prefetch slot (its copies complete: PF - 1 younger groups
+// may still be in flight), with the substitutions of walk_load: zeros below
+// the lattice, the wall temperature on Dirichlet rows, no rho or u on solid rows.
+template <bool STEADY, int PF>
+__device__ __forceinline__ void walk_take(const StepArgs& A, const WalkCtx& C, WalkState& S, int row) {
+  cp_async_wait<PF - 1>();
+  const float T = PFW(0, row, C.i), R = PFW(1, row, C.i), U = PFW(2, row, C.i), V = PFW(3, row, C.i);
+  if (STEADY) {
+    S.pT = T;
+    S.pR = R;
+    S.pUx = U;
+    S.pUy = V;
+    return;
+  }
+  const Geo g = make_geo(A);
+  const int gr = row < A.ny ? row : A.ny - 1;
+  const bool below = row < 0, solid = !below && g.solid_row(gr);
+  S.pT = below ? 0.f : (g.dirichlet_row(gr) ? (gr == 0 ? A.T_bottom : A.T_top) : T);
+  S.pR = below || solid ? 0.f : R;
+  S.pUx = below || solid ? 0.f : U;
+  S.pUy = below || solid ? 0.f : V;
+}
+
 #define SW(off, slot, col) s_walk[(off) + (slot) * EW_W + (col)]
 
 // One walk step.  STEADY: an interior segment past its first eight steps:
 // every phase is active and no row of the step is solid, Dirichlet, a ghost,
 // a wall-flux row or the top row, so all row tests compile away.
-template <int P, bool STEADY>
+template <int P, bool STEADY, int PF>
 __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, WalkState& S, int t) {
   constexpr int P0 = P & 3, P1 = (P + 3) & 3, P2 = (P + 2) & 3, P3 = (P + 1) & 3;  // rows r, r-1, r-2, r-3
   const Geo g = make_geo(A);
@@ -117,7 +162,12 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
   auto wall_lam = [&](int row) -> float { return g.top_wall && row == ny - 1 ? A.lambda_top : A.lambda_w; };
 
   // ---- load phase: row r (prefetched) into the rings; prefetch row r + 1
+  // (PF = 0: into registers) or start the copies of row r + PF (PF > 0)
   {
+    if constexpr (PF > 0) {
+      walk_take<STEADY, PF>(A, C, S, r);
+      walk_fetch(A, C, r + PF);
+    }
     float lam;
     if (STEADY) {
       lam = S.pR * A.cvk;
@@ -134,7 +184,7 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
     SW(EW_OFF_UY, P0, i) = S.pUy;
     SW(EW_OFF_LAM, P0, i) = lam;
     const float rho_r = S.pR;
-    walk_load<STEADY>(A, C, S, r + 1);
+    if constexpr (PF == 0) walk_load<STEADY>(A, C, S, r + 1);
     __syncthreads();
     S.dx[P0] = SW(EW_OFF_UX, P0, ie) - SW(EW_OFF_UX, P0, iw);
     S.sy[P0] = SW(EW_OFF_UY, P0, ie) + SW(EW_OFF_UY, P0, iw);
@@ -304,7 +354,9 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
 #undef SW
 
 // Walk of strip sx, segment sg (rows [sg L, sg L + L)) of one domain.
+template <int PF>
 __device__ __forceinline__ void energy_walk(const StepArgs& A, int L, int sx, int sg, int part, int s, int nsub) {
+  static_assert(PF >= 0 && PF < EW_RPF, "prefetch depth within the prefetch ring");
   __shared__ float s_red[EW_W / 32][NEPART][2];
   __shared__ int s_err;
   WalkCtx C;
@@ -344,7 +396,12 @@ __device__ __forceinline__ void energy_walk(const StepArgs& A, int L, int sx, in
 #pragma unroll
   for (int q = 0; q < 3 * EW_R; ++q) s_walk[EW_OFF_T1 + q * EW_W + C.i] = 0.f;
   const int t0 = C.ys - 4;  // a multiple of four: t & 3 is the unrolled phase
-  walk_load<false>(A, C, S, t0);
+  if constexpr (PF == 0) {
+    walk_load<false>(A, C, S, t0);
+  } else {
+#pragma unroll
+    for (int k = 0; k < PF; ++k) walk_fetch(A, C, t0 + k);
+  }
   // Steps t .. t+3 touch rows t - 5 .. t + 4.  They run in the steady form when
   // every phase of each is active (t >= ys + 4, t + 3 < ye + 4) and those rows
   // are fluid rows at least two rows from the wall rows and three from the top
@@ -352,30 +409,31 @@ __device__ __forceinline__ void energy_walk(const StepArgs& A, int L, int sx, in
   const int t_lo = max(C.ys + 4, A.W + 7), t_hi = min(C.ye, A.ny - 7);  // steady groups: t_lo <= t <= t_hi
   for (int t = t0; t < C.ye + 4; t += 4) {
     if (t >= t_lo && t <= t_hi) {
-      walk_step<0, true>(A, C, S, t);
-      walk_step<1, true>(A, C, S, t + 1);
-      walk_step<2, true>(A, C, S, t + 2);
-      walk_step<3, true>(A, C, S, t + 3);
+      walk_step<0, true, PF>(A, C, S, t);
+      walk_step<1, true, PF>(A, C, S, t + 1);
+      walk_step<2, true, PF>(A, C, S, t + 2);
+      walk_step<3, true, PF>(A, C, S, t + 3);
     } else {
-      walk_step<0, false>(A, C, S, t);
-      walk_step<1, false>(A, C, S, t + 1);
-      walk_step<2, false>(A, C, S, t + 2);
-      walk_step<3, false>(A, C, S, t + 3);
+      walk_step<0, false, PF>(A, C, S, t);
+      walk_step<1, false, PF>(A, C, S, t + 1);
+      walk_step<2, false, PF>(A, C, S, t + 2);
+      walk_step<3, false, PF>(A, C, S, t + 3);
     }
   }
+  if constexpr (PF > 0) cp_async_wait<0>();  // copies of the rows past the walk: none left in flight at exit
   float ah[NEPART] = {S.qbh, S.qth, S.qih, S.eh}, al[NEPART] = {S.qbl, S.qtl, S.qil, S.el};
   if (S.err) atomicOr(&s_err, S.err);
   block_partials<EW_W, NEPART>(ah, al, s_red, A.epart + (long long)part * NEPART, s > 1);
   if (threadIdx.x == 0 && s_err) atomicOr(&A.state->error_flags, s_err);
 }
 
-template <int L, int MINB>
+template <int L, int MINB, int PF>
 __global__ void __launch_bounds__(EW_W, MINB) k_energy_walk(const StepArgs A, int s, int nsub) {
   static_assert(L % 4 == 0, "segments start on a multiple of four rows");
-  energy_walk(A, L, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, s, nsub);
+  energy_walk<PF>(A, L, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, s, nsub);
 }
 
-template <int L, int MINB>
+template <int L, int MINB, int PF>
 __global__ void __launch_bounds__(EW_W, MINB) k_energy_walk_batch(const StepArgs P, const DomArgs* __restrict__ desc,
                                                                const int2* __restrict__ blk,
                                                                const int* __restrict__ active, int s, int nsub) {
@@ -389,7 +447,7 @@ __global__ void __launch_bounds__(EW_W, MINB) k_energy_walk_batch(const StepArgs
   apply_dom(A, sD);
   const int local = s_bl.y;
   const int strips = (A.nx + EW_OUT - 1) / EW_OUT;
-  energy_walk(A, L, local % strips, local / strips, local, s, nsub);
+  energy_walk<PF>(A, L, local % strips, local / strips, local, s, nsub);
 }
 
 }  // namespace hlb

@@ -91,4 +91,18 @@ struct DomArgs {
   double* epart;
 };
 
+// Asynchronous 4-byte global-to-shared copies (cp.async, .ca).  The kernels
+// that use them copy into and later read only slots of their own thread, so
+// cp.async.wait_group alone makes the data visible to the reader.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// all but the N most recently committed groups of this thread complete
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 }  // namespace hlb

@@ -121,11 +121,6 @@ struct MarchRows {
   __device__ __forceinline__ bool ghost(int y, int lo, int hi) const { return top_open && y == ny && in(y - 1, lo, hi); }
 };
 
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 // all but the most recent group complete: the row pulled now has arrived, the next one may be in flight
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 

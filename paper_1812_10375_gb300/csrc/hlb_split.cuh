@@ -45,10 +45,13 @@ constexpr int FL_FW = FL_TX + 2;   // psi frame: the tile and a one-cell ring
 // Compiled split-step variants: flow tile (fluid rows, threads per CTA, CTAs
 // per SM) and energy layout (rows per thread run, runs, CTAs per SM).
 // TILE(TYF, NTHF, MINBF, R, NPH, MINB): the energy tile of R-row runs;
-// WALK(TYF, NTHF, MINBF, L, MINB): the row-walking energy kernel over L-row
-// segments, sized for MINB CTAs per SM.
+// WALK(TYF, NTHF, MINBF, L, MINB, PF): the row-walking energy kernel over
+// L-row segments, sized for MINB CTAs per SM, its input rows fetched PF rows
+// ahead by asynchronous copies into shared memory (PF = 0: one row ahead into
+// registers).
 #define HLB_SPLIT_VARIANTS(TILE, WALK) \
-  WALK(16, 256, 3, 96, 8) WALK(16, 256, 3, 64, 10) WALK(16, 256, 3, 32, 8) TILE(16, 256, 3, 8, 4, 2)
+  WALK(16, 256, 3, 64, 10, 6) WALK(16, 256, 3, 96, 8, 4) WALK(16, 256, 3, 96, 8, 0) WALK(16, 256, 3, 32, 8, 0) \
+  TILE(16, 256, 3, 8, 4, 2)
 
 constexpr int EN_TX = 56, EN_TY = 24, EN_H = 4;
 constexpr int EN_FW = EN_TX + 2 * EN_H;  // 64 frame columns, one per thread

@@ -90,6 +90,7 @@ def lib() -> C.CDLL:
             "hlb_batch_destroy": (st, [vp]),
             "hlb_tile_variants": (C.c_int, [P(C.c_int), P(C.c_int), P(C.c_int), C.c_int]),
             "hlb_variant_kind": (C.c_int, [C.c_int]),
+            "hlb_variant_energy_rows": (C.c_int, [C.c_int]),
             "hlb_autotune": (st, [vp, C.c_int, P(C.c_int), P(C.c_float), C.c_int]),
             "hlb_batch_autotune": (st, [vp, C.c_int, P(C.c_int), P(C.c_float), C.c_int]),
             "hlb_set_tile_variant": (st, [vp, C.c_int]),
@@ -205,6 +206,13 @@ def variant_kinds():
     """HLB_KIND_* of every compiled variant, in the order of tile_variants()."""
     n = lib().hlb_tile_variants(None, None, None, 0)
     return [int(lib().hlb_variant_kind(k)) for k in range(n)]
+
+
+def variant_energy_rows():
+    """Per compiled variant: the segment height of a split variant's row-walking
+    energy kernel, 0 for the tiled energy kernel, -1 for the fused kinds."""
+    n = lib().hlb_tile_variants(None, None, None, 0)
+    return [int(lib().hlb_variant_energy_rows(k)) for k in range(n)]
 
 
 def _autotune(fn, handle, steps, stream):

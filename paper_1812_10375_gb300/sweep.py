@@ -466,11 +466,12 @@ def pph_study(n=32, full=40000, slots_per_size=None, seed=STUDY_SEED, policy=Non
                then its result and whose slot is refilled at once, or lets
                it run to `full`.
 
-    The timed regions cover stepping, refills, history reads and policy
-    calls; creating the domains or batch and their first fields is set-up,
-    timed separately and excluded from all three arms.  The batched arm gives
-    the full-run wall flux of every point, against which the surrogate arm's
-    accepted points are checked."""
+    Every arm counts, per point, its initial fields (set_wall, set_fields,
+    the nucleation sites), its steps, the reads of its history and, in the
+    surrogate arm, the policy's call; allocating the domains (one per size)
+    or the batch is set-up, timed separately and excluded from all three.
+    The batched arm gives the full-run wall flux of every point, against
+    which the surrogate arm's accepted points are checked."""
     import torch
     from .surrogate import Ensemble
     ens, meta = Ensemble.load(policy or policy_path())
@@ -484,23 +485,27 @@ def pph_study(n=32, full=40000, slots_per_size=None, seed=STUDY_SEED, policy=Non
              for s, v in by_size.items()}
     params = [params_for(c) for c in pts]
 
-    # ---- plain: one domain at a time
-    t_plain = setup_plain = 0.0
+    # ---- plain: one domain at a time (one domain per size, allocated up front)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    doms = {}
+    for s in sizes:
+        k0 = by_size[s][0]
+        doms[s] = hlb.Domain(params[k0][0])
+    torch.cuda.synchronize()
+    setup_plain = time.perf_counter() - t0
+    t0 = time.perf_counter()
     for k, c in enumerate(pts):
         p, Tc = params[k]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        d = hlb.Domain(p)
+        d = doms[c.nx]
+        d.set_wall(p.T_bottom)
         _setup_domain(d, c, p, Tc)
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
         d.step(full)
         d.diag(check_flags=False)
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    for d in doms.values():
         d.close()
-        setup_plain += t1 - t0
-        t_plain += t2 - t1
 
     def slot_arm(use_policy):
         """Run all points through the slots; returns (seconds, set-up seconds, per-point record)."""
@@ -511,16 +516,17 @@ def pph_study(n=32, full=40000, slots_per_size=None, seed=STUDY_SEED, policy=Non
             slot_pts += by_size[s][:nslot[s]]
         queue = {s: list(by_size[s][nslot[s]:]) for s in sizes}
         b = hlb.Batch([params[k][0] for k in slot_pts])
-        for i, k in enumerate(slot_pts):
-            _setup(b, i, pts[k], params[k][0], params[k][1])
         torch.cuda.synchronize()
         t1 = time.perf_counter()
+        for i, k in enumerate(slot_pts):
+            _setup(b, i, pts[k], params[k][0], params[k][1])
         age = [0] * len(slot_pts)
         rec = {}
         live = set(range(len(slot_pts)))
-        chunk = hs if use_policy else full
+        # the next event of a slot: the policy's look at hist_steps, the end at full
+        nxt = lambda i: (hs if use_policy and age[i] < hs else full) - age[i]
         while live:
-            step = min(chunk - age[i] % chunk if age[i] < full else 0 for i in live) or chunk
+            step = min(nxt(i) for i in live)
             b.step(step)
             for i in list(live):
                 age[i] += step
@@ -569,7 +575,8 @@ def pph_study(n=32, full=40000, slots_per_size=None, seed=STUDY_SEED, policy=Non
             "setup_seconds_excluded": {"plain": setup_plain, "batched": setup_batch,
                                        "batched_with_surrogate": setup_sur},
             "slots": int(sum(nslot.values())), "accepted": len(acc),
-            "accepted_max_error": max(err) if err else 0.0, "work_fraction": float(spent),
+            "accepted_max_error": max(err) if err else 0.0,
+            "accepted_errors": sorted(round(float(e), 5) for e in err), "work_fraction": float(spent),
             "policy": {"kind": kind, "threshold": thr, "spread_max": smax, "hist_steps": hs,
                        "calibration_max_error": float(meta["calibration_max_error"]),
                        "calibration_accepted": int(meta["calibration_accepted"]),

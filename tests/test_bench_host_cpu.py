@@ -10,7 +10,11 @@ import bench
 def test_kernel_name_and_launch_count():
     assert bench.kernel_name((52, 28, 512)) == "k_step_batch"
     assert bench.kernel_name((0, 48, 0)) == "k_march_batch"
-    assert bench.kernel_name((64, 16, 256), bench.KIND_SPLIT) == "k_flow_batch+k_energy_batch"
+    assert bench.kernel_name((64, 16, 256), bench.KIND_SPLIT, 0) == "k_flow_batch+k_energy_batch"
+    assert bench.kernel_name((64, 16, 256), bench.KIND_SPLIT, 96) == "k_flow_batch+k_energy_walk_batch"
+    assert bench.variant_key((64, 16, 256), bench.KIND_SPLIT, 96) == "64x16x256_walk96"
+    assert bench.variant_key((64, 16, 256), bench.KIND_SPLIT, 0) == "64x16x256_tile"
+    assert bench.variant_key((52, 28, 512)) == "52x28x512"
     assert bench.profile_name((64, 16, 256), bench.KIND_SPLIT) == "k_flow_energy_batch"
     cases = [SimpleNamespace(nx=n) for n in (256, 320, 300, 512, 500)]
     assert bench.step_launches(cases, (52, 20, 512)) == 1
@@ -21,10 +25,10 @@ def test_kernel_name_and_launch_count():
     assert bench.step_launches(cases, (64, 16, 256), bench.KIND_SPLIT, nsub=3) == 4
 
 
-def _profile(root, h, lines):
+def _profile(root, h, lines, name="k_step_batch"):
     (root / "profiles").mkdir(parents=True, exist_ok=True)
     body = ["# summary", f"- kernel_source_hash: `{h}`"] + lines
-    (root / "profiles" / "k_step_batch_sweep32.md").write_text("\n".join(body) + "\n")
+    (root / "profiles" / f"{name}_sweep32.md").write_text("\n".join(body) + "\n")
 
 
 def test_traffic_is_read_only_for_the_current_kernel(tmp_path, monkeypatch):
@@ -38,6 +42,12 @@ def test_traffic_is_read_only_for_the_current_kernel(tmp_path, monkeypatch):
     assert bench.read_traffic((52, 16, 256)) is None      # not captured
     _profile(tmp_path, "stale0", ["- dram_bytes_per_launch_full_sweep_52x28x512: 351090176"])
     assert bench.read_traffic((52, 28, 512)) is None      # kernel changed since the capture
+    # split variants: one summary for the split step, keyed by the energy kernel
+    _profile(tmp_path, "abc123", ["- dram_bytes_per_launch_full_sweep_64x16x256_walk96: 476000000"],
+             name="k_flow_energy_batch")
+    assert bench.read_traffic((64, 16, 256), bench.KIND_SPLIT, 96) == 476000000.0
+    assert bench.read_traffic((64, 16, 256), bench.KIND_SPLIT, 64) is None
+    assert bench.read_traffic((64, 16, 256), bench.KIND_SPLIT, 0) is None
 
 
 def test_peak_prefers_the_measured_file(tmp_path, monkeypatch):
