@@ -282,8 +282,21 @@ hlb_status hlb_batch_step_profiled(hlb_batch* b, void* ev_before, void* ev_after
 
 /* As hlb_batch_step_profiled, with one more event (may be NULL) recorded
  * between the flow kernel and the energy kernels of a split step (not
- * recorded by a fused variant), so that each kernel can be timed. */
+ * recorded by a fused variant, nor in two lanes), so that each kernel can be
+ * timed. */
 hlb_status hlb_batch_step_phases(hlb_batch* b, void* ev_before, void* ev_flow, void* ev_after);
+
+/* Lanes of the split step (lanes = 1 or 2; 1 after hlb_batch_init).  With 2,
+ * the domains are cut into two contiguous groups of about equal cell count;
+ * the second group's launches go to a stream of the library's own, and its
+ * flow kernel of a step waits only for the first group's, so that the
+ * first group's energy kernels run beside the second group's flow kernel and
+ * the second's energy kernels beside the first's next flow kernel.  Results
+ * are those of one lane bit for bit (the groups' domains are independent).
+ * Every batch call returns with the second stream joined into the batch
+ * stream, so the caller still sees one stream.  HLB_EINVAL for another lane
+ * count; a batch of one domain or a fused variant runs in one lane. */
+hlb_status hlb_batch_set_lanes(hlb_batch* b, int lanes);
 
 /* As hlb_read / hlb_diag for domain i. */
 hlb_status hlb_batch_read(hlb_batch* b, int i, float* d_rho, float* d_ux, float* d_uy, float* d_T);

@@ -696,10 +696,21 @@ struct hlb_batch {
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev_join;
   cudaEvent_t ev_fork = nullptr;
+  // split step in two lanes: domains [0, lane_split) on the batch stream,
+  // [lane_split, n) on side[0], whose flow kernel of a step waits for the first
+  // lane's, so that one lane's energy kernels run beside the other lane's flow
+  // kernel (the flow kernel is bound by DRAM, the energy kernel by issue)
+  int lanes = 1;
+  int lane_split = 0, lane_blk = 0, lane_eblk = 0;  // first domain, flow block, energy block of lane B
+  cudaEvent_t ev_lane = nullptr;       // lane A's flow kernel of the current step done
+  cudaEvent_t ev_lane_join = nullptr;  // lane B's last work done
+  bool lane_pending = false;           // lane B has work not yet joined into the batch stream
   ~hlb_batch() {
     for (cudaStream_t s : side) cudaStreamDestroy(s);
     for (cudaEvent_t e : ev_join) cudaEventDestroy(e);
     if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_lane) cudaEventDestroy(ev_lane);
+    if (ev_lane_join) cudaEventDestroy(ev_lane_join);
   }
 };
 
@@ -817,9 +828,58 @@ hlb_status upload_tables(hlb_batch* b) {
 // One batched step.  Events (any may be null): `before` the step kernels,
 // `mid` after the flow kernel of a split step, `after` the step kernels
 // (before the reduction).
+// Make the batch stream wait for everything lane B has been given.
+hlb_status lane_join(hlb_batch* b) {
+  if (!b->lane_pending) return HLB_OK;
+  if (cudaEventRecord(b->ev_lane_join, b->side[0]) != cudaSuccess ||
+      cudaStreamWaitEvent(b->stream, b->ev_lane_join, 0) != cudaSuccess)
+    return HLB_ECUDA;
+  b->lane_pending = false;
+  return HLB_OK;
+}
+
+bool two_lanes(const hlb_batch* b) { return is_split(b->variant) && b->lanes == 2 && b->n >= 2; }
+
+// One split step in two lanes (see hlb_batch::lanes); lane B is left pending.
+hlb_status batch_launch_lanes(hlb_batch* b, const DomArgs* desc) {
+  const FlowVariant& fv = FLOWS[b->variant];
+  const int nsub = b->dom[0].p.n_sub;
+  const int m = b->lane_split;
+  cudaStream_t a = b->stream, s2 = b->side[0];
+  fv.launch_batch(b->lane_blk, fv.smem, a, b->phys, desc, b->d_blk, b->d_active, b->d_lag);
+  if (cudaEventRecord(b->ev_lane, a) != cudaSuccess) return HLB_ECUDA;
+  for (int s = 1; s <= nsub; ++s) fv.energy_batch(b->lane_eblk, a, b->phys, desc, b->d_eblk, b->d_active, s, nsub);
+  k_reduce_split_batch<<<m, 256, 0, a>>>(b->d_sra, b->d_active, b->d_lag, HIST_CAP);
+  if (cudaStreamWaitEvent(s2, b->ev_lane, 0) != cudaSuccess) return HLB_ECUDA;
+  fv.launch_batch(b->total_tiles - b->lane_blk, fv.smem, s2, b->phys, desc, b->d_blk + b->lane_blk, b->d_active,
+                  b->d_lag);
+  for (int s = 1; s <= nsub; ++s)
+    fv.energy_batch(b->total_etiles - b->lane_eblk, s2, b->phys, desc, b->d_eblk + b->lane_eblk, b->d_active, s,
+                    nsub);
+  k_reduce_split_batch<<<b->n - m, 256, 0, s2>>>(b->d_sra + m, b->d_active + m, b->d_lag + m, HIST_CAP);
+  b->lane_pending = true;
+  return cudaGetLastError() == cudaSuccess ? HLB_OK : HLB_ECUDA;
+}
+
 hlb_status batch_launch(hlb_batch* b, cudaEvent_t before, cudaEvent_t after, cudaEvent_t mid = nullptr) {
   if (before && cudaEventRecord(before, b->stream) != cudaSuccess) return HLB_ECUDA;
   const DomArgs* desc = b->d_desc + (size_t)b->parity * b->n;
+  if (two_lanes(b)) {
+    // the flow/energy boundary is not a point in time here: `mid` is not recorded
+    hlb_status st = batch_launch_lanes(b, desc);
+    if (st == HLB_OK && after) st = lane_join(b);
+    if (st != HLB_OK) return st;
+    if (after && cudaEventRecord(after, b->stream) != cudaSuccess) return HLB_ECUDA;
+    b->parity ^= 1;
+    b->steps += 1;
+    for (int i = 0; i < b->n; ++i) {
+      if (b->active[i]) {
+        b->dom[i].parity ^= 1;
+        b->dom[i].steps += 1;
+      }
+    }
+    return HLB_OK;
+  }
   if (is_split(b->variant)) {
     const FlowVariant& fv = FLOWS[b->variant];
     fv.launch_batch(b->total_tiles, fv.smem, b->stream, b->phys, desc, b->d_blk, b->d_active, b->d_lag);
@@ -890,6 +950,7 @@ hlb_status batch_build_graph(hlb_batch* b) {
   if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HLB_ECUDA;
   hlb_status st = HLB_OK;
   for (int k = 0; k < GRAPH_STEPS && st == HLB_OK; ++k) st = batch_launch(b, nullptr, nullptr);
+  if (st == HLB_OK) st = lane_join(b);  // a capture ends with every forked stream joined
   const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
   b->steps = s0;
   b->parity = 0;
@@ -923,8 +984,42 @@ bool batch_variant_ok(const hlb_batch* b, int v) {
   return true;
 }
 
+// Lane B of the two-lane split step: the domains from the first one at which
+// the cells of lane A reach half of the batch's, their flow and energy blocks;
+// a side stream and the two events.
+hlb_status lane_setup(hlb_batch* b) {
+  if (!is_split(b->variant) || b->n < 2) return HLB_OK;
+  double total = 0.0, acc = 0.0;
+  for (int i = 0; i < b->n; ++i) total += (double)b->dom[i].p.nx * b->dom[i].p.ny;
+  int m = 1;
+  for (int i = 0; i < b->n - 1; ++i) {
+    acc += (double)b->dom[i].p.nx * b->dom[i].p.ny;
+    m = i + 1;
+    if (acc >= 0.5 * total) break;
+  }
+  b->lane_split = m;
+  b->lane_blk = b->tile_off[m];
+  int e = 0;
+  while (e < (int)b->eblk.size() && b->eblk[e].x < m) ++e;
+  b->lane_eblk = e;
+  if (b->side.empty()) {
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ej = nullptr;
+    if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) return HLB_ECUDA;
+    b->side.push_back(s2);
+    if (cudaEventCreateWithFlags(&ej, cudaEventDisableTiming) != cudaSuccess) return HLB_ECUDA;
+    b->ev_join.push_back(ej);
+  }
+  if (!b->ev_lane && cudaEventCreateWithFlags(&b->ev_lane, cudaEventDisableTiming) != cudaSuccess) return HLB_ECUDA;
+  if (!b->ev_lane_join && cudaEventCreateWithFlags(&b->ev_lane_join, cudaEventDisableTiming) != cudaSuccess)
+    return HLB_ECUDA;
+  return HLB_OK;
+}
+
 hlb_status set_batch_variant(hlb_batch* b, int v) {
   if (!batch_variant_ok(b, v)) return HLB_EINVAL;
+  const hlb_status sj = lane_join(b);
+  if (sj != HLB_OK) return sj;
   b->variant = v;
   b->tile_off.assign(b->n + 1, 0);
   for (int i = 0; i < b->n; ++i) {
@@ -979,6 +1074,8 @@ hlb_status set_batch_variant(hlb_batch* b, int v) {
       for (int t = b->tile_off[i]; t < b->tile_off[i + 1]; ++t) b->blk.push_back(make_int2(i, t - b->tile_off[i]));
   }
   b->smem = is_split(v) ? FLOWS[v].smem : (is_march(v) ? march_smem(MARCH_MAX_NX) : VARIANTS[tiled_index(v)].smem);
+  const hlb_status st = lane_setup(b);
+  if (st != HLB_OK) return st;
   batch_drop_graph(b);
   return upload_tables(b);
 }
@@ -1419,6 +1516,9 @@ hlb_status hlb_batch_step(hlb_batch* b, int nsteps) {
   const bool graphs = b->stream != nullptr;
   while (nsteps > 0 && st == HLB_OK) {
     if (graphs && b->parity == 0 && nsteps >= GRAPH_STEPS) {
+      // the graph's lane-B kernels are not on the side stream: join it first
+      st = lane_join(b);
+      if (st != HLB_OK) return st;
       if (!b->graph) {
         st = batch_build_graph(b);
         if (st != HLB_OK) return st;
@@ -1434,21 +1534,35 @@ hlb_status hlb_batch_step(hlb_batch* b, int nsteps) {
       nsteps -= 1;
     }
   }
-  return st;
+  const hlb_status sj = lane_join(b);
+  return st != HLB_OK ? st : sj;
+}
+
+hlb_status hlb_batch_set_lanes(hlb_batch* b, int lanes) {
+  if (!b || (lanes != 1 && lanes != 2)) return HLB_EINVAL;
+  const hlb_status st = lane_join(b);
+  if (st != HLB_OK) return st;
+  b->lanes = lanes;
+  batch_drop_graph(b);
+  return lane_setup(b);
 }
 
 hlb_status hlb_batch_step_profiled(hlb_batch* b, void* ev_before, void* ev_after) {
   if (!b) return HLB_EINVAL;
   for (int i = 0; i < b->n; ++i)
     if (!b->dom[i].fields_set) return HLB_ESTATE;
-  return batch_launch(b, (cudaEvent_t)ev_before, (cudaEvent_t)ev_after);
+  const hlb_status st = batch_launch(b, (cudaEvent_t)ev_before, (cudaEvent_t)ev_after);
+  const hlb_status sj = lane_join(b);
+  return st != HLB_OK ? st : sj;
 }
 
 hlb_status hlb_batch_step_phases(hlb_batch* b, void* ev_before, void* ev_flow, void* ev_after) {
   if (!b) return HLB_EINVAL;
   for (int i = 0; i < b->n; ++i)
     if (!b->dom[i].fields_set) return HLB_ESTATE;
-  return batch_launch(b, (cudaEvent_t)ev_before, (cudaEvent_t)ev_after, (cudaEvent_t)ev_flow);
+  const hlb_status st = batch_launch(b, (cudaEvent_t)ev_before, (cudaEvent_t)ev_after, (cudaEvent_t)ev_flow);
+  const hlb_status sj = lane_join(b);
+  return st != HLB_OK ? st : sj;
 }
 
 hlb_status hlb_batch_read(hlb_batch* b, int i, float* d_rho, float* d_ux, float* d_uy, float* d_T) {
@@ -1577,8 +1691,10 @@ hlb_status hlb_batch_autotune(hlb_batch* b, int steps_per_variant, int* chosen, 
     if (st != HLB_OK) break;
     st = batch_launch(b, nullptr, nullptr);  // one untimed step per variant (first-launch costs)
     if (st != HLB_OK) break;
+    if (st == HLB_OK) st = lane_join(b);
     cudaEventRecord(e0, b->stream);
     for (int k = 0; k < steps_per_variant && st == HLB_OK; ++k) st = batch_launch(b, nullptr, nullptr);
+    if (st == HLB_OK) st = lane_join(b);
     cudaEventRecord(e1, b->stream);
     float ms = 0.f;
     if (st == HLB_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))

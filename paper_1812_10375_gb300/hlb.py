@@ -83,6 +83,7 @@ def lib() -> C.CDLL:
             "hlb_batch_step": (st, [vp, C.c_int]),
             "hlb_batch_step_profiled": (st, [vp, vp, vp]),
             "hlb_batch_step_phases": (st, [vp, vp, vp, vp]),
+            "hlb_batch_set_lanes": (st, [vp, C.c_int]),
             "hlb_batch_read": (st, [vp, C.c_int, vp, vp, vp, vp]),
             "hlb_batch_diag": (st, [vp, C.c_int, P(hlb_diag_record)]),
             "hlb_batch_flux_history": (st, [vp, C.c_int, P(C.c_double), C.c_int, P(C.c_int)]),
@@ -406,6 +407,10 @@ class Batch:
         check("hlb_batch_step_phases",
               lib().hlb_batch_step_phases(self._h, _event_handle(ev_before), _event_handle(ev_flow),
                                           _event_handle(ev_after)))
+
+    def set_lanes(self, lanes):
+        """Run the split step in 1 or 2 lanes (see hlb_batch_set_lanes)."""
+        check("hlb_batch_set_lanes", lib().hlb_batch_set_lanes(self._h, int(lanes)))
 
     def read(self, i):
         import torch

@@ -163,3 +163,33 @@ def test_nonfinite_input_is_reported_and_blocks_steps(coex):
     ok = gpu_domain(case, coex)
     ok.step(5)
     assert ok.diag().error_flags == 0
+
+
+def test_two_lanes_match_one_lane_bit_for_bit(coex):
+    """The two-lane split step (hlb_batch_set_lanes) only reorders launches of
+    independent domains: 37 steps (two captured graphs, direct steps at both
+    parities), a slot stopped and refilled half way, give the one-lane fields,
+    diagnostics and flux histories bit for bit."""
+    import torch
+    from paper_1812_10375_gb300 import hlb
+    cases = _cases()
+    runs = []
+    for lanes in (1, 2):
+        b = _batch(cases, coex)
+        b.set_lanes(lanes)
+        b.step(19)
+        b.stop(2)
+        b.step(3)
+        rho0, T0 = wl.initial_fields(cases[2], coex["rho_l"], coex["rho_v"], coex["Tc"])
+        b.set_fields(2, torch.tensor(rho0, dtype=torch.float32, device="cuda"),
+                     torch.tensor(T0, dtype=torch.float32, device="cuda"))
+        b.step(15)
+        runs.append([([t.cpu().numpy() for t in b.read(i)], b.diag(i), b.flux_history(i)) for i in range(len(cases))])
+        b.close()
+    for i, ((f1, d1, h1), (f2, d2, h2)) in enumerate(zip(*runs)):
+        for x, y in zip(f1, f2):
+            assert np.array_equal(x, y), cases[i].name
+        assert d1 == d2 and np.array_equal(h1, h2), cases[i].name
+    assert runs[0][2][1].step == 15 and runs[0][0][1].step == 37
+    with pytest.raises(hlb.HlbError):
+        _batch(cases[:1], coex).set_lanes(3)

@@ -107,35 +107,49 @@ def test_boiling_time_averaged_flux_matches_oracle(coex):
 
 
 def test_departure_period_matches_oracle(coex):
-    """Bubble departure (Section 4.3): a 64 x 140 lattice with a 10-row heater
+    """Bubble departure (Section 4.3): a 64 x 200 lattice with a 10-row heater
     at Ts + 0.11 Tc, one nucleation site (g_min = -0.3) and a vapour bubble of
-    radius 12 seeded on it.  Densities every 20 steps over 20,000 steps go
-    through the departure detector (paper_1812_10375_gb300.departure) for the
-    FP32 GPU run and the FP64 oracle run: both see the same departures, at
-    times within 3% of the departure period, and periods within 3%."""
+    radius 12 seeded on it, 45,000 steps.  Densities every 20 steps go through
+    the departure detector for the FP32 GPU run; the FP64 oracle's departures
+    of the same case, from the same detector, are stored in
+    tests/golden/departures_64x200.json (written by the committed oracle-only
+    script beside it): four departures about 10,000 steps apart.  The GPU
+    sees as many, each within 3% of the period of the oracle's, with a
+    period within 3% of the oracle's; the product's own detector
+    (paper_1812_10375_gb300.departure) sees the same events."""
+    import json
+    import os
+    import sys
     from paper_1812_10375_gb300 import departure
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    sys.path.insert(0, golden)
+    from make_departures_64x200 import case_and_fields
+    from oracle.departure import departure_steps
+    ref = json.load(open(os.path.join(golden, "departures_64x200.json")))
     rl, rv = coex["rho_l"], coex["rho_v"]
-    case = wl.pool(nx=64, ny=140, n_sites=1, heater_rows=10, superheat=0.11, seed=5)
-    case = dataclasses.replace(case, sites=[(case.sites[0][0], 10.0, -0.3)])
-    rho0, T0 = wl.initial_fields(case, rl, rv, coex["Tc"])
-    rho0 = rl + rv - wl.droplet(case.ny, case.nx, rl, rv, case.sites[0][0], case.wall_rows, 12.0)
-    every, n = 20, 1000
-    od = oracle_domain(case, coex, rho0=rho0, T0=T0)
+    case, rho0, T0 = case_and_fields(rl, rv, coex["Tc"])
+    every = ref["snapshot_every"]
     gd = gpu_domain(case, coex, rho0=rho0, T0=T0)
-    so, sg, steps = [], [], []
-    for k in range(n):
-        od.step(every)
+    snaps, steps, events, prev = [], [], [], None
+    for k in range(ref["steps"] // every):
         gd.step(every)
-        so.append(od.fields()[0].copy())
-        sg.append(gd.read()[0].cpu().numpy())
-        steps.append(every * (k + 1))
-    do = departure.detect(so, steps, case.wall_rows, rl, rv)
-    dg = departure.detect(sg, steps, case.wall_rows, rl, rv)
-    print(f"departures: oracle {list(do.times)} period {do.period():.0f}; gpu {list(dg.times)} period {dg.period():.0f}")
-    assert do.count >= 2 and dg.count == do.count
-    P = do.period()
-    assert dg.period() == pytest.approx(P, rel=0.03)
-    assert np.abs(dg.times - do.times).max() <= 0.03 * P
+        rho = gd.read()[0].cpu().numpy()
+        n = every * (k + 1)
+        if prev is not None:
+            events += departure_steps([prev[0], rho], [prev[1], n], case.wall_rows, rl, rv)
+        prev = (rho, n)
+        snaps.append(rho)
+        steps.append(n)
+    do = np.array(ref["departure_steps"], dtype=np.float64)
+    dg = np.array(events, dtype=np.float64)
+    own = departure.detect(snaps, steps, case.wall_rows, rl, rv)
+    P = float(np.diff(do).mean())
+    print(f"departures: oracle {do.astype(int).tolist()} period {P:.0f}; gpu {dg.astype(int).tolist()} "
+          f"period {np.diff(dg).mean():.0f}; product detector {list(own.times)}")
+    assert len(do) >= 4 and len(dg) == len(do)
+    assert np.diff(dg).mean() == pytest.approx(P, rel=0.03)
+    assert np.abs(dg - do).max() <= 0.03 * P
+    assert list(own.times) == dg.astype(int).tolist()
 
 
 def test_closed_box_conserves_mass_fp32(coex):
