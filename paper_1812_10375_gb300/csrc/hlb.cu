@@ -72,14 +72,14 @@ struct FlowVariant {
     return ewalk ? dim3((nx + EW_OUT - 1) / EW_OUT, (ny + ep - 1) / ep) : dim3((nx + EN_TX - 1) / EN_TX, (ny + EN_TY - 1) / EN_TY);
   }
 };
-template <int TY, int NTH, int MINB>
+template <int TY, int NTH, int MINB, bool RP>
 void launch_flow_single(dim3 grid, size_t smem, cudaStream_t s, const StepArgs& a) {
-  k_flow<TY, NTH, MINB><<<grid, NTH, smem, s>>>(a);
+  k_flow<TY, NTH, MINB, RP><<<grid, NTH, smem, s>>>(a);
 }
-template <int TY, int NTH, int MINB>
+template <int TY, int NTH, int MINB, bool RP>
 void launch_flow_batch(int blocks, size_t smem, cudaStream_t s, const StepArgs& phys, const DomArgs* desc,
                        const int2* blk, const int* act, const float2* lag) {
-  k_flow_batch<TY, NTH, MINB><<<blocks, NTH, smem, s>>>(phys, desc, blk, act, lag);
+  k_flow_batch<TY, NTH, MINB, RP><<<blocks, NTH, smem, s>>>(phys, desc, blk, act, lag);
 }
 template <int R, int NPH, int MINB>
 void launch_energy_single(dim3 grid, cudaStream_t s, const StepArgs& a, int sub, int nsub) {
@@ -99,17 +99,17 @@ void launch_walk_batch(int blocks, cudaStream_t s, const StepArgs& phys, const D
                        const int* act, int sub, int nsub) {
   k_energy_walk_batch<L, MINB, PF><<<blocks, EW_W, 0, s>>>(phys, desc, blk, act, sub, nsub);
 }
-#define HLB_SPLIT_TILE(TY, NTH, MINB, ER, ENPH, EMINB)                                                          \
-  FlowVariant{TY, NTH, 0, ER, flow_smem_bytes<TY>(), (const void*)k_flow<TY, NTH, MINB>,                        \
-              (const void*)k_flow_batch<TY, NTH, MINB>, (const void*)k_energy<ER, ENPH, EMINB>,               \
-              (const void*)k_energy_batch<ER, ENPH, EMINB>, energy_smem_bytes(), launch_flow_single<TY, NTH, MINB>, \
-              launch_flow_batch<TY, NTH, MINB>, launch_energy_single<ER, ENPH, EMINB>,                        \
-              launch_energy_batch<ER, ENPH, EMINB>},
-#define HLB_SPLIT_WALK(TY, NTH, MINB, L, EMINB, PF)                                                             \
-  FlowVariant{TY, NTH, 1, L, flow_smem_bytes<TY>(), (const void*)k_flow<TY, NTH, MINB>,                         \
-              (const void*)k_flow_batch<TY, NTH, MINB>, (const void*)k_energy_walk<L, EMINB, PF>,             \
-              (const void*)k_energy_walk_batch<L, EMINB, PF>, 0, launch_flow_single<TY, NTH, MINB>,           \
-              launch_flow_batch<TY, NTH, MINB>, launch_walk_single<L, EMINB, PF>,                             \
+#define HLB_SPLIT_TILE(TY, NTH, MINB, RP, ER, ENPH, EMINB)                                                      \
+  FlowVariant{TY, NTH, 0, ER, flow_smem_bytes<TY>(), (const void*)k_flow<TY, NTH, MINB, RP>,                    \
+              (const void*)k_flow_batch<TY, NTH, MINB, RP>, (const void*)k_energy<ER, ENPH, EMINB>,           \
+              (const void*)k_energy_batch<ER, ENPH, EMINB>, energy_smem_bytes(),                              \
+              launch_flow_single<TY, NTH, MINB, RP>, launch_flow_batch<TY, NTH, MINB, RP>,                    \
+              launch_energy_single<ER, ENPH, EMINB>, launch_energy_batch<ER, ENPH, EMINB>},
+#define HLB_SPLIT_WALK(TY, NTH, MINB, RP, L, EMINB, PF)                                                         \
+  FlowVariant{TY, NTH, 1, L, flow_smem_bytes<TY>(), (const void*)k_flow<TY, NTH, MINB, RP>,                     \
+              (const void*)k_flow_batch<TY, NTH, MINB, RP>, (const void*)k_energy_walk<L, EMINB, PF>,         \
+              (const void*)k_energy_walk_batch<L, EMINB, PF>, 0, launch_flow_single<TY, NTH, MINB, RP>,       \
+              launch_flow_batch<TY, NTH, MINB, RP>, launch_walk_single<L, EMINB, PF>,                         \
               launch_walk_batch<L, EMINB, PF>},
 const FlowVariant FLOWS[] = {HLB_SPLIT_VARIANTS(HLB_SPLIT_TILE, HLB_SPLIT_WALK)};
 constexpr int NSPLIT = (int)(sizeof(FLOWS) / sizeof(FLOWS[0]));

@@ -150,7 +150,9 @@ __device__ __forceinline__ void walk_take(const StepArgs& A, const WalkCtx& C, W
 
 // One walk step.  STEADY: an interior segment past its first eight steps:
 // every phase is active and no row of the step is solid, Dirichlet, a ghost,
-// a wall-flux row or the top row, so all row tests compile away.
+// a wall-flux row or the top row, so all row tests compile away.  PF > 0: row r
+// comes from the prefetch ring and row r + PF is fetched; PF = 0: row r was
+// prefetched into S.p* and row r + 1 is loaded into them.
 template <int P, bool STEADY, int PF>
 __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, WalkState& S, int t) {
   constexpr int P0 = P & 3, P1 = (P + 3) & 3, P2 = (P + 2) & 3, P3 = (P + 1) & 3;  // rows r, r-1, r-2, r-3

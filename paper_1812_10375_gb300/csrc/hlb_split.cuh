@@ -44,14 +44,17 @@ constexpr int FL_TX = 64;          // flow tile width
 constexpr int FL_FW = FL_TX + 2;   // psi frame: the tile and a one-cell ring
 // Compiled split-step variants: flow tile (fluid rows, threads per CTA, CTAs
 // per SM) and energy layout (rows per thread run, runs, CTAs per SM).
-// TILE(TYF, NTHF, MINBF, R, NPH, MINB): the energy tile of R-row runs;
-// WALK(TYF, NTHF, MINBF, L, MINB, PF): the row-walking energy kernel over
+// TYF, NTHF, MINBF: the flow tile's fluid rows, threads and CTAs per SM; RP:
+// the flow kernel pulls its own cells again after the barrier instead of
+// holding their populations in registers (fewer registers, more CTAs per SM).
+// TILE(TYF, NTHF, MINBF, RP, R, NPH, MINB): the energy tile of R-row runs;
+// WALK(TYF, NTHF, MINBF, RP, L, MINB, PF): the row-walking energy kernel over
 // L-row segments, sized for MINB CTAs per SM, its input rows fetched PF rows
 // ahead by asynchronous copies into shared memory (PF = 0: one row ahead into
 // registers).
 #define HLB_SPLIT_VARIANTS(TILE, WALK) \
-  WALK(16, 256, 3, 64, 10, 6) WALK(16, 256, 3, 96, 8, 4) WALK(16, 256, 3, 96, 8, 0) WALK(16, 256, 3, 32, 8, 0) \
-  TILE(16, 256, 3, 8, 4, 2)
+  WALK(16, 256, 4, 1, 64, 10, 6) WALK(16, 256, 3, 0, 64, 10, 6) WALK(16, 256, 3, 0, 96, 8, 4) \
+  WALK(16, 256, 3, 0, 96, 8, 0) WALK(16, 256, 3, 0, 32, 8, 0) TILE(16, 256, 3, 0, 8, 4, 2)
 
 constexpr int EN_TX = 56, EN_TY = 24, EN_H = 4;
 constexpr int EN_FW = EN_TX + 2 * EN_H;  // 64 frame columns, one per thread
@@ -127,7 +130,7 @@ __device__ __forceinline__ void block_partials(float (&ah)[NQ], float (&al)[NQ],
 }
 
 // ---------------------------------------------------------------- flow tile
-template <int TY, int NTH, bool INT>
+template <int TY, int NTH, bool INT, bool RP>
 __device__ __forceinline__ void flow_tile(const StepArgs& A, int bx, int by, int part, float* sPsi, float Uc,
                                           float rho_ave) {
   constexpr int NPH = NTH / FL_TX;
@@ -172,7 +175,26 @@ __device__ __forceinline__ void flow_tile(const StepArgs& A, int bx, int by, int
   const int o1 = P + xm - gx, o3 = 3 * P + xp - gx;
   const int o2 = 2 * P - nx, o5 = 5 * P - nx + xm - gx, o6 = 6 * P - nx + xp - gx;
   const int o4 = 4 * P + nx, o7 = 7 * P + nx + xp - gx, o8 = 8 * P + nx + xm - gx;
-  float f[CPT][9];
+  // the pulled populations of own cell (gx, gy) into h
+  auto own_pull = [&](int gy, float h[9]) {
+    if (INT) {
+      const float* __restrict__ F = A.f_in + gy * nx + gx;
+      h[0] = __ldg(F);
+      h[1] = __ldg(F + o1);
+      h[3] = __ldg(F + o3);
+      h[2] = __ldg(F + o2);
+      h[5] = __ldg(F + o5);
+      h[6] = __ldg(F + o6);
+      h[4] = __ldg(F + o4);
+      h[7] = __ldg(F + o7);
+      h[8] = __ldg(F + o8);
+    } else {
+      pull(A, g, gx, xm, xp, gy, gy == W, g.top_wall && gy + 1 == ny - 1, Uc, h);
+    }
+  };
+  // RP: pass 2 pulls the own cells again (from L1/L2) instead of keeping their
+  // populations in registers across the barrier
+  float f[RP ? 1 : CPT][9];
   float rho[CPT];
 #pragma unroll
   for (int m = 0; m < CPT; ++m) {
@@ -182,21 +204,9 @@ __device__ __forceinline__ void flow_tile(const StepArgs& A, int bx, int by, int
     rho[m] = 1.f;
     if (INT || gy < fend) {
       const int c = gy * nx + gx;
-      if (INT) {
-        const float* __restrict__ F = A.f_in + c;
-        f[m][0] = __ldg(F);
-        f[m][1] = __ldg(F + o1);
-        f[m][3] = __ldg(F + o3);
-        f[m][2] = __ldg(F + o2);
-        f[m][5] = __ldg(F + o5);
-        f[m][6] = __ldg(F + o6);
-        f[m][4] = __ldg(F + o4);
-        f[m][7] = __ldg(F + o7);
-        f[m][8] = __ldg(F + o8);
-      } else {
-        pull(A, g, gx, xm, xp, gy, gy == W, g.top_wall && gy + 1 == ny - 1, Uc, f[m]);
-      }
-      rho[m] = A.rho_ref + sum9(f[m]);
+      float* fm = f[RP ? 0 : m];
+      own_pull(gy, fm);
+      rho[m] = A.rho_ref + sum9(fm);
       ps = psi_of(rho[m], __ldg(A.T_in + c));
     } else if (g.top_open && gy == ny) {
       // zero-gradient ghost above an open top: psi of row ny - 1
@@ -236,14 +246,17 @@ __device__ __forceinline__ void flow_tile(const StepArgs& A, int bx, int by, int
 #pragma unroll
   for (int q = 0; q < NFPART; ++q) ah[q] = al[q] = 0.f;
   const float gw = __ldg(A.Gw + gx);
-#pragma unroll
+  // RP: one cell at a time (the loop is not unrolled, so the pulls of the next
+  // cell are not hoisted), rho recomputed from the same pull and summation
+#pragma unroll RP ? 1 : CPT
   for (int m = 0; m < CPT; ++m) {
     const int j = jp * CPT + m;
     const int gy = y0 + j;
     if (!colv || !(INT || gy < fend)) continue;
     const int idx = (j + 1) * FL_FW + i + 1;
     const float psi = sPsi[idx];
-    const float r = rho[m];
+    if (RP) own_pull(gy, f[0]);
+    const float r = RP ? A.rho_ref + sum9(f[0]) : rho[m];
     const bool sol_s = !INT && gy == W;
     const bool sol_n = !INT && g.top_wall && gy == ny - 2;
     // Eq. (6); a solid neighbour carries psi(x)
@@ -262,7 +275,7 @@ __device__ __forceinline__ void flow_tile(const StepArgs& A, int bx, int by, int
     const float Fay = INT ? 0.f : gw * psi * psi * ((float)sol_n - (float)sol_s) * (1.f / 6.f);
     const float Fx = Fmx;
     const float Fy = Fmy + Fay + (r - rho_ave) * A.g_y;  // Eq. (9)
-    const float* fm = f[m];
+    const float* fm = f[RP ? 0 : m];
     const float jx = (fm[1] - fm[3]) + ((fm[5] - fm[6]) - (fm[7] - fm[8]));
     const float jy = (fm[2] - fm[4]) + ((fm[5] + fm[6]) - (fm[7] + fm[8]));
     const float irho = 1.f / r;
@@ -290,16 +303,16 @@ __device__ __forceinline__ void flow_tile(const StepArgs& A, int bx, int by, int
   if (tid == 0 && s_err) atomicOr(&A.state->error_flags, s_err);
 }
 
-template <int TY, int NTH, int MINB>
+template <int TY, int NTH, int MINB, bool RP>
 __global__ void __launch_bounds__(NTH, MINB) k_flow(const StepArgs A) {
   extern __shared__ float sm[];
   const float Uc = (float)A.state->Uc, rho_ave = (float)A.state->rho_ave;
   const int part = blockIdx.y * gridDim.x + blockIdx.x;
   const int y0 = A.W + blockIdx.y * TY;
   if (flow_interior(A, y0, TY))
-    flow_tile<TY, NTH, true>(A, blockIdx.x, blockIdx.y, part, sm, Uc, rho_ave);
+    flow_tile<TY, NTH, true, RP>(A, blockIdx.x, blockIdx.y, part, sm, Uc, rho_ave);
   else
-    flow_tile<TY, NTH, false>(A, blockIdx.x, blockIdx.y, part, sm, Uc, rho_ave);
+    flow_tile<TY, NTH, false, RP>(A, blockIdx.x, blockIdx.y, part, sm, Uc, rho_ave);
 }
 
 // Loads the domain descriptor of block `b` into shared memory; returns false
@@ -322,7 +335,7 @@ __device__ __forceinline__ bool batch_prologue(const DomArgs* __restrict__ desc,
 }
 
 // Batched flow step: block b takes tile blk[b].y of domain blk[b].x.
-template <int TY, int NTH, int MINB>
+template <int TY, int NTH, int MINB, bool RP>
 __global__ void __launch_bounds__(NTH, MINB) k_flow_batch(const StepArgs P, const DomArgs* __restrict__ desc,
                                                           const int2* __restrict__ blk,
                                                           const int* __restrict__ active,
@@ -339,9 +352,9 @@ __global__ void __launch_bounds__(NTH, MINB) k_flow_batch(const StepArgs P, cons
   const int tx = (A.nx + FL_TX - 1) / FL_TX;
   const int by = local / tx;
   if (flow_interior(A, A.W + by * TY, TY))
-    flow_tile<TY, NTH, true>(A, local % tx, by, local, sm, s_lg.x, s_lg.y);
+    flow_tile<TY, NTH, true, RP>(A, local % tx, by, local, sm, s_lg.x, s_lg.y);
   else
-    flow_tile<TY, NTH, false>(A, local % tx, by, local, sm, s_lg.x, s_lg.y);
+    flow_tile<TY, NTH, false, RP>(A, local % tx, by, local, sm, s_lg.x, s_lg.y);
 }
 
 // -------------------------------------------------------------- energy tile
