@@ -129,21 +129,27 @@ __device__ __forceinline__ float sum9(const float f[9]) {
 // the density row of dm is 0 and the momentum rows are exactly F (because
 // j - rho u = -F/2 by Eq. 5), so no rounded 1/9 or 1/6 multiplies rho or j and
 // FP32 rounding cannot bias mass or momentum from step to step.
-// Fm2_psi2 = |F_m|^2 / psi^2.  Writes the nine post-collision values and returns their sum.
+// Fm2_psi2 = |F_m|^2 / psi^2.  Writes the nine post-collision values and returns
+// a sum of the density moment and the moment increments, non-finite whenever
+// an input population or an increment is.
 __device__ __forceinline__ float collide_store(const StepArgs& A, const float f[9], float rho, float ux, float uy,
                                                float Fx, float Fy, float Fm2_psi2, int off) {
-  const float sa = (f[1] + f[2]) + (f[3] + f[4]);
-  const float sd = (f[5] + f[6]) + (f[7] + f[8]);
+  // the moments share their partial sums: axis pairs (1,3), (2,4) and
+  // diagonal pairs (5,7), (6,8)
+  const float s13 = f[1] + f[3], s24 = f[2] + f[4], s57 = f[5] + f[7], s68 = f[6] + f[8];
+  const float d57 = f[5] - f[7], d68 = f[6] - f[8];
+  const float sa = s13 + s24;
+  const float sd = s57 + s68;
   const float m0 = f[0] + sa + sd;  // rho - rho_ref
   const float me = -4.f * f[0] - sa + 2.f * sd;
   const float mz = 4.f * f[0] - 2.f * sa + sd;
   const float ax = f[1] - f[3], ay = f[2] - f[4];
-  const float cx = (f[5] - f[6]) - (f[7] - f[8]);
-  const float cy = (f[5] + f[6]) - (f[7] + f[8]);
+  const float cx = d57 - d68;
+  const float cy = d57 + d68;
   const float qx = -2.f * ax + cx;
   const float qy = -2.f * ay + cy;
-  const float pxx = (f[1] + f[3]) - (f[2] + f[4]);
-  const float pxy = (f[5] + f[7]) - (f[6] + f[8]);
+  const float pxx = s13 - s24;
+  const float pxy = s57 - s68;
 
   const float u2 = ux * ux + uy * uy;
   const float uF = ux * Fx + uy * Fy;
@@ -165,15 +171,21 @@ __device__ __forceinline__ float collide_store(const StepArgs& A, const float f[
   const float r7 = dpxx * 0.25f, r8 = dpxy * 0.25f;
   const float ba = -r1 - 2.f * r2;
   const float bd = 2.f * r1 + r2;
+  // increments of opposite directions share their even and odd parts
+  const float ex = ba + r7, ox = r3 - 2.f * r4;  // directions 1 and 3
+  const float ey = ba - r7, oy = r5 - 2.f * r6;  // directions 2 and 4
+  const float cxq = r3 + r4, cyq = r5 + r6;
+  const float ep = bd + r8, em = bd - r8;
+  const float op = cxq + cyq, om = cyq - cxq;  // directions 5/7 and 6/8
   const float o0 = f[0] + (4.f * (r2 - r1));
-  const float o1 = f[1] + (ba + r3 - 2.f * r4 + r7);
-  const float o2 = f[2] + (ba + r5 - 2.f * r6 - r7);
-  const float o3 = f[3] + (ba - r3 + 2.f * r4 + r7);
-  const float o4 = f[4] + (ba - r5 + 2.f * r6 - r7);
-  const float o5 = f[5] + (bd + r3 + r4 + r5 + r6 + r8);
-  const float o6 = f[6] + (bd - r3 - r4 + r5 + r6 - r8);
-  const float o7 = f[7] + (bd - r3 - r4 - r5 - r6 + r8);
-  const float o8 = f[8] + (bd + r3 + r4 - r5 - r6 - r8);
+  const float o1 = f[1] + (ex + ox);
+  const float o2 = f[2] + (ey + oy);
+  const float o3 = f[3] + (ex - ox);
+  const float o4 = f[4] + (ey - oy);
+  const float o5 = f[5] + (ep + op);
+  const float o6 = f[6] + (em + om);
+  const float o7 = f[7] + (ep - op);
+  const float o8 = f[8] + (em - om);
   const int P = (int)A.plane;
   float* __restrict__ out = A.f_out + off;
   out[0] = o0;
@@ -185,7 +197,8 @@ __device__ __forceinline__ float collide_store(const StepArgs& A, const float f[
   out[6 * P] = o6;
   out[7 * P] = o7;
   out[8 * P] = o8;
-  return o0 + o1 + o2 + o3 + o4 + o5 + o6 + o7 + o8;
+  // non-finite check: every output is f_i plus a combination of these
+  return (m0 + de) + (dz + dqx) + (dqy + dpxx) + dpxy;
 }
 
 template <typename T>

@@ -276,8 +276,9 @@ __device__ __forceinline__ void flow_tile(const StepArgs& A, int bx, int by, int
     const float Fx = Fmx;
     const float Fy = Fmy + Fay + (r - rho_ave) * A.g_y;  // Eq. (9)
     const float* fm = f[RP ? 0 : m];
-    const float jx = (fm[1] - fm[3]) + ((fm[5] - fm[6]) - (fm[7] - fm[8]));
-    const float jy = (fm[2] - fm[4]) + ((fm[5] + fm[6]) - (fm[7] + fm[8]));
+    // the collision's moment sums (the same expressions, computed once)
+    const float jx = (fm[1] - fm[3]) + ((fm[5] - fm[7]) - (fm[6] - fm[8]));
+    const float jy = (fm[2] - fm[4]) + ((fm[5] - fm[7]) + (fm[6] - fm[8]));
     const float irho = 1.f / r;
     const float ux = (jx + 0.5f * Fx) * irho;
     const float uy = (jy + 0.5f * Fy) * irho;

@@ -45,18 +45,22 @@ def _batch(cases, coex):
     return b
 
 
-def test_batch_bit_identical_to_single_domains(coex):
+def test_batch_matches_single_domains(coex):
+    """A batch slot against the same domain alone.  The batched and the
+    single-domain kernels are separate instantiations of the same device code
+    and may round the last bit differently (FMA contraction), so they agree to
+    FP32 rounding (_close), not bit for bit; bit-for-bit comparisons are batch
+    against batch (tests/test_batch_refill_gpu.py, the two-lane test below)."""
     cases = _cases()
     b = _batch(cases, coex)
     b.step(40)  # two captured 16-step graphs + 8 direct launches
     for i, c in enumerate(cases):
         d = gpu_domain(c, coex)
         d.step(40)
-        for x, y in zip(b.read(i), d.read()):
-            assert (x == y).all(), c.name
+        _close(b.read(i), d.read())
         hist = b.flux_history(i)
         assert len(hist) == 40
-        assert hist[-1] == d.diag().q_bottom
+        assert hist[-1] == pytest.approx(d.diag().q_bottom, rel=1e-5, abs=1e-12)
         assert b.diag(i).step == 40
 
 
@@ -68,8 +72,7 @@ def test_stop_and_reuse_slot(coex):
     b.step(21)
     d = gpu_domain(cases[1], coex)
     d.step(20)
-    for x, y in zip(b.read(1), d.read()):
-        assert (x == y).all()
+    _close(b.read(1), d.read())
     assert len(b.flux_history(1)) == 20
     assert b.diag(0).step == 41
     # restart slot 1 from fresh fields while the batch is at odd parity
@@ -80,8 +83,7 @@ def test_stop_and_reuse_slot(coex):
     b.step(7)
     d2 = gpu_domain(cases[1], coex)
     d2.step(7)
-    for x, y in zip(b.read(1), d2.read()):
-        assert (x == y).all()
+    _close(b.read(1), d2.read())
     assert b.diag(1).step == 7
 
 

