@@ -53,8 +53,8 @@ constexpr int FL_FW = FL_TX + 2;   // psi frame: the tile and a one-cell ring
 // ahead by asynchronous copies into shared memory (PF = 0: one row ahead into
 // registers).
 #define HLB_SPLIT_VARIANTS(TILE, WALK) \
-  WALK(16, 256, 4, 1, 64, 10, 6) WALK(16, 256, 3, 0, 64, 10, 6) WALK(16, 256, 3, 0, 96, 8, 4) \
-  WALK(16, 256, 3, 0, 96, 8, 0) WALK(16, 256, 3, 0, 32, 8, 0) TILE(16, 256, 3, 0, 8, 4, 2)
+  WALK(24, 256, 4, 1, 64, 10, 6) WALK(16, 256, 4, 1, 64, 10, 6) WALK(16, 256, 3, 0, 64, 10, 6) \
+  WALK(16, 256, 3, 0, 96, 8, 4) WALK(16, 256, 3, 0, 96, 8, 0) TILE(16, 256, 3, 0, 8, 4, 2)
 
 constexpr int EN_TX = 56, EN_TY = 24, EN_H = 4;
 constexpr int EN_FW = EN_TX + 2 * EN_H;  // 64 frame columns, one per thread
