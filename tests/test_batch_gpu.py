@@ -87,6 +87,50 @@ def test_stop_and_reuse_slot(coex):
     assert b.diag(1).step == 7
 
 
+def test_steps_with_every_slot_stopped_change_nothing(coex):
+    """The empty case of the early-stop path: with every slot stopped a step
+    launches blocks that all return at once.  Fields, checkpoints (state,
+    outlet memory and history) and step counters stay as they were, bit for
+    bit, no error is raised, and a slot refilled afterwards runs as a fresh
+    batch does."""
+    import torch
+    cases = _cases()
+    b = _batch(cases, coex)
+    b.step(9)  # odd: the batch stops at buffer parity 1
+    for i in range(len(cases)):
+        b.stop(i)
+    before = [([t.cpu().numpy() for t in b.read(i)], b.checkpoint(i), b.diag(i).step) for i in range(len(cases))]
+    b.step(37)  # two captured graphs and five direct launches over stopped slots
+    for i in range(len(cases)):
+        fields, ck, step = before[i]
+        for x, y in zip(fields, b.read(i)):
+            assert np.array_equal(x, y.cpu().numpy()), i
+        assert b.checkpoint(i) == ck and b.diag(i).step == step == 9
+        assert b.diag(i).error_flags == 0
+    rho0, T0 = wl.initial_fields(cases[2], coex["rho_l"], coex["rho_v"], coex["Tc"])
+    b.set_fields(2, torch.tensor(rho0, dtype=torch.float32, device="cuda"),
+                 torch.tensor(T0, dtype=torch.float32, device="cuda"))
+    b.set_nucleation_sites(2, cases[2].sites)
+    b.step(11)
+    fresh = _batch(cases, coex)
+    fresh.step(11)
+    for x, y in zip(b.read(2), fresh.read(2)):
+        assert np.array_equal(x.cpu().numpy(), y.cpu().numpy())
+    assert b.diag(2).step == 11 and b.diag(0).step == 9
+
+
+def test_batch_of_one_domain(coex):
+    """The smallest batch: one domain (one lane, no lane split) against the
+    same domain alone, through graph replay and direct launches."""
+    case = _cases()[3]
+    b = _batch([case], coex)
+    b.step(35)
+    d = gpu_domain(case, coex)
+    d.step(35)
+    _close(b.read(0), d.read())
+    assert b.diag(0).step == 35 and len(b.flux_history(0)) == 35
+
+
 def _close(fields, ref):
     """Two kernel variants evaluate a cell's update with the same arithmetic but
     may round differently (tiled and row-marching kernels) and sum the FP64
