@@ -25,8 +25,10 @@ populations that entered it at the previous step) stays with the top rank.
 
 This module holds no arithmetic of the method: the slab bounds, the halo
 width, and the send/receive schedule of one exchange, with `exchange`
-moving row blocks of numpy arrays over torch.distributed point-to-point
-calls (gloo on the CPU, NCCL with device buffers).
+moving row blocks of host (numpy) arrays over torch.distributed
+point-to-point calls on a gloo group.  A device-resident slab would follow
+the same schedule with device tensors over NCCL; that path is not built
+here (one GPU per process and no multi-GPU host to run it on).
 """
 from __future__ import annotations
 
