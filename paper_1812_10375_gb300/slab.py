@@ -27,8 +27,7 @@ This module holds no arithmetic of the method: the slab bounds, the halo
 width, and the send/receive schedule of one exchange, with `exchange`
 moving row blocks of host (numpy) arrays over torch.distributed
 point-to-point calls on a gloo group.  A device-resident slab would follow
-the same schedule with device tensors over NCCL; that path is not built
-here (one GPU per process and no multi-GPU host to run it on).
+the same schedule with device tensors over NCCL; that path is not built.
 """
 from __future__ import annotations
 
