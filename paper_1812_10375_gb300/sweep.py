@@ -352,20 +352,63 @@ def choose_threshold(ens, results, L0, tol=0.03, floor=0.5):
 def policy_score(prob, kind):
     """Acceptance score from the ensemble-mean regime probabilities: 'not_film'
     is the probability that the point does not end in film boiling (the vapour
-    film forms late, after the history window); 'no_boiling' the probability
-    that it does not boil at all, where the quasi-steady flux is a fixed
-    fraction of the early flux (transient conduction)."""
+    film forms late, after the history window); 'no_boiling' and
+    'no_boiling_ratio' the probability that it does not boil at all, where the
+    quasi-steady flux is a fixed fraction of the early flux (transient
+    conduction)."""
     return 1.0 - prob[:, -1] if kind == "not_film" else prob[:, 0]
 
 
-def choose_policy(ens, results, L0, tol=0.03, floor=0.5, kind="not_film"):
+# The 'no_boiling_ratio' policy takes the network's regime probabilities but
+# not its flux: a point that does not boil conducts heat from the heater into
+# the liquid, and its quasi-steady wall flux is the mean flux of the last
+# RATIO_WIN steps of the history window times a ratio set by the geometry
+# (the heater, the materials and the initial fields are the same for every
+# sweep point; only the side nx differs), fitted on the training points that
+# ended without boiling.
+RATIO_WIN = 500
+
+
+def late_flux(history, hist_steps):
+    """Mean wall flux over the last RATIO_WIN steps of the first hist_steps."""
+    h = np.asarray(history, dtype=np.float64)[:hist_steps]
+    return float(h[-RATIO_WIN:].mean())
+
+
+def fit_conduction_ratio(results, hist_steps):
+    """Least-squares (c0, c1) of q_qs / late_flux = c0 + c1 / nx over the
+    results of regime 0 (no boiling); (0, 0) with fewer than two of them."""
+    rows = [r for r in results if r.regime == 0]
+    if len(rows) < 2:
+        return 0.0, 0.0
+    A = np.array([[1.0, 1.0 / r.case.nx] for r in rows])
+    y = np.array([r.q_qs / late_flux(r.history, hist_steps) for r in rows])
+    c0, c1 = np.linalg.lstsq(A, y, rcond=None)[0]
+    return float(c0), float(c1)
+
+
+def conduction_q(ratio, nx, history, hist_steps):
+    """The 'no_boiling_ratio' prediction of the quasi-steady flux of a point."""
+    return (ratio[0] + ratio[1] / nx) * late_flux(history, hist_steps)
+
+
+def policy_q(kind, qp, results, ratio, hist_steps):
+    """Predicted quasi-steady flux of each result under a policy kind."""
+    if kind != "no_boiling_ratio":
+        return qp
+    return np.array([conduction_q(ratio, r.case.nx, r.history, hist_steps) for r in results])
+
+
+def choose_policy(ens, results, L0, tol=0.03, floor=0.5, kind="not_film", ratio=(0.0, 0.0), hist_steps=None):
     """Acceptance by score and ensemble agreement: among the pairs (score
     threshold, spread limit) taken from the calibration points, the one that
     accepts the most calibration points while every accepted one stays within
     `tol` of its full run.  Returns (score threshold, spread limit); (1.01, 0)
-    accepts nothing."""
+    accepts nothing.  `ratio` and `hist_steps` serve the 'no_boiling_ratio'
+    kind (conduction_q)."""
     hist, scal, q, _ = features(results, L0)
     qp, spread, prob = ens.predict(hist, scal)
+    qp = policy_q(kind, qp, results, ratio, hist_steps)
     score = policy_score(prob, kind)
     err = np.abs(qp - q) / np.maximum(np.abs(q), 1e-12)
     best, best_n = (1.01, 0.0), 0
@@ -378,14 +421,17 @@ def choose_policy(ens, results, L0, tol=0.03, floor=0.5, kind="not_film"):
     return best
 
 
-def evaluate_policy(ens, results, L0, threshold, hist_steps, full_steps, cells, spread_max=None, kind="not_film"):
+def evaluate_policy(ens, results, L0, threshold, hist_steps, full_steps, cells, spread_max=None, kind="not_film",
+                    ratio=(0.0, 0.0)):
     """Stop a point after `hist_steps` when its acceptance score reaches the
-    threshold (the ensemble-mean prediction is then the point's result), else
-    run it in full.  Returns the accepted mask, the relative errors of the
-    accepted points against their full runs, and the cell updates spent
-    relative to running every point in full."""
+    threshold (the policy's prediction is then the point's result: the
+    ensemble mean, or conduction_q for 'no_boiling_ratio'), else run it in
+    full.  Returns the accepted mask, the relative errors of the accepted
+    points against their full runs, and the cell updates spent relative to
+    running every point in full."""
     hist, scal, q, _ = features(results, L0)
     qp, spread, prob = ens.predict(hist, scal)
+    qp = policy_q(kind, qp, results, ratio, hist_steps)
     score = policy_score(prob, kind)
     acc = score >= threshold
     if spread_max is not None:
@@ -413,10 +459,11 @@ def train_policy(n=256, full=40000, hist_steps=5000, n_fit=160, members=4, epoch
 
     n sweep points (seed TRAIN_SEED, sides 256-512) run `full` steps in one
     batch; the ensemble is fitted by the CUDA kernels on the first n_fit; on
-    the remaining points (calibration only) the policy kind ('no_boiling' or
-    'not_film'), the score threshold and the ensemble-spread limit are chosen
+    the remaining points (calibration only) the policy kind ('no_boiling',
+    'not_film' or 'no_boiling_ratio', whose conduction ratio is fitted on the
+    fit points), the score threshold and the ensemble-spread limit are chosen
     that accept the most calibration points with every accepted one within
-    `tol` of its full run (2%, under the 3% bar, to leave room for unseen
+    `tol` of its full run (below the 3% bar, to leave room for unseen
     points).  Writes the ensemble and the policy to `out` (policy_path())."""
     import os
     from .surrogate import Ensemble
@@ -432,17 +479,18 @@ def train_policy(n=256, full=40000, hist_steps=5000, n_fit=160, members=4, epoch
     L0 = ens.members[0].net.cfg.L0
     hist, scal, q, lab = features(fit, L0)
     ens.fit(hist, scal, q, lab, epochs=epochs, batch=64, lr=1e-3)
+    ratio = fit_conduction_ratio(fit, hist_steps)
     best = None
-    for kind in ("no_boiling", "not_film"):
-        thr, smax = choose_policy(ens, cal, L0, tol=tol, kind=kind)
+    for kind in ("no_boiling", "not_film", "no_boiling_ratio"):
+        thr, smax = choose_policy(ens, cal, L0, tol=tol, kind=kind, ratio=ratio, hist_steps=hist_steps)
         acc, err, _ = evaluate_policy(ens, cal, L0, thr, hist_steps, full, [r.case.nx * r.case.ny for r in cal],
-                                      spread_max=smax, kind=kind)
+                                      spread_max=smax, kind=kind, ratio=ratio)
         if best is None or int(acc.sum()) > best[3]:
             best = (kind, thr, smax, int(acc.sum()), float(err.max()) if len(err) else 0.0)
     kind, thr, smax, n_acc, e_max = best
     meta = dict(kind=kind, threshold=thr, spread_max=smax, hist_steps=hist_steps, full_steps=full, tol=tol,
                 calibration_points=len(cal), calibration_accepted=n_acc, calibration_max_error=e_max,
-                train_seed=TRAIN_SEED, fit_points=n_fit)
+                train_seed=TRAIN_SEED, fit_points=n_fit, cond_c0=ratio[0], cond_c1=ratio[1])
     ens.save(out or policy_path(), **meta)
     return meta
 
@@ -477,6 +525,7 @@ def pph_study(n=32, full=40000, slots_per_size=None, seed=STUDY_SEED, policy=Non
     ens, meta = Ensemble.load(policy or policy_path())
     kind, thr = str(meta["kind"]), float(meta["threshold"])
     smax, hs = float(meta["spread_max"]), int(meta["hist_steps"])
+    ratio = (float(meta.get("cond_c0", 0.0)), float(meta.get("cond_c1", 0.0)))
     L0 = ens.members[0].net.cfg.L0
     pts = make_points(n, seed=seed)
     sizes = sorted(set(c.nx for c in pts))
@@ -542,7 +591,8 @@ def pph_study(n=32, full=40000, slots_per_size=None, seed=STUDY_SEED, policy=Non
                     scal = np.array([[c.T_bottom_over_Tc - wl.TS_OVER_TC, len(c.sites) / 10.0]])
                     qp, spread, prob = ens.predict(hist, scal)
                     if policy_score(prob, kind)[0] >= thr and spread[0] <= smax:
-                        done = dict(q=float(qp[0]), steps=hs, accepted=True)
+                        qk = conduction_q(ratio, c.nx, h, hs) if kind == "no_boiling_ratio" else float(qp[0])
+                        done = dict(q=qk, steps=hs, accepted=True)
                 if done is None:
                     continue
                 rec[k] = done
@@ -578,6 +628,7 @@ def pph_study(n=32, full=40000, slots_per_size=None, seed=STUDY_SEED, policy=Non
             "accepted_max_error": max(err) if err else 0.0,
             "accepted_errors": sorted(round(float(e), 5) for e in err), "work_fraction": float(spent),
             "policy": {"kind": kind, "threshold": thr, "spread_max": smax, "hist_steps": hs,
+                       "conduction_ratio": list(ratio) if kind == "no_boiling_ratio" else None,
                        "calibration_max_error": float(meta["calibration_max_error"]),
                        "calibration_accepted": int(meta["calibration_accepted"]),
                        "calibration_points": int(meta["calibration_points"])},

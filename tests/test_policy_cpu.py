@@ -105,3 +105,58 @@ def test_regime_labels_follow_the_coverage_edges():
     edges = list(sur.COVERAGE_EDGES)
     assert [sur.regime_of(c) for c in [0.0] + edges + [1.0]] == [0] + list(range(1, len(edges) + 1)) + [len(edges)]
     assert all(sur.regime_of(e - 1e-9) == k for k, e in enumerate(edges))
+
+
+def _ratio_results(c0, c1, rng, n=12, hs=2000, full_scale=None):
+    """Regime-0 results whose quasi-steady flux is exactly (c0 + c1/nx) times
+    the mean of the last RATIO_WIN history steps, plus boiling ones (regime 2)
+    whose flux is unrelated."""
+    out = []
+    for k in range(n):
+        nx = int(rng.choice([256, 320, 384, 448, 512]))
+        case = SimpleNamespace(nx=nx, ny=nx, T_bottom_over_Tc=0.9, sites=[(1.0, 2.0, 0.0)] * 3)
+        hist = 1.0 + rng.random(hs)
+        late = hist[-sweep.RATIO_WIN:].mean()
+        boiling = k % 3 == 2
+        q = 5.0 * late if boiling else (c0 + c1 / nx) * late
+        out.append(sweep.PointResult(case, 0.05, 3, hist, float(q), 0.0, 2 if boiling else 0))
+    return out
+
+
+def test_conduction_ratio_is_recovered_from_regime_0_points():
+    rng = np.random.default_rng(11)
+    res = _ratio_results(0.45, -2.0, rng)
+    c0, c1 = sweep.fit_conduction_ratio(res, 2000)
+    assert c0 == pytest.approx(0.45, rel=1e-9) and c1 == pytest.approx(-2.0, rel=1e-7)
+    r = res[0]
+    assert sweep.conduction_q((c0, c1), r.case.nx, r.history, 2000) == pytest.approx(r.q_qs, rel=1e-9)
+    # the window is the last RATIO_WIN steps of the first hist_steps, whatever follows
+    longer = np.concatenate([r.history, np.full(500, 1e6)])
+    assert sweep.late_flux(longer, 2000) == pytest.approx(r.history[-sweep.RATIO_WIN:].mean())
+    assert sweep.fit_conduction_ratio([res[2]], 2000) == (0.0, 0.0)  # no regime-0 point
+
+
+def test_ratio_policy_takes_the_ratio_prediction_and_the_no_boiling_score():
+    """The 'no_boiling_ratio' kind ignores the ensemble's flux: with exact
+    ratios every regime-0 point is within any tolerance, boiling ones are 400%
+    off, so the best pair accepts exactly the points whose no-boiling score
+    lies above every boiling point's (brute force over the same candidates)."""
+    rng = np.random.default_rng(5)
+    res = _ratio_results(0.44, -1.5, rng, n=15)
+    n = len(res)
+    qp = np.full(n, 123.0)  # a useless network flux
+    p_none = rng.random(n) * 0.5 + np.array([0.5 if r.regime == 0 else 0.0 for r in res])
+    spread = np.zeros(n)
+    ens = StandIn(qp, spread, _prob(p_none, np.zeros(n)))
+    ratio = sweep.fit_conduction_ratio(res, 2000)
+    thr, smax = sweep.choose_policy(ens, res, L0, tol=0.01, floor=0.3, kind="no_boiling_ratio", ratio=ratio,
+                                    hist_steps=2000)
+    boil = np.array([r.regime != 0 for r in res])
+    expect = int(((p_none > p_none[boil].max()) & ~boil).sum())
+    acc = (p_none >= thr) & (spread <= smax)
+    assert int(acc.sum()) == expect > 0 and not (acc & boil).any()
+    acc2, err, frac = sweep.evaluate_policy(ens, res, L0, thr, 2000, 40000, [r.case.nx ** 2 for r in res],
+                                            spread_max=smax, kind="no_boiling_ratio", ratio=ratio)
+    assert acc2.tolist() == acc.tolist() and err.max() < 1e-9
+    # the same points under the network's flux are all rejected
+    assert sweep.choose_policy(ens, res, L0, tol=0.01, floor=0.3, kind="no_boiling") == (1.01, 0.0)
