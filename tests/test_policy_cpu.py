@@ -160,3 +160,20 @@ def test_ratio_policy_takes_the_ratio_prediction_and_the_no_boiling_score():
     assert acc2.tolist() == acc.tolist() and err.max() < 1e-9
     # the same points under the network's flux are all rejected
     assert sweep.choose_policy(ens, res, L0, tol=0.01, floor=0.3, kind="no_boiling") == (1.01, 0.0)
+
+
+def test_frozen_policy_metadata_is_consistent():
+    """The committed policy file is one train_policy writes: a known kind, a
+    score threshold in range, calibration errors within its tolerance and
+    under the 3% bar, and (for the ratio kind) a conduction ratio that keeps
+    c0 + c1/nx between 0.4 and 0.5 for the sweep's sides."""
+    z = np.load(sweep.policy_path())
+    kind = str(z["kind"][()])
+    assert kind in ("no_boiling", "not_film", "no_boiling_ratio")
+    assert 0.5 <= float(z["threshold"]) <= 1.01
+    assert int(z["calibration_accepted"]) <= int(z["calibration_points"])
+    assert float(z["calibration_max_error"]) <= float(z["tol"]) < 0.03
+    assert int(z["hist_steps"]) < int(z["full_steps"])
+    if kind == "no_boiling_ratio":
+        c0, c1 = float(z["cond_c0"]), float(z["cond_c1"])
+        assert all(0.4 < c0 + c1 / nx < 0.5 for nx in (256, 320, 384, 448, 512))
