@@ -38,7 +38,7 @@ constexpr int EW_OFF_TN = 0, EW_OFF_T1 = EW_RTN * EW_W, EW_OFF_T2 = EW_OFF_T1 + 
               EW_OFF_PF = EW_OFF_LAM + EW_R * EW_W;
 // The rings of the walking kernels, at a fixed layout so that every access is
 // an immediate offset from one shared-memory base.
-__shared__ float s_walk[EW_SMEM_FLOATS];
+__shared__ __align__(16) float s_walk[EW_SMEM_FLOATS];
 
 // Per-thread state of the walk.  Arrays indexed [row & 3] are row rings; the
 // walk is unrolled by four so that every index is a compile-time constant.
@@ -66,6 +66,9 @@ struct WalkCtx {
   bool own_col;
   int ys, ye;  // output rows of the segment
   bool last;
+  // prefetch in 16-byte pieces (nx a multiple of 4): this thread's piece of
+  // row y starts at vsrc + y * nx in the lattice
+  const float* vsrc;
 };
 
 // RK4 right-hand side at one cell from the coefficient row and the 3 x 3 stencil.
@@ -109,26 +112,36 @@ __device__ __forceinline__ void walk_load(const StepArgs& A, const WalkCtx& C, W
 
 // Start the copies of row `row` (clamped to the lattice: the ghost rows above
 // it repeat row ny - 1) into its prefetch slot; rows below the lattice are not
-// read.  Every call commits one group, empty or not, so that the groups of the
-// rows in flight stay counted.
+// read.  With 16-byte rows (nx a multiple of 4) the CTA's 64 threads copy the
+// 4 planes x 64 frame columns as 64 pieces of 4 columns, one per thread (a
+// piece starts on a multiple of 4 and never straddles the periodic edge);
+// otherwise each thread copies its own column of the 4 planes.  Every call
+// commits one group, empty or not, so that the groups of the rows in flight
+// stay counted.
+template <bool VEC>
 __device__ __forceinline__ void walk_fetch(const StepArgs& A, const WalkCtx& C, int row) {
   if (row >= 0) {
     const int gr = row < A.ny ? row : A.ny - 1;
-    const int c = gr * A.nx + C.gx;
-    cp_async4(&PFW(0, row, C.i), C.T_in + c);
-    cp_async4(&PFW(1, row, C.i), C.rho_n + c);
-    cp_async4(&PFW(2, row, C.i), C.ux_n + c);
-    cp_async4(&PFW(3, row, C.i), C.uy_n + c);
+    if constexpr (VEC) {
+      const int dst = (C.i >> 4) * EW_RPF * EW_W + 4 * (C.i & 15);  // plane i / 16, columns 4 (i % 16) ..
+      cp_async16(&s_walk[EW_OFF_PF + dst + (row & (EW_RPF - 1)) * EW_W], C.vsrc + gr * A.nx);
+    } else {
+      const int c = gr * A.nx + C.gx;
+      cp_async4(&PFW(0, row, C.i), C.T_in + c);
+      cp_async4(&PFW(1, row, C.i), C.rho_n + c);
+      cp_async4(&PFW(2, row, C.i), C.ux_n + c);
+      cp_async4(&PFW(3, row, C.i), C.uy_n + c);
+    }
   }
   cp_async_commit();
 }
 
-// Row `row` from its prefetch slot (its copies complete: PF - 1 younger groups
-// may still be in flight), with the substitutions of walk_load: zeros below
-// the lattice, the wall temperature on Dirichlet rows, no rho or u on solid rows.
+// Row `row` from its prefetch slot, with the substitutions of walk_load: zeros
+// below the lattice, the wall temperature on Dirichlet rows, no rho or u on
+// solid rows.  The slot's copies (made by other threads) completed before the
+// last barrier of the previous walk step (walk_step waits for them there).
 template <bool STEADY, int PF>
 __device__ __forceinline__ void walk_take(const StepArgs& A, const WalkCtx& C, WalkState& S, int row) {
-  cp_async_wait<PF - 1>();
   const float T = PFW(0, row, C.i), R = PFW(1, row, C.i), U = PFW(2, row, C.i), V = PFW(3, row, C.i);
   if (STEADY) {
     S.pT = T;
@@ -153,7 +166,7 @@ __device__ __forceinline__ void walk_take(const StepArgs& A, const WalkCtx& C, W
 // a wall-flux row or the top row, so all row tests compile away.  PF > 0: row r
 // comes from the prefetch ring and row r + PF is fetched; PF = 0: row r was
 // prefetched into S.p* and row r + 1 is loaded into them.
-template <int P, bool STEADY, int PF>
+template <int P, bool STEADY, int PF, bool VEC>
 __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, WalkState& S, int t) {
   constexpr int P0 = P & 3, P1 = (P + 3) & 3, P2 = (P + 2) & 3, P3 = (P + 1) & 3;  // rows r, r-1, r-2, r-3
   const Geo g = make_geo(A);
@@ -168,7 +181,7 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
   {
     if constexpr (PF > 0) {
       walk_take<STEADY, PF>(A, C, S, r);
-      walk_fetch(A, C, r + PF);
+      walk_fetch<VEC>(A, C, r + PF);
     }
     float lam;
     if (STEADY) {
@@ -327,6 +340,9 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
       SW(EW_OFF_T3, P3, i) = v;
     }
   }
+  // row r + 1's copies (this thread's) complete; after the barrier every
+  // thread's are, and the next walk step takes the row
+  if constexpr (PF > 0) cp_async_wait<PF - 1>();
   __syncthreads();
 
   // ---- stage 4 at y = r - 4: T3 at rows r - 5 .. r - 3; the new temperature
@@ -356,7 +372,7 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
 #undef SW
 
 // Walk of strip sx, segment sg (rows [sg L, sg L + L)) of one domain.
-template <int PF>
+template <int PF, bool VEC>
 __device__ __forceinline__ void energy_walk(const StepArgs& A, int L, int sx, int sg, int part, int s, int nsub) {
   static_assert(PF >= 0 && PF < EW_RPF, "prefetch depth within the prefetch ring");
   __shared__ float s_red[EW_W / 32][NEPART][2];
@@ -377,6 +393,17 @@ __device__ __forceinline__ void energy_walk(const StepArgs& A, int L, int sx, in
   C.ys = sg * L;
   C.ye = C.ys + L < A.ny ? C.ys + L : A.ny;
   C.last = s == nsub;
+  if constexpr (VEC) {
+    // thread i copies plane i / 16, frame columns 4 (i % 16) .. + 3: a piece
+    // starts on a multiple of 4 columns and, nx being one too, never
+    // straddles the periodic edge
+    static_assert(EW_W == 4 * 16, "16-byte prefetch: four planes of sixteen 4-column pieces");
+    const int plane = C.i >> 4, col = 4 * (C.i & 15);
+    const float* base = plane == 0 ? C.T_in : (plane == 1 ? C.rho_n : (plane == 2 ? C.ux_n : C.uy_n));
+    C.vsrc = base + wrapx(sx * EW_OUT - EW_H + col, A.nx);
+  } else {
+    C.vsrc = nullptr;
+  }
   if (threadIdx.x == 0) s_err = 0;
 
   WalkState S;
@@ -402,7 +429,9 @@ __device__ __forceinline__ void energy_walk(const StepArgs& A, int L, int sx, in
     walk_load<false>(A, C, S, t0);
   } else {
 #pragma unroll
-    for (int k = 0; k < PF; ++k) walk_fetch(A, C, t0 + k);
+    for (int k = 0; k < PF; ++k) walk_fetch<VEC>(A, C, t0 + k);
+    cp_async_wait<PF - 1>();  // row t0, for the first walk step
+    __syncthreads();
   }
   // Steps t .. t+3 touch rows t - 5 .. t + 4.  They run in the steady form when
   // every phase of each is active (t >= ys + 4, t + 3 < ye + 4) and those rows
@@ -411,15 +440,15 @@ __device__ __forceinline__ void energy_walk(const StepArgs& A, int L, int sx, in
   const int t_lo = max(C.ys + 4, A.W + 7), t_hi = min(C.ye, A.ny - 7);  // steady groups: t_lo <= t <= t_hi
   for (int t = t0; t < C.ye + 4; t += 4) {
     if (t >= t_lo && t <= t_hi) {
-      walk_step<0, true, PF>(A, C, S, t);
-      walk_step<1, true, PF>(A, C, S, t + 1);
-      walk_step<2, true, PF>(A, C, S, t + 2);
-      walk_step<3, true, PF>(A, C, S, t + 3);
+      walk_step<0, true, PF, VEC>(A, C, S, t);
+      walk_step<1, true, PF, VEC>(A, C, S, t + 1);
+      walk_step<2, true, PF, VEC>(A, C, S, t + 2);
+      walk_step<3, true, PF, VEC>(A, C, S, t + 3);
     } else {
-      walk_step<0, false, PF>(A, C, S, t);
-      walk_step<1, false, PF>(A, C, S, t + 1);
-      walk_step<2, false, PF>(A, C, S, t + 2);
-      walk_step<3, false, PF>(A, C, S, t + 3);
+      walk_step<0, false, PF, VEC>(A, C, S, t);
+      walk_step<1, false, PF, VEC>(A, C, S, t + 1);
+      walk_step<2, false, PF, VEC>(A, C, S, t + 2);
+      walk_step<3, false, PF, VEC>(A, C, S, t + 3);
     }
   }
   if constexpr (PF > 0) cp_async_wait<0>();  // copies of the rows past the walk: none left in flight at exit
@@ -432,7 +461,11 @@ __device__ __forceinline__ void energy_walk(const StepArgs& A, int L, int sx, in
 template <int L, int MINB, int PF>
 __global__ void __launch_bounds__(EW_W, MINB) k_energy_walk(const StepArgs A, int s, int nsub) {
   static_assert(L % 4 == 0, "segments start on a multiple of four rows");
-  energy_walk<PF>(A, L, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, s, nsub);
+  // 16-byte prefetch pieces where the rows allow them (nx a multiple of 4)
+  if (PF > 0 && (A.nx & 3) == 0)
+    energy_walk<PF, true>(A, L, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, s, nsub);
+  else
+    energy_walk<PF, false>(A, L, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, s, nsub);
 }
 
 template <int L, int MINB, int PF>
@@ -449,7 +482,10 @@ __global__ void __launch_bounds__(EW_W, MINB) k_energy_walk_batch(const StepArgs
   apply_dom(A, sD);
   const int local = s_bl.y;
   const int strips = (A.nx + EW_OUT - 1) / EW_OUT;
-  energy_walk<PF>(A, L, local % strips, local / strips, local, s, nsub);
+  if (PF > 0 && (A.nx & 3) == 0)
+    energy_walk<PF, true>(A, L, local % strips, local / strips, local, s, nsub);
+  else
+    energy_walk<PF, false>(A, L, local % strips, local / strips, local, s, nsub);
 }
 
 }  // namespace hlb
