@@ -161,13 +161,17 @@ __device__ __forceinline__ void walk_take(const StepArgs& A, const WalkCtx& C, W
 
 #define SW(off, slot, col) s_walk[(off) + (slot) * EW_W + (col)]
 
-// One walk step.  STEADY: an interior segment past its first eight steps:
+enum { WALK_GENERAL = 0, WALK_FILL = 1, WALK_STEADY = 2 };
+
+// One walk step.  MODE WALK_STEADY: an interior segment past its first eight steps:
 // every phase is active and no row of the step is solid, Dirichlet, a ghost,
 // a wall-flux row or the top row, so all row tests compile away.  PF > 0: row r
 // comes from the prefetch ring and row r + PF is fetched; PF = 0: row r was
 // prefetched into S.p* and row r + 1 is loaded into them.
-template <int P, bool STEADY, int PF, bool VEC>
+template <int P, int MODE, int PF, bool VEC>
 __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, WalkState& S, int t) {
+  // RANGE: the segment's row-range tests; BND: the boundary rows' tests
+  constexpr bool RANGE = MODE != WALK_STEADY, BND = MODE == WALK_GENERAL;
   constexpr int P0 = P & 3, P1 = (P + 3) & 3, P2 = (P + 2) & 3, P3 = (P + 1) & 3;  // rows r, r-1, r-2, r-3
   const Geo g = make_geo(A);
   const int ny = A.ny, W = A.W;
@@ -180,11 +184,11 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
   // (PF = 0: into registers) or start the copies of row r + PF (PF > 0)
   {
     if constexpr (PF > 0) {
-      walk_take<STEADY, PF>(A, C, S, r);
+      walk_take<!BND, PF>(A, C, S, r);
       walk_fetch<VEC>(A, C, r + PF);
     }
     float lam;
-    if (STEADY) {
+    if (!BND) {
       lam = S.pR * A.cvk;
     } else {
       const int gr = r < ny ? r : ny - 1;
@@ -199,30 +203,30 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
     SW(EW_OFF_UY, P0, i) = S.pUy;
     SW(EW_OFF_LAM, P0, i) = lam;
     const float rho_r = S.pR;
-    if constexpr (PF == 0) walk_load<STEADY>(A, C, S, r + 1);
+    if constexpr (PF == 0) walk_load<!BND>(A, C, S, r + 1);
     __syncthreads();
     S.dx[P0] = SW(EW_OFF_UX, P0, ie) - SW(EW_OFF_UX, P0, iw);
     S.sy[P0] = SW(EW_OFF_UY, P0, ie) + SW(EW_OFF_UY, P0, iw);
     // ---- coefficients of row y = r - 1 (ring 3 of the segment)
     const int y = r - 1;
-    if (STEADY || (y >= C.ys - 3 && y < C.ye + 3 && y >= 0 && y < ny)) {
+    if (!RANGE || (y >= C.ys - 3 && y < C.ye + 3 && y >= 0 && y < ny)) {
       float* cf = S.cf[P1];
 #pragma unroll
       for (int q = 0; q < NCOEF; ++q) cf[q] = 0.f;
-      const bool ysolid = !STEADY && g.solid_row(y);
+      const bool ysolid = BND && g.solid_row(y);
       S.rcv[P1] = ysolid ? A.rcv_w : S.rho1 * A.cv;
       const float l = S.lam[P1];
-      const float lS = (STEADY || y > 0) ? S.lam[P2] : l;
-      if (!STEADY) S.qf[P1] = y == ny - 2 ? harm(l, S.lam[P0]) : harm(l, lS);
-      if (STEADY || !g.dirichlet_row(y)) {
+      const float lS = (!BND || y > 0) ? S.lam[P2] : l;
+      if (BND) S.qf[P1] = y == ny - 2 ? harm(l, S.lam[P0]) : harm(l, lS);
+      if (!BND || !g.dirichlet_row(y)) {
         // lambda_f / (rho cv) = 2 kd lambda_nb / (lambda + lambda_nb), kd = lambda / (rho cv) of the row
         const float kd = ysolid ? l * A.inv_rcv_w : A.kd;
         const float lE = SW(EW_OFF_LAM, P1, ie), lW = SW(EW_OFF_LAM, P1, iw);
-        const float lN = (!STEADY && g.top_open && y == ny - 1) ? l : S.lam[P0];
+        const float lN = (BND && g.top_open && y == ny - 1) ? l : S.lam[P0];
         const float cE = 2.f * kd * lE / (l + lE), cW = 2.f * kd * lW / (l + lW);
         const float cN = 2.f * kd * lN / (l + lN);
         // row 0 under an imposed flux: no conductive flux through its bottom face
-        const float cS = (!STEADY && y == 0) ? 0.f : 2.f * kd * lS / (l + lS);
+        const float cS = (BND && y == 0) ? 0.f : 2.f * kd * lS / (l + lS);
         if (ysolid) {
           cf[C_AE] = cE;
           cf[C_AW] = cW;
@@ -250,26 +254,26 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
   // q_bottom (face 0|1), q_interface (face W-1|W) and q_top (face ny-2|ny-1 under
   // a top wall) accumulate the RK-weighted conductive flux of every stage
   auto wall_flux = [&](int y, float wk, float qf, float TS, float Tp, float TN) {
-    if (STEADY || !C.own_col) return;
+    if (!BND || !C.own_col) return;
     if (y == 1) ff_add(S.qbh, S.qbl, wk * qf * (TS - Tp));
     if (y == W) ff_add(S.qih, S.qil, wk * qf * (TS - Tp));
     if (g.top_wall && y == ny - 2) ff_add(S.qth, S.qtl, wk * qf * (Tp - TN));
   };
   auto special = [&](int y) -> bool {
-    return !STEADY && (y == 1 || y == W || (g.top_wall && y == ny - 2) || (y == 0 && g.bottom_flux));
+    return BND && (y == 1 || y == W || (g.top_wall && y == ny - 2) || (y == 0 && g.bottom_flux));
   };
   const float qc = A.q_in * A.inv_rcv_w;
 
   // ---- stage 1 at y = r - 1: T^n at rows r - 2 .. r
   {
     const int y = r - 1;
-    if (STEADY || (y >= C.ys - 3 && y < C.ye + 3 && y >= 0)) {
+    if (!RANGE || (y >= C.ys - 3 && y < C.ye + 3 && y >= 0)) {
       float v;
-      if (STEADY || y < ny) {
+      if (!BND || y < ny) {
         const int lo = EW_OFF_TN + ((r - 2) & (EW_RTN - 1)) * EW_W, mid = EW_OFF_TN + ((r - 1) & (EW_RTN - 1)) * EW_W,
                   hi = EW_OFF_TN + (r & (EW_RTN - 1)) * EW_W;
         const float Tp = S.tn[P1];
-        const float TS = (STEADY || y > 0) ? S.tn[P2] : Tp;
+        const float TS = (!BND || y > 0) ? S.tn[P2] : Tp;
         const float TN = S.tn[P0];
         float kk = walk_K(A, S.cf[P1], Tp, s_walk[mid + ie], s_walk[mid + iw], TN, TS, s_walk[hi + ie],
                           s_walk[hi + iw], s_walk[lo + ie], s_walk[lo + iw]);
@@ -291,12 +295,12 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
   // ---- stage 2 at y = r - 2: T1 at rows r - 3 .. r - 1
   {
     const int y = r - 2;
-    if (STEADY || (y >= C.ys - 2 && y < C.ye + 2 && y >= 0)) {
+    if (!RANGE || (y >= C.ys - 2 && y < C.ye + 2 && y >= 0)) {
       float v;
-      if (STEADY || y < ny) {
+      if (!BND || y < ny) {
         const int lo = EW_OFF_T1 + P3 * EW_W, mid = EW_OFF_T1 + P2 * EW_W, hi = EW_OFF_T1 + P1 * EW_W;
         const float Tp = S.t1[P2];
-        const float TS = (STEADY || y > 0) ? S.t1[P3] : Tp;
+        const float TS = (!BND || y > 0) ? S.t1[P3] : Tp;
         const float TN = S.t1[P1];
         float kk = walk_K(A, S.cf[P2], Tp, s_walk[mid + ie], s_walk[mid + iw], TN, TS, s_walk[hi + ie],
                           s_walk[hi + iw], s_walk[lo + ie], s_walk[lo + iw]);
@@ -318,12 +322,12 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
   // ---- stage 3 at y = r - 3: T2 at rows r - 4 .. r - 2
   {
     const int y = r - 3;
-    if (STEADY || (y >= C.ys - 1 && y < C.ye + 1 && y >= 0)) {
+    if (!RANGE || (y >= C.ys - 1 && y < C.ye + 1 && y >= 0)) {
       float v;
-      if (STEADY || y < ny) {
+      if (!BND || y < ny) {
         const int lo = EW_OFF_T2 + P0 * EW_W, mid = EW_OFF_T2 + P3 * EW_W, hi = EW_OFF_T2 + P2 * EW_W;
         const float Tp = S.t2[P3];
-        const float TS = (STEADY || y > 0) ? S.t2[P0] : Tp;
+        const float TS = (!BND || y > 0) ? S.t2[P0] : Tp;
         const float TN = S.t2[P2];
         float kk = walk_K(A, S.cf[P3], Tp, s_walk[mid + ie], s_walk[mid + iw], TN, TS, s_walk[hi + ie],
                           s_walk[hi + iw], s_walk[lo + ie], s_walk[lo + iw]);
@@ -348,10 +352,10 @@ __device__ __forceinline__ void walk_step(const StepArgs& A, const WalkCtx& C, W
   // ---- stage 4 at y = r - 4: T3 at rows r - 5 .. r - 3; the new temperature
   {
     const int y = r - 4;
-    if (STEADY || (y >= C.ys && y < C.ye)) {
+    if (!RANGE || (y >= C.ys && y < C.ye)) {
       const int lo = EW_OFF_T3 + P1 * EW_W, mid = EW_OFF_T3 + P0 * EW_W, hi = EW_OFF_T3 + P3 * EW_W;
       const float Tp = S.t3[P0];
-      const float TS = (STEADY || y > 0) ? S.t3[P1] : Tp;
+      const float TS = (!BND || y > 0) ? S.t3[P1] : Tp;
       const float TN = S.t3[P3];
       float kk = walk_K(A, S.cf[P0], Tp, s_walk[mid + ie], s_walk[mid + iw], TN, TS, s_walk[hi + ie],
                         s_walk[hi + iw], s_walk[lo + ie], s_walk[lo + iw]);
@@ -437,18 +441,27 @@ __device__ __forceinline__ void energy_walk(const StepArgs& A, int L, int sx, in
   // every phase of each is active (t >= ys + 4, t + 3 < ye + 4) and those rows
   // are fluid rows at least two rows from the wall rows and three from the top
   // (no solid, Dirichlet, ghost, top or wall-flux row).
-  const int t_lo = max(C.ys + 4, A.W + 7), t_hi = min(C.ye, A.ny - 7);  // steady groups: t_lo <= t <= t_hi
+  // Groups whose rows are all such rows but not every phase is active (the
+  // pipeline's fill at the segment's start) run WALK_FILL: the row-range tests
+  // of the general form without its boundary-row tests.
+  const int r_lo = A.W + 7, r_hi = A.ny - 7;
+  const int t_lo = max(C.ys + 4, r_lo), t_hi = min(C.ye, r_hi);  // steady groups: t_lo <= t <= t_hi
   for (int t = t0; t < C.ye + 4; t += 4) {
     if (t >= t_lo && t <= t_hi) {
-      walk_step<0, true, PF, VEC>(A, C, S, t);
-      walk_step<1, true, PF, VEC>(A, C, S, t + 1);
-      walk_step<2, true, PF, VEC>(A, C, S, t + 2);
-      walk_step<3, true, PF, VEC>(A, C, S, t + 3);
+      walk_step<0, WALK_STEADY, PF, VEC>(A, C, S, t);
+      walk_step<1, WALK_STEADY, PF, VEC>(A, C, S, t + 1);
+      walk_step<2, WALK_STEADY, PF, VEC>(A, C, S, t + 2);
+      walk_step<3, WALK_STEADY, PF, VEC>(A, C, S, t + 3);
+    } else if (t >= r_lo && t <= r_hi) {
+      walk_step<0, WALK_FILL, PF, VEC>(A, C, S, t);
+      walk_step<1, WALK_FILL, PF, VEC>(A, C, S, t + 1);
+      walk_step<2, WALK_FILL, PF, VEC>(A, C, S, t + 2);
+      walk_step<3, WALK_FILL, PF, VEC>(A, C, S, t + 3);
     } else {
-      walk_step<0, false, PF, VEC>(A, C, S, t);
-      walk_step<1, false, PF, VEC>(A, C, S, t + 1);
-      walk_step<2, false, PF, VEC>(A, C, S, t + 2);
-      walk_step<3, false, PF, VEC>(A, C, S, t + 3);
+      walk_step<0, WALK_GENERAL, PF, VEC>(A, C, S, t);
+      walk_step<1, WALK_GENERAL, PF, VEC>(A, C, S, t + 1);
+      walk_step<2, WALK_GENERAL, PF, VEC>(A, C, S, t + 2);
+      walk_step<3, WALK_GENERAL, PF, VEC>(A, C, S, t + 3);
     }
   }
   if constexpr (PF > 0) cp_async_wait<0>();  // copies of the rows past the walk: none left in flight at exit
